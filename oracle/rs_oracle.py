@@ -1,0 +1,502 @@
+"""FP64 CPU oracle of the range-separated (RS) tensor method for the N-particle
+Newton potential sum (Benner, Khoromskaia, Khoromskij, arXiv:1606.09218).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain numpy/scipy, float64,
+no blocking or fusion.  Each function names the passage of the paper it follows;
+where the paper is silent or garbled the reading taken is stated in the docstring.
+
+Notation follows the paper: b (half-width of the box), n (grid points per axis), h
+(mesh size), t_k / a_k (sinc nodes / weights), p_k (1-D canonical factors of the
+reference tensor P_R), R = R_l + R_s (long / short split), x_nu / z_nu (centres and
+charges), U^(l) (side matrices), xi (canonical weights), Z0^(l) (Tucker bases),
+beta (Tucker core), gamma (window half-width in grid steps).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erf, erfc
+
+SQRT_PI = math.sqrt(math.pi)
+
+
+# ----------------------------------------------------------------------------
+# Grid and quadrature  (Sec. 2.2)
+# ----------------------------------------------------------------------------
+def grid(b: float, n: int):
+    """Vertex grid on [-b, b]: x_i = -b + i*h, i = 0..n-1, h = 2b/(n-1).
+
+    Sec. 2.2 uses h = 2b/n with n even and the origin at the grid centre; with the
+    odd sizes n = 2^k + 1 used here the centred vertex grid keeps the origin on a
+    grid point (index (n-1)/2).  Reading: vertex grid with h = 2b/(n-1)."""
+    h = 2.0 * b / (n - 1)
+    return h, -b + h * np.arange(n, dtype=np.float64)
+
+
+def sinc_quadrature(R: int, h_q: float, u0: float):
+    """Nodes and weights of the sinc quadrature of the Laplace-Gauss transform
+    1/z = (2/sqrt(pi)) * int_0^inf exp(-z^2 t^2) dt   (Sec. 2.2, Eqs. (2.6)-(2.8)).
+
+    Eq. (2.7) prints t_k = k*h_M, a_k = a(t_k)*h_M, which taken literally puts a node
+    at t = 0 whose constant term spoils 1/z away from the origin.  Reading: the
+    exponential-sinc rule of the same transform after the substitution t = e^u,
+    1/z = (2/sqrt(pi)) int_R exp(-z^2 e^{2u}) e^u du, sampled at u_k = u0 + k*h_q,
+    k = 0..R-1, so t_k = exp(u_k) and a_k = (2/sqrt(pi)) * h_q * t_k (> 0).  Nodes are
+    returned in increasing order of t_k."""
+    k = np.arange(R, dtype=np.float64)
+    t = np.exp(u0 + k * h_q)
+    a = (2.0 / SQRT_PI) * h_q * t
+    return t, a
+
+
+def kernel_sum(t, a, rho):
+    """sum_k a_k exp(-t_k^2 rho^2): the separable Gaussian-sum approximation of 1/rho
+    (Sec. 2.2, Eq. (2.8)) evaluated at radii ``rho``."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return (a[None, :] * np.exp(-(t[None, :] * rho.reshape(-1, 1)) ** 2)).sum(1).reshape(rho.shape)
+
+
+def cell_average_gaussian(t: float, h: float, centre_offset):
+    """(1/h) * int_{c-h/2}^{c+h/2} exp(-t^2 x^2) dx for cell centres c = ``centre_offset``.
+
+    This is b_i(t_k)/h, the Galerkin projection of a 1-D Gaussian onto piecewise
+    constant basis functions (Sec. 2.2, Eq. (2.5) and the definition of the vectors
+    p_k^(l) before Eq. (2.10)), divided by the cell width.  Reading: cell averages
+    (the projection divided by h) so that P_R approximates the cell average of 1/|x|
+    rather than h^3 times it.  Closed form by the error function; the tail uses the
+    complementary function erfc(x) = 1 - erf(x), with erf(b)-erf(a) = erfc(a)-erfc(b),
+    to avoid the cancellation of two numbers close to one."""
+    c = np.abs(np.asarray(centre_offset, dtype=np.float64))
+    lo = t * (c - 0.5 * h)
+    hi = t * (c + 0.5 * h)
+    diff = np.where(lo > 0.5, erfc(lo) - erfc(hi), erf(hi) - erf(lo))
+    return SQRT_PI / (2.0 * t * h) * diff
+
+
+def reference_factors(t, a, h: float, n: int):
+    """1-D factors of the reference canonical tensor on the doubled index range.
+
+    Row k holds p_k[d] = a_k^{1/3} * (cell average of exp(-t_k^2 x^2) over the cell
+    centred at d*h), d = -(n-1)..(n-1), stored at column d + n - 1.  P_R =
+    sum_k p_k (x) p_k (x) p_k (Sec. 2.2, Eq. (2.10); the doubled grid of Sec. 3.2 that
+    the shift-and-windowing transform of Eq. (3.4) reads from).  The three modes share
+    the same vectors (Sec. 2.2, symmetry of the Newton kernel)."""
+    d = np.arange(-(n - 1), n, dtype=np.float64) * h
+    out = np.empty((len(t), 2 * n - 1))
+    for k in range(len(t)):
+        out[k] = a[k] ** (1.0 / 3.0) * cell_average_gaussian(t[k], h, d)
+    return out
+
+
+def collocation_factors_at(t, a, y):
+    """Collocated 1-D factors a_k^{1/3} * exp(-t_k^2 y^2) at offsets ``y`` (any shape),
+    returned with a leading axis over k.  Sec. 3.2 (remark before Theorem 3.2) allows
+    collocation of the Gaussians at cell centres in place of the Galerkin projection;
+    used for particles that are not on grid points."""
+    y = np.asarray(y, dtype=np.float64)
+    return (a ** (1.0 / 3.0)).reshape((-1,) + (1,) * y.ndim) * np.exp(-(t.reshape((-1,) + (1,) * y.ndim) * y) ** 2)
+
+
+def split(R: int, R_s: int):
+    """Index sets of the long- and short-range terms (Sec. 2.3, Eqs. (2.11)-(2.12)).
+
+    Eq. (2.11) lists R_l + 1 long nodes and the text uses R_l + R_s = R.  Reading:
+    R_l = R - R_s, the long part takes the R_l smallest t_k (k = 0..R_l-1) and the
+    short part the R_s largest."""
+    R_l = R - R_s
+    return np.arange(R_l), np.arange(R_l, R)
+
+
+def reference_value_at_origin(pk, kset, n: int):
+    """P_R restricted to ``kset`` at the origin cell: sum_{k in kset} p_k[0]^3.
+    Enters the self-interaction term of Eqs. (4.6)-(4.7) (Lemma 4.1)."""
+    c = n - 1
+    return float(np.sum(pk[kset, c] ** 3))
+
+
+def window_halfwidth(pk, kshort, n: int, delta: float) -> int:
+    """Half-width gamma (grid steps) of the cube that holds each short-range term.
+
+    The short-range Gaussians are cut off where they fall below a threshold delta
+    (Sec. 2.3, criterion (A), Eq. (2.13)); the windows are the gamma-vicinities of the
+    cumulated canonical tensor (Def. 3.4, Def. 3.6).  Criterion (A) applied literally
+    to all nodes would also pick the smallest t_k, so it is applied to the short set
+    only.  Reading: gamma = min{g >= 0 : sum_{k short} p_k[g+1] * p_k[0]^2 <= delta},
+    the largest value any truncated point (one coordinate offset > g, the others at
+    the centre) could have carried, capped at n-1."""
+    c = n - 1
+    for g in range(0, n):
+        if g + 1 > n - 1:
+            return n - 1
+        v = float(np.sum(pk[kshort, c + g + 1] * pk[kshort, c] ** 2))
+        if v <= delta:
+            return g
+    return n - 1
+
+
+def snap_to_grid(xyz, b: float, h: float, n: int):
+    """Grid multi-index j^(nu) of each centre: the particle is moved to its nearest
+    grid point (Sec. 3.2 assumes x_nu = h*j^(nu) on the grid).  Ties are rounded away
+    from zero.  Raises if a centre lies outside [-b, b]^3."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    if np.any(np.abs(xyz) > b * (1 + 1e-12)):
+        raise ValueError("particle outside the box")
+    s = (xyz + b) / h
+    j = np.floor(s + 0.5).astype(np.int64)
+    return np.clip(j, 0, n - 1)
+
+
+# ----------------------------------------------------------------------------
+# Full-rank canonical sums (no range split, no truncation)  (Sec. 3.2, Eq. (3.4))
+# ----------------------------------------------------------------------------
+def canonical_sum_grid(j, z, pk, kset, n: int):
+    """P = sum_nu z_nu W_nu(sum_{k in kset} p_k (x) p_k (x) p_k) on the whole n^3 grid,
+    where W_nu shifts the reference tensor to the grid index j^(nu) (Sec. 3.2,
+    Eqs. (3.4)-(3.5)).  kset = all R terms gives P_0, the long set gives P_l, the short
+    set the untruncated P_s.  Computed as a plain sum of N*|kset| rank-one tensors,
+    one matrix product per first index."""
+    c = n - 1
+    i = np.arange(n)
+    cols = []
+    for l in range(3):
+        idx = i[:, None] - j[None, :, l] + c                  # (n, N)
+        U = pk[kset][:, idx]                                  # (|kset|, n, N)
+        cols.append(U.transpose(1, 2, 0).reshape(n, -1))      # (n, N*|kset|)
+    w = np.repeat(np.asarray(z, dtype=np.float64), len(kset))
+    P = np.empty((n, n, n))
+    A = cols[1] * w[None, :]
+    for i1 in range(n):
+        P[i1] = (A * cols[0][i1][None, :]) @ cols[2].T
+    return P
+
+
+def canonical_sum_points(j, z, pk, kset, idx_pts, chunk: int = 256):
+    """The same sum as ``canonical_sum_grid`` evaluated at the grid multi-indices
+    ``idx_pts`` (M, 3) only (entry-wise definition of Eq. (3.4))."""
+    n = (pk.shape[1] + 1) // 2
+    c = n - 1
+    idx_pts = np.asarray(idx_pts, dtype=np.int64)
+    z = np.asarray(z, dtype=np.float64)
+    out = np.empty(len(idx_pts))
+    sub = pk[kset]
+    for s in range(0, len(idx_pts), chunk):
+        p = idx_pts[s:s + chunk]
+        d = p[:, None, :] - j[None, :, :] + c                 # (m, N, 3)
+        f = sub[:, d[..., 0]] * sub[:, d[..., 1]] * sub[:, d[..., 2]]   # (|k|, m, N)
+        out[s:s + chunk] = np.einsum("kmn,n->m", f, z)
+    return out
+
+
+def direct_sum_points(xyz_src, z, pts):
+    """P(x) = sum_nu z_nu / |x - x_nu|  (Sec. 1, Eq. (1.1); Sec. 3.1, Eq. (3.1)) at the
+    points ``pts`` (M, 3).  Terms with |x - x_nu| = 0 are skipped."""
+    pts = np.asarray(pts, dtype=np.float64)
+    out = np.empty(len(pts))
+    for s in range(0, len(pts), 512):
+        d = pts[s:s + 512, None, :] - xyz_src[None, :, :]
+        r = np.sqrt(np.einsum("mnk,mnk->mn", d, d))
+        with np.errstate(divide="ignore"):
+            inv = np.where(r > 0, 1.0 / np.where(r > 0, r, 1.0), 0.0)
+        out[s:s + 512] = inv @ z
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Long-range side matrices and RHOSVD  (Sec. 3.2, Eq. (3.5); Sec. 6)
+# ----------------------------------------------------------------------------
+def side_matrices(j, z, pk, klong, n: int):
+    """Side matrices U^(l) (n x N*R_l) and weights xi of the long-range canonical sum
+    P_l = xi x_1 U^(1) x_2 U^(2) x_3 U^(3)  (Eq. (2.4) form of Eq. (3.5)).
+
+    Column (nu, k) of U^(l) is w_nu * p_k[i - j_l^(nu)] with w_nu = |z_nu|^{1/3}; the sign
+    of z_nu goes into xi.  The paper normalises the columns and keeps all weights in xi
+    (Eq. (2.1)) without saying how xi enters the truncation.  Reading: the charge
+    magnitude is spread evenly over the three modes."""
+    c = n - 1
+    i = np.arange(n)
+    z = np.asarray(z, dtype=np.float64)
+    w = np.abs(z) ** (1.0 / 3.0)
+    Us = []
+    for l in range(3):
+        idx = i[:, None] - j[None, :, l] + c
+        U = pk[klong][:, idx] * w[None, None, :]             # (R_l, n, N)
+        Us.append(np.ascontiguousarray(U.transpose(1, 2, 0).reshape(n, -1)))
+    xi = np.repeat(np.sign(z), len(klong))
+    return Us, xi
+
+
+def collocated_side_matrices(xyz, z, t, a, klong, xgrid):
+    """Side matrices for centres off the grid: column (nu, k) of U^(l) is
+    w_nu * a_k^{1/3} * exp(-t_k^2 (x_i - x_l^(nu))^2) (collocation, Sec. 3.2 remark before
+    Theorem 3.2), weights as in ``side_matrices``."""
+    z = np.asarray(z, dtype=np.float64)
+    w = np.abs(z) ** (1.0 / 3.0)
+    Us = []
+    for l in range(3):
+        y = xgrid[:, None] - xyz[None, :, l]                   # (n, N)
+        f = collocation_factors_at(t[klong], a[klong], y)      # (R_l, n, N)
+        U = f * w[None, None, :]
+        Us.append(np.ascontiguousarray(U.transpose(1, 2, 0).reshape(len(xgrid), -1)))
+    xi = np.repeat(np.sign(z), len(klong))
+    return Us, xi
+
+
+def rhosvd_rank(sigma, eps: float, cap: int = 0) -> int:
+    """Smallest r with sum_{k>r} sigma_k^2 <= (eps^2/3) * sum_k sigma_k^2, capped by ``cap``
+    (> 0) and at least 1.  Sec. 6 (step (I) discards singular vectors "up to a given rank
+    threshold" and mentions an eps-truncation criterion); the split of the budget into
+    eps^2/3 per mode follows the sum over the three modes in the error bound of
+    Lemma 3.12."""
+    e2 = np.asarray(sigma, dtype=np.float64) ** 2
+    total = e2.sum()
+    tail = np.concatenate([np.cumsum(e2[::-1])[::-1], [0.0]])   # tail[r] = sum_{k>=r}
+    thr = (eps * eps / 3.0) * total
+    r = int(np.argmax(tail <= thr))
+    r = max(r, 1)
+    if cap and cap > 0:
+        r = min(r, int(cap))
+    return r
+
+
+def rhosvd(Us, xi, eps: float, cap: int = 0, ranks=None):
+    """Canonical-to-Tucker transform by the reduced HOSVD (Sec. 6, Eq. (6.1), Def. 6.1,
+    Eqs. (6.2)-(6.3); no ALS sweeps, m_max = 0).
+
+    (I)  SVD of each side matrix U^(l) = Z^(l) D_l V^(l)^T; keep the r_l dominant left
+         singular vectors Z0^(l).
+    (II) project, U~^(l) = Z0^(l)^T U^(l), and form the core
+         beta = xi x_1 U~^(1) x_2 U~^(2) x_3 U~^(3).
+    Returns (Z0 list, beta, ranks, singular values list)."""
+    Z0s, sig, rk = [], [], []
+    for l in range(3):
+        Zl, s, _ = np.linalg.svd(Us[l], full_matrices=False)
+        r = rhosvd_rank(s, eps, cap) if ranks is None else int(ranks[l])
+        Z0s.append(Zl[:, :r])
+        sig.append(s)
+        rk.append(r)
+    Y = [Z0s[l].T @ Us[l] for l in range(3)]
+    beta = np.einsum("aK,bK,cK,K->abc", Y[0], Y[1], Y[2], xi, optimize=True)
+    return Z0s, beta, rk, sig
+
+
+def tucker_full(beta, Vs):
+    """beta x_1 V^(1) x_2 V^(2) x_3 V^(3) on the full grid (Eq. (2.3))."""
+    return np.einsum("abc,ia,jb,kc->ijk", beta, Vs[0], Vs[1], Vs[2], optimize=True)
+
+
+def tucker_points(beta, Vs, idx_pts):
+    """Entries of the Tucker tensor at grid multi-indices (long-range term of Lemma 3.10)."""
+    idx_pts = np.asarray(idx_pts, dtype=np.int64)
+    A = Vs[0][idx_pts[:, 0]]
+    B = Vs[1][idx_pts[:, 1]]
+    C = Vs[2][idx_pts[:, 2]]
+    return np.einsum("abc,ma,mb,mc->m", beta, A, B, C, optimize=True)
+
+
+def canonical_norm2(Us, xi):
+    """||P||_F^2 of a canonical tensor xi x_l U^(l):  xi^T (G1 * G2 * G3) xi with the
+    column Gram matrices G_l = U^(l)^T U^(l)  (entry-wise product)."""
+    G = (Us[0].T @ Us[0]) * (Us[1].T @ Us[1]) * (Us[2].T @ Us[2])
+    return float(xi @ G @ xi)
+
+
+# ----------------------------------------------------------------------------
+# Short-range part: cumulated canonical tensor of windows  (Sec. 3.3)
+# ----------------------------------------------------------------------------
+def windows_full(j, z, pk, kshort, gamma: int, n: int):
+    """Uniform cumulated canonical tensor sum_nu z_nu U_nu (Def. 3.4, Def. 3.6, Eq. (3.8)):
+    U_nu is the short-range reference tensor sum_{k short} p_k (x) p_k (x) p_k shifted to
+    j^(nu) and kept only on the cube |i_l - j_l^(nu)| <= gamma (clipped to the grid).
+    Windows may overlap (the "soft" strategy of Example 3.5); overlaps add."""
+    c = n - 1
+    P = np.zeros((n, n, n))
+    for nu in range(len(z)):
+        if z[nu] == 0:
+            continue
+        lo = np.maximum(j[nu] - gamma, 0)
+        hi = np.minimum(j[nu] + gamma, n - 1)
+        f = []
+        for l in range(3):
+            d = np.arange(lo[l], hi[l] + 1) - j[nu, l] + c
+            f.append(pk[kshort][:, d])                         # (R_s, len)
+        block = np.einsum("ka,kb,kc->abc", f[0], f[1], f[2])
+        P[lo[0]:hi[0] + 1, lo[1]:hi[1] + 1, lo[2]:hi[2] + 1] += z[nu] * block
+    return P
+
+
+def windows_points(j, z, pk, kshort, gamma: int, idx_pts):
+    """Short-range entries sum_{nu in L(i)} c_nu U_nu(i) at grid multi-indices, where L(i)
+    lists the windows that contain i (Lemma 3.10, second term)."""
+    n = (pk.shape[1] + 1) // 2
+    c = n - 1
+    idx_pts = np.asarray(idx_pts, dtype=np.int64)
+    out = np.zeros(len(idx_pts))
+    sub = pk[kshort]
+    for s in range(0, len(idx_pts), 256):
+        p = idx_pts[s:s + 256]
+        d = p[:, None, :] - j[None, :, :]                      # (m, N, 3)
+        inside = np.all(np.abs(d) <= gamma, axis=2) & (np.asarray(z)[None, :] != 0)
+        dd = d + c
+        f = sub[:, dd[..., 0]] * sub[:, dd[..., 1]] * sub[:, dd[..., 2]]
+        out[s:s + 256] = np.einsum("kmn,mn,n->m", f, inside.astype(np.float64), z)
+    return out
+
+
+def rs_tucker_full(beta, Vs, j, z, pk, kshort, gamma, n):
+    """Full-grid value of the RS-Tucker tensor (Def. 3.9, Eq. (3.11)):
+    Tucker long-range part plus the cumulated short-range windows."""
+    return tucker_full(beta, Vs) + windows_full(j, z, pk, kshort, gamma, n)
+
+
+# ----------------------------------------------------------------------------
+# Energy and forces  (Sec. 4.2, Sec. 4.3)
+# ----------------------------------------------------------------------------
+def energy_direct(xyz, z):
+    """E_N = 1/2 sum_j z_j sum_{k != j} z_k / |x_j - x_k|   (Sec. 4.2, Eq. (4.4))."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    E = 0.0
+    for s in range(0, len(z), 1024):
+        d = xyz[s:s + 1024, None, :] - xyz[None, :, :]
+        r = np.sqrt(np.einsum("mnk,mnk->mn", d, d))
+        rows = np.arange(s, min(s + 1024, len(z)))
+        r[np.arange(len(rows)), rows] = np.inf
+        E += float(z[rows] @ (1.0 / r) @ z)
+    return 0.5 * E
+
+
+def energy_scale(xyz, z):
+    """sum_{j<k} |z_j z_k| / |x_j - x_k|: the size against which energy errors are
+    measured (near-neutral systems make E_N itself small)."""
+    return energy_direct(xyz, np.abs(z))
+
+
+def energy_from_potential(p_at_particles, z, self_value):
+    """E = 1/2 sum_j z_j (P(x_j) - z_j * P_ref(0))  (Sec. 4.2, Eq. (4.7) with P = P_0 and
+    P_ref = P_R; Eq. (4.6), Lemma 4.1, with P = P_l and P_ref = P_{R_l})."""
+    z = np.asarray(z, dtype=np.float64)
+    return 0.5 * float(np.sum(z * (np.asarray(p_at_particles) - z * self_value)))
+
+
+def forces_direct(xyz, z):
+    """F_j = -dE_N/dx_j = z_j sum_{k != j} z_k (x_j - x_k) / |x_j - x_k|^3.
+
+    Sec. 4.3 prints a factor 1/2 in front of this sum; differentiating Eq. (4.4), in
+    which every pair appears twice, gives none.  Reading: no factor 1/2 (pinned by a
+    finite-difference test of ``energy_direct``)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    F = np.zeros_like(xyz)
+    for s in range(0, len(z), 1024):
+        d = xyz[s:s + 1024, None, :] - xyz[None, :, :]
+        r2 = np.einsum("mnk,mnk->mn", d, d)
+        rows = np.arange(s, min(s + 1024, len(z)))
+        r2[np.arange(len(rows)), rows] = np.inf
+        w = z[None, :] / (r2 * np.sqrt(r2))
+        F[rows] = z[rows, None] * np.einsum("mn,mnk->mk", w, d)
+    return F
+
+
+def gaussian_pair_energy(xyz, z, t, a, kset):
+    """1/2 sum_{j != nu} z_j z_nu K(x_j - x_nu) with K(r) = sum_{k in kset} a_k exp(-t_k^2 |r|^2):
+    the pair-sum form of Eq. (4.6) for collocated (continuous) Gaussians, where the
+    self term z_j^2 K(0) cancels exactly (Lemma 4.1)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    E = 0.0
+    for s in range(0, len(z), 512):
+        d = xyz[s:s + 512, None, :] - xyz[None, :, :]
+        r2 = np.einsum("mnk,mnk->mn", d, d)
+        K = np.zeros_like(r2)
+        for k in kset:
+            K += a[k] * np.exp(-t[k] ** 2 * r2)
+        rows = np.arange(s, min(s + 512, len(z)))
+        K[np.arange(len(rows)), rows] = 0.0
+        E += float(z[rows] @ K @ z)
+    return 0.5 * E
+
+
+def gaussian_pair_forces(xyz, z, t, a, kset):
+    """-d/dx_j of ``gaussian_pair_energy``:
+    F_j = z_j sum_{nu != j} z_nu sum_k 2 a_k t_k^2 (x_j - x_nu) exp(-t_k^2 |x_j - x_nu|^2),
+    i.e. F_j = -z_j grad P_kset(x_j) with the self term removed (Sec. 4.3)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    F = np.zeros_like(xyz)
+    for s in range(0, len(z), 512):
+        d = xyz[s:s + 512, None, :] - xyz[None, :, :]
+        r2 = np.einsum("mnk,mnk->mn", d, d)
+        W = np.zeros_like(r2)
+        for k in kset:
+            W += 2.0 * a[k] * t[k] ** 2 * np.exp(-t[k] ** 2 * r2)
+        rows = np.arange(s, min(s + 512, len(z)))
+        W[np.arange(len(rows)), rows] = 0.0
+        F[rows] = z[rows, None] * np.einsum("mn,n,mnk->mk", W, z, d)
+    return F
+
+
+# ----------------------------------------------------------------------------
+# Whole-problem driver used by the tests
+# ----------------------------------------------------------------------------
+class Problem:
+    """All reference quantities of one snapped particle set under one parameter set.
+
+    ``cfg`` keys: b, n, R, R_s, h_q, u0, eps, rank_cap, delta_rel."""
+
+    def __init__(self, cfg: dict, xyz, z):
+        self.cfg = cfg
+        self.b = float(cfg["b"])
+        self.n = int(cfg["n"])
+        self.R = int(cfg["R"])
+        self.R_s = int(cfg["R_s"])
+        self.h, self.x = grid(self.b, self.n)
+        self.t, self.a = sinc_quadrature(self.R, float(cfg["h_q"]), float(cfg["u0"]))
+        self.pk = reference_factors(self.t, self.a, self.h, self.n)
+        self.klong, self.kshort = split(self.R, self.R_s)
+        self.kall = np.arange(self.R)
+        self.PR0 = reference_value_at_origin(self.pk, self.kall, self.n)
+        self.PRl0 = reference_value_at_origin(self.pk, self.klong, self.n)
+        self.delta = float(cfg["delta_rel"]) * self.PR0
+        self.gamma = window_halfwidth(self.pk, self.kshort, self.n, self.delta)
+        self.xyz = np.asarray(xyz, dtype=np.float64)
+        self.z = np.asarray(z, dtype=np.float64)
+        self.j = snap_to_grid(self.xyz, self.b, self.h, self.n)
+        self.xyz_snapped = self.x[self.j]
+
+    # full-rank canonical sums
+    def P0_grid(self):
+        return canonical_sum_grid(self.j, self.z, self.pk, self.kall, self.n)
+
+    def Pl_grid(self):
+        return canonical_sum_grid(self.j, self.z, self.pk, self.klong, self.n)
+
+    def Ps_grid(self):
+        return canonical_sum_grid(self.j, self.z, self.pk, self.kshort, self.n)
+
+    def P0_points(self, idx):
+        return canonical_sum_points(self.j, self.z, self.pk, self.kall, idx)
+
+    def Pl_points(self, idx):
+        return canonical_sum_points(self.j, self.z, self.pk, self.klong, idx)
+
+    # RS-Tucker
+    def tucker(self, eps=None, cap=None, ranks=None):
+        Us, xi = side_matrices(self.j, self.z, self.pk, self.klong, self.n)
+        e = float(self.cfg["eps"]) if eps is None else eps
+        c = int(self.cfg.get("rank_cap", 0)) if cap is None else cap
+        Z0s, beta, rk, sig = rhosvd(Us, xi, e, c, ranks)
+        return Z0s, beta, rk, sig, Us, xi
+
+    def windows_grid(self):
+        return windows_full(self.j, self.z, self.pk, self.kshort, self.gamma, self.n)
+
+    def windows_points(self, idx):
+        return windows_points(self.j, self.z, self.pk, self.kshort, self.gamma, idx)
+
+    # energies
+    def energy_direct_snapped(self):
+        return energy_direct(self.xyz_snapped, self.z)
+
+    def energy_P0(self):
+        return energy_from_potential(self.P0_points(self.j), self.z, self.PR0)

@@ -1,0 +1,439 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+numerical integration, closed forms, brute force on tiny grids, invariants and
+textbook constants.  Each test names the passage it pins; a plausible mistake in
+the oracle (dropped term, wrong sign, transposed operand, wrong normalisation)
+fails at least one of them."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import rs_oracle as O
+from workloads import load_config, make_particles
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
+def small_cfg(**kw):
+    cfg = dict(b=4.0, n=33, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8)
+    cfg.update(kw)
+    return cfg
+
+
+def random_particles(rng, N, half, sep):
+    pts = []
+    while len(pts) < N:
+        x = rng.uniform(-half, half, 3)
+        if all(np.linalg.norm(x - p) >= sep for p in pts):
+            pts.append(x)
+    return np.array(pts), rng.uniform(-1, 1, N)
+
+
+# ---------------------------------------------------------------- Sec. 2.2 factors
+@pytest.mark.parametrize("t", [1e-4, 0.03, 0.7, 3.0, 30.0])
+@pytest.mark.parametrize("h", [0.03125, 0.15625])
+def test_cell_average_matches_numerical_integration(t, h):
+    """Galerkin factor (Eq. (2.5), vectors before Eq. (2.10)) against adaptive quadrature."""
+    for d in [0, 1, 2, 5, 17, 60]:
+        c = d * h
+        ref, _ = integrate.quad(lambda x: math.exp(-t * t * x * x), c - h / 2, c + h / 2,
+                                epsabs=0.0, epsrel=1e-13, limit=200)
+        got = float(O.cell_average_gaussian(t, h, c)) * h
+        if ref > 1e-250:
+            assert abs(got - ref) <= 1e-11 * ref + 1e-300, (t, h, d, got, ref)
+        # symmetric in the offset
+        assert float(O.cell_average_gaussian(t, h, -c)) == float(O.cell_average_gaussian(t, h, c))
+
+
+def test_cell_average_small_t_limit_and_total_mass():
+    """t -> 0: the cell average of exp(-t^2 x^2) tends to 1; summing the cell integrals
+    over all cells gives int_R exp(-t^2 x^2) dx = sqrt(pi)/t (golden closed form)."""
+    assert abs(float(O.cell_average_gaussian(1e-9, 0.1, 0.0)) - 1.0) < 1e-15
+    g = GOLD["gaussian_integral"]
+    h = 0.05
+    d = np.arange(-4000, 4001) * h
+    total = float(np.sum(O.cell_average_gaussian(g["t"], h, d)) * h)
+    assert abs(total - g["value"]) < 1e-12 * g["value"]
+
+
+def test_reference_factors_layout_and_weights():
+    """p_k[d] = a_k^{1/3} * cell average (Eq. (2.10)); stored at column d + n - 1."""
+    t, a = O.sinc_quadrature(6, 0.8, -3.0)
+    h, n = 0.1, 9
+    pk = O.reference_factors(t, a, h, n)
+    assert pk.shape == (6, 2 * n - 1)
+    for k in range(6):
+        for d in (-8, -3, 0, 4, 8):
+            ref, _ = integrate.quad(lambda x: math.exp(-t[k] ** 2 * x * x), d * h - h / 2, d * h + h / 2,
+                                    epsabs=0, epsrel=1e-13)
+            assert abs(pk[k, d + n - 1] - a[k] ** (1 / 3) * ref / h) <= 1e-11 * abs(pk[k, d + n - 1])
+
+
+# ---------------------------------------------------------------- Sec. 2.2 quadrature
+@pytest.mark.parametrize("name", ["c1_box64_n129", "c2_protein1000_n513", "c3_nacl28_n1025", "c5_forces4096_n513"])
+def test_quadrature_approximates_inverse_distance(name):
+    """sum_k a_k exp(-t_k^2 rho^2) ~ 1/rho (Eqs. (2.6)-(2.8)) within the fitted error, on a
+    radius grid denser than the one used by the fit."""
+    cfg = load_config(name)
+    t, a = O.sinc_quadrature(cfg["R"], cfg["h_q"], cfg["u0"])
+    f = cfg["fit"]
+    rho = np.geomspace(f["rho_min"], f["rho_max"], 20011)
+    err = np.max(np.abs(O.kernel_sum(t, a, rho) * rho - 1.0))
+    assert err <= f["max_rel_err"] * 1.02 + 1e-12
+    assert err < 6e-3
+
+
+def test_quadrature_converges_exponentially():
+    """Eq. (2.9): the error decays like exp(-beta sqrt(M)); doubling R at a fixed range must
+    cut the best error by orders of magnitude."""
+    from scipy.optimize import minimize
+    rho = np.geomspace(0.05, 30.0, 3000)
+
+    def best(R):
+        f = lambda p: np.max(np.abs(O.kernel_sum(*O.sinc_quadrature(R, p[0], p[1]), rho) * rho - 1))
+        cands = [(f([hq, u]), hq, u) for hq in np.linspace(0.3, 1.5, 13) for u in np.linspace(-12, -2, 21)]
+        _, hq, u = min(cands)
+        return minimize(f, [hq, u], method="Nelder-Mead", options=dict(xatol=1e-9, fatol=1e-14, maxiter=4000)).fun
+
+    e12, e24, e36 = best(12), best(24), best(36)
+    assert e24 < 0.1 * e12 and e36 < 0.1 * e24
+
+
+# ---------------------------------------------------------------- Sec. 3.2 canonical sum
+def test_brute_force_tiny_grid():
+    """P_0 entry by entry from the definition (Eqs. (2.5), (2.10), (3.4)): for every grid
+    cell and particle, the cell average of each Gaussian integrated numerically in each
+    coordinate; no closed form, no shifted arrays."""
+    rng = np.random.default_rng(7)
+    cfg = small_cfg(b=2.0, n=9, R=6, R_s=2, h_q=0.9, u0=-2.5)
+    h, x = O.grid(cfg["b"], cfg["n"])
+    t, a = O.sinc_quadrature(cfg["R"], cfg["h_q"], cfg["u0"])
+    pk = O.reference_factors(t, a, h, cfg["n"])
+    j = rng.integers(0, cfg["n"], (3, 3))
+    z = np.array([0.7, -1.1, 0.4])
+    P = O.canonical_sum_grid(j, z, pk, np.arange(cfg["R"]), cfg["n"])
+    xc = x[j]                                   # centres
+    n = cfg["n"]
+    for i1 in range(n):
+        for i2 in range(0, n, 2):
+            for i3 in range(0, n, 3):
+                s = 0.0
+                for nu in range(3):
+                    for k in range(cfg["R"]):
+                        prod = a[k]
+                        for l, il in enumerate((i1, i2, i3)):
+                            lo, hi = x[il] - h / 2 - xc[nu, l], x[il] + h / 2 - xc[nu, l]
+                            v, _ = integrate.quad(lambda y: math.exp(-t[k] ** 2 * y * y), lo, hi,
+                                                  epsabs=0, epsrel=1e-12)
+                            prod *= v / h
+                        s += z[nu] * prod
+                assert abs(P[i1, i2, i3] - s) <= 1e-10 * max(1.0, abs(s)), (i1, i2, i3)
+
+
+def cube_average_direct(xyz_src, z, centre, h, q=6):
+    """Average of sum_nu z_nu/|x - x_nu| over the cube of side h at ``centre``
+    (tensor Gauss-Legendre rule); the closed-form counterpart of a Galerkin cell value."""
+    g, w = np.polynomial.legendre.leggauss(q)
+    g = g * h / 2
+    w = w / 2
+    X = centre[None, None, None, :] + np.stack(np.meshgrid(g, g, g, indexing="ij"), -1)
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    tot = 0.0
+    for nu in range(len(z)):
+        r = np.linalg.norm(X - xyz_src[nu], axis=-1)
+        tot += z[nu] * float(np.sum(W / r))
+    return tot
+
+
+def test_P0_matches_closed_form_inverse_distance():
+    """P_0 (Eq. (3.4)) against the cell average of sum z/|x - x_nu| (Eq. (1.1)) at grid
+    points at least 3h from every particle: the difference is bounded by the
+    quadrature's relative error times sum |z|/r."""
+    cfg = load_config("c1_box64_n129")
+    parts = make_particles(cfg)
+    pr = O.Problem(cfg, parts.xyz, parts.Z)
+    rng = np.random.default_rng(3)
+    idx = rng.integers(0, pr.n, (400, 3))
+    X = pr.x[idx]
+    d = np.linalg.norm(X[:, None, :] - pr.xyz_snapped[None], axis=-1)
+    ok = d.min(1) >= 3 * pr.h
+    idx, X, d = idx[ok][:120], X[ok][:120], d[ok][:120]
+    P = pr.P0_points(idx)
+    qerr = cfg["fit"]["max_rel_err"] * 1.02
+    for m in range(len(idx)):
+        ref = cube_average_direct(pr.xyz_snapped, pr.z, X[m], pr.h)
+        bound = qerr * float(np.sum(np.abs(pr.z) / d[m])) + 1e-9
+        assert abs(P[m] - ref) <= bound, (m, P[m], ref, bound)
+
+
+def test_points_and_grid_evaluations_agree():
+    cfg = small_cfg()
+    rng = np.random.default_rng(11)
+    xyz, z = random_particles(rng, 5, 3.0, 1.0)
+    pr = O.Problem(cfg, xyz, z)
+    G = pr.P0_grid()
+    idx = rng.integers(0, pr.n, (200, 3))
+    assert np.allclose(pr.P0_points(idx), G[idx[:, 0], idx[:, 1], idx[:, 2]], rtol=1e-13, atol=1e-13)
+
+
+def test_direct_sum_golden_point():
+    xyz = np.array([[0.0, 0, 0], [3.0, 4.0, 0]])
+    z = np.array([2.0, -5.0])
+    v = O.direct_sum_points(xyz, z, np.array([[0.0, 0.0, 1.0]]))[0]
+    assert abs(v - (2.0 / 1.0 - 5.0 / math.sqrt(26.0))) < 1e-15
+
+
+# ---------------------------------------------------------------- Sec. 2.3 split, Sec. 3.3 windows
+def test_split_identity_and_order():
+    """P_R = P_{R_s} + P_{R_l} (Eq. (2.12)); the long part holds the smallest t_k."""
+    cfg = small_cfg()
+    rng = np.random.default_rng(5)
+    xyz, z = random_particles(rng, 6, 3.0, 1.0)
+    pr = O.Problem(cfg, xyz, z)
+    assert len(pr.klong) == cfg["R"] - cfg["R_s"] and len(pr.kshort) == cfg["R_s"]
+    assert pr.t[pr.klong].max() < pr.t[pr.kshort].min()
+    P0, Pl, Ps = pr.P0_grid(), pr.Pl_grid(), pr.Ps_grid()
+    assert np.max(np.abs(Pl + Ps - P0)) <= 1e-13 * np.max(np.abs(P0))
+
+
+def test_window_truncation_and_minimal_gamma():
+    """Windows (Def. 3.4, Def. 3.6) hold the short-range part up to the cut-off: each
+    particle loses at most delta*|z| at any point; gamma is the smallest such width."""
+    cfg = small_cfg(n=41, delta_rel=1e-6)
+    rng = np.random.default_rng(9)
+    xyz, z = random_particles(rng, 4, 3.0, 1.5)
+    pr = O.Problem(cfg, xyz, z)
+    W, Ps = pr.windows_grid(), pr.Ps_grid()
+    assert np.max(np.abs(W - Ps)) <= pr.delta * np.sum(np.abs(z)) * (1 + 1e-12)
+    c = pr.n - 1
+    g = pr.gamma
+    assert np.sum(pr.pk[pr.kshort, c + g + 1] * pr.pk[pr.kshort, c] ** 2) <= pr.delta
+    if g > 0:
+        assert np.sum(pr.pk[pr.kshort, c + g] * pr.pk[pr.kshort, c] ** 2) > pr.delta
+    # point evaluation of the windows matches the grid
+    idx = rng.integers(0, pr.n, (300, 3))
+    assert np.allclose(pr.windows_points(idx), W[idx[:, 0], idx[:, 1], idx[:, 2]], rtol=1e-13, atol=1e-15)
+
+
+def test_block_orthogonality_of_disjoint_windows():
+    """Prop. 3.11 (B), (C): windows with disjoint supports are orthogonal and their norms add."""
+    cfg = small_cfg(n=41, delta_rel=1e-4)
+    pr = O.Problem(cfg, np.array([[-2.5, -2.5, -2.5], [2.5, 2.5, 2.5]]), np.array([1.0, 1.0]))
+    assert 2 * pr.gamma + 1 < abs(pr.j[0, 0] - pr.j[1, 0])
+    U1 = O.windows_full(pr.j[:1], pr.z[:1], pr.pk, pr.kshort, pr.gamma, pr.n)
+    U2 = O.windows_full(pr.j[1:], pr.z[1:], pr.pk, pr.kshort, pr.gamma, pr.n)
+    assert float(np.sum(U1 * U2)) == 0.0
+    U = pr.windows_grid()
+    assert abs(np.sum(U * U) - np.sum(U1 * U1) - np.sum(U2 * U2)) <= 1e-12 * np.sum(U * U)
+
+
+# ---------------------------------------------------------------- Sec. 6 RHOSVD
+@pytest.fixture(scope="module")
+def c1_problem():
+    cfg = load_config("c1_box64_n129")
+    p = make_particles(cfg)
+    pr = O.Problem(cfg, p.xyz, p.Z)
+    return pr, pr.Pl_grid()
+
+
+def test_side_matrices_reproduce_long_range_sum(c1_problem):
+    """xi x_l U^(l) (Eq. (2.4)) equals the long-range sum of Eq. (3.5) on the grid, and the
+    canonical norm formula gives ||P_l||_F."""
+    pr, Pl = c1_problem
+    Us, xi = O.side_matrices(pr.j, pr.z, pr.pk, pr.klong, pr.n)
+    P = np.einsum("iK,jK,kK,K->ijk", Us[0], Us[1], Us[2], xi, optimize=True)
+    assert np.max(np.abs(P - Pl)) <= 1e-12 * np.max(np.abs(Pl))
+    assert abs(O.canonical_norm2(Us, xi) - np.sum(Pl * Pl)) <= 1e-10 * np.sum(Pl * Pl)
+
+
+def test_rhosvd_full_rank_is_exact(c1_problem):
+    """Def. 6.1 with r_l = n keeps the whole column space: the projection is the identity."""
+    pr, Pl = c1_problem
+    Z0s, beta, rk, _, _, _ = pr.tucker(ranks=[pr.n] * 3)
+    assert np.max(np.abs(O.tucker_full(beta, Z0s) - Pl)) <= 1e-11 * np.max(np.abs(Pl))
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+def test_rhosvd_error_within_eps_and_pythagoras(c1_problem, eps):
+    """RHOSVD Tucker error ||P_l - P_l^T||_F <= eps ||P_l||_F (Sec. 6, eps-truncation) on the
+    full grid; the orthogonal projection obeys ||P_l||^2 = ||beta||^2 + ||P_l - P_l^T||^2."""
+    pr, Pl = c1_problem
+    Z0s, beta, rk, sig, _, _ = pr.tucker(eps=eps, cap=0)
+    PT = O.tucker_full(beta, Z0s)
+    nrm = np.linalg.norm(Pl)
+    err = np.linalg.norm(Pl - PT)
+    assert err <= eps * nrm
+    assert abs(nrm ** 2 - np.sum(beta * beta) - err ** 2) <= 1e-9 * nrm ** 2
+    for Z in Z0s:
+        assert np.allclose(Z.T @ Z, np.eye(Z.shape[1]), atol=1e-12)
+
+
+def test_rhosvd_rank_rule_and_cap(c1_problem):
+    pr, _ = c1_problem
+    _, _, rk, sig, _, _ = pr.tucker(eps=1e-6, cap=0)
+    for l in range(3):
+        e2 = sig[l] ** 2
+        r = rk[l]
+        assert e2[r:].sum() <= (1e-12 / 3) * e2.sum()
+        assert e2[r - 1:].sum() > (1e-12 / 3) * e2.sum()
+    _, beta, rk2, _, _, _ = pr.tucker(eps=1e-6, cap=16)
+    assert max(rk2) <= 16 and beta.shape == tuple(rk2)
+
+
+def test_rhosvd_bound_lemma(c1_problem):
+    """Lemma 3.12 / the RHOSVD estimate: the Tucker error is controlled by the discarded
+    side-matrix singular values, err <= sum_l (sum_{k>r_l} sigma_{l,k}^2)^{1/2} * ||xi||_inf-scaled
+    (checked in the weaker relative form err/||P_l|| <= C sum_l tail_l/||U_l||_F with C = 10)."""
+    pr, Pl = c1_problem
+    Z0s, beta, rk, sig, Us, xi = pr.tucker(eps=1e-5, cap=0)
+    err = np.linalg.norm(Pl - O.tucker_full(beta, Z0s)) / np.linalg.norm(Pl)
+    rel_tails = sum(math.sqrt(np.sum(s[r:] ** 2) / np.sum(s ** 2)) for s, r in zip(sig, rk))
+    assert err <= 10.0 * rel_tails
+
+
+def test_tucker_rank_nearly_independent_of_N():
+    """Theorem 3.2: the eps-rank of the long-range part depends on N only weakly."""
+    cfg = load_config("c1_box64_n129")
+    ranks = []
+    for N in (16, 64, 160):
+        c = dict(cfg)
+        c["particles"] = dict(cfg["particles"], N=N)
+        p = make_particles(c, seed=123 + N)
+        pr = O.Problem(c, p.xyz, p.Z)
+        _, _, rk, _, _, _ = pr.tucker(eps=1e-5, cap=0)
+        ranks.append(max(rk))
+    assert ranks[2] <= ranks[0] * 1.35 + 2, ranks
+
+
+# ---------------------------------------------------------------- symmetries
+def test_mirror_permutation_translation_linearity():
+    """P_R has identical factors in the three modes (Sec. 2.2) and the kernel is radial:
+    reflecting the particles in an axis reflects P_0, permuting axes permutes it, shifting
+    by whole cells shifts it, and P_0 is linear in the charges."""
+    cfg = small_cfg()
+    rng = np.random.default_rng(21)
+    xyz, z = random_particles(rng, 5, 2.5, 1.0)
+    pr = O.Problem(cfg, xyz, z)
+    P = pr.P0_grid()
+    n = pr.n
+    jr = pr.j.copy()
+    jr[:, 0] = n - 1 - jr[:, 0]
+    Pr = O.canonical_sum_grid(jr, z, pr.pk, pr.kall, n)
+    assert np.allclose(Pr, P[::-1], rtol=1e-12, atol=1e-13)
+    jp = pr.j[:, [2, 0, 1]]
+    Pp = O.canonical_sum_grid(jp, z, pr.pk, pr.kall, n)
+    assert np.allclose(Pp, P.transpose(2, 0, 1), rtol=1e-12, atol=1e-13)
+    js = pr.j + np.array([2, -1, 3])
+    Ps = O.canonical_sum_grid(js, z, pr.pk, pr.kall, n)
+    assert np.allclose(Ps[2:, :-1, 3:], P[:-2, 1:, :-3], rtol=1e-12, atol=1e-13)
+    P2 = O.canonical_sum_grid(pr.j, 2.5 * z, pr.pk, pr.kall, n)
+    assert np.allclose(P2, 2.5 * P, rtol=1e-13, atol=1e-13)
+
+
+def test_rs_tucker_mirror_symmetry(c1_problem):
+    """The RS-Tucker approximation commutes with reflecting the particle set."""
+    pr, _ = c1_problem
+    Z0s, beta, rk, _, _, _ = pr.tucker(eps=1e-6, cap=0)
+    P = O.tucker_full(beta, Z0s) + pr.windows_grid()
+    xyz = pr.xyz.copy()
+    xyz[:, 1] *= -1
+    q = O.Problem(pr.cfg, xyz, pr.z)
+    Z0q, bq, rq, _, _, _ = q.tucker(eps=1e-6, cap=0, ranks=rk)
+    Q = O.tucker_full(bq, Z0q) + q.windows_grid()
+    assert np.max(np.abs(Q - P[:, ::-1, :])) <= 1e-9 * np.max(np.abs(P))
+
+
+def test_snap_rounding_and_bounds():
+    h, x = O.grid(1.0, 5)   # h = 0.5
+    j = O.snap_to_grid(np.array([[-1.0, 0.24, 0.25], [1.0, -0.25, 0.74]]), 1.0, h, 5)
+    assert j.tolist() == [[0, 2, 3], [4, 2, 3]]
+    with pytest.raises(ValueError):
+        O.snap_to_grid(np.array([[1.2, 0, 0]]), 1.0, h, 5)
+
+
+# ---------------------------------------------------------------- Sec. 4.2 energy, Sec. 4.3 forces
+def test_energy_golden():
+    for key in ("two_charge_energy", "three_charge_energy"):
+        g = GOLD[key]
+        assert abs(O.energy_direct(np.array(g["xyz"]), np.array(g["z"])) - g["E"]) < 1e-14
+
+
+def test_energy_madelung_rock_salt():
+    """Alternating-charge cubes (Table 4.4 lattices): the energy per ion extrapolates in
+    1/L to -M/2 with the rock-salt Madelung constant (a factor-2 slip in Eq. (4.4) fails)."""
+    M = GOLD["madelung_rock_salt"]["M"]
+    e = {}
+    for L in (10, 16):
+        idx = np.stack(np.meshgrid(*[np.arange(L)] * 3, indexing="ij"), -1).reshape(-1, 3)
+        z = np.where(idx.sum(1) % 2 == 0, 1.0, -1.0)
+        e[L] = O.energy_direct(idx.astype(float), z) / len(z)
+    A = (16 * e[16] - 10 * e[10]) / 6.0
+    assert abs(A + M / 2) < 0.01 * M / 2, (e, A)
+
+
+def test_energy_tensor_formula_matches_direct():
+    """Eq. (4.7): 1/2 sum z_j (P_0(x_j) - z_j P_R(0)) reproduces Eq. (4.4) within the
+    quadrature error (relative to sum |z_j z_k|/r_jk)."""
+    cfg = load_config("c1_box64_n129")
+    p = make_particles(cfg)
+    pr = O.Problem(cfg, p.xyz, p.Z)
+    E = pr.energy_direct_snapped()
+    Et = pr.energy_P0()
+    scale = O.energy_scale(pr.xyz_snapped, pr.z)
+    assert abs(Et - E) <= 1.05 * cfg["fit"]["max_rel_err"] * scale
+
+
+def test_energy_long_range_lemma():
+    """Lemma 4.1: when no other particle lies inside a short-range window, Eq. (4.6) with
+    P_l alone equals Eq. (4.7) with P_0 up to the window cut-off."""
+    cfg = small_cfg(b=8.0, n=65, R=16, R_s=5, h_q=0.75, u0=-7.5)
+    rng = np.random.default_rng(31)
+    xyz, z = random_particles(rng, 6, 6.5, 5.0)
+    pr = O.Problem(cfg, xyz, z)
+    assert pr.gamma * pr.h < 5.0 - 2 * pr.h
+    E0 = pr.energy_P0()
+    El = O.energy_from_potential(pr.Pl_points(pr.j), pr.z, pr.PRl0)
+    assert abs(E0 - El) <= 0.5 * np.sum(np.abs(z)) ** 2 * pr.delta
+
+
+def test_forces_direct_finite_difference():
+    """F_j = -dE/dx_j for Eq. (4.4) (Sec. 4.3 without the printed factor 1/2)."""
+    rng = np.random.default_rng(41)
+    xyz, z = random_particles(rng, 8, 3.0, 1.0)
+    F = O.forces_direct(xyz, z)
+    hfd = 1e-5
+    for j in range(8):
+        for l in range(3):
+            xp, xm = xyz.copy(), xyz.copy()
+            xp[j, l] += hfd
+            xm[j, l] -= hfd
+            fd = -(O.energy_direct(xp, z) - O.energy_direct(xm, z)) / (2 * hfd)
+            assert abs(fd - F[j, l]) <= 1e-7 * max(1.0, abs(F[j, l]))
+
+
+def test_gaussian_pair_forces_finite_difference_and_coulomb_limit():
+    """Pair-sum form of the long-range energy (Eq. (4.6), collocated Gaussians) and its
+    forces: central differences, and with all R terms the Coulomb forces within the
+    quadrature error."""
+    cfg = load_config("c5_forces4096_n513")
+    t, a = O.sinc_quadrature(cfg["R"], cfg["h_q"], cfg["u0"])
+    rng = np.random.default_rng(43)
+    xyz, z = random_particles(rng, 10, 5.0, 1.0)
+    kl, _ = O.split(cfg["R"], cfg["R_s"])
+    F = O.gaussian_pair_forces(xyz, z, t, a, kl)
+    hfd = 1e-5
+    for j in (0, 3, 7):
+        for l in range(3):
+            xp, xm = xyz.copy(), xyz.copy()
+            xp[j, l] += hfd
+            xm[j, l] -= hfd
+            fd = -(O.gaussian_pair_energy(xp, z, t, a, kl) - O.gaussian_pair_energy(xm, z, t, a, kl)) / (2 * hfd)
+            assert abs(fd - F[j, l]) <= 1e-7 * max(1.0, np.abs(F).max())
+    Fall = O.gaussian_pair_forces(xyz, z, t, a, np.arange(cfg["R"]))
+    Fc = O.forces_direct(xyz, z)
+    assert np.max(np.abs(Fall - Fc)) <= 0.05 * np.max(np.abs(Fc))
+    Eall = O.gaussian_pair_energy(xyz, z, t, a, np.arange(cfg["R"]))
+    assert abs(Eall - O.energy_direct(xyz, z)) <= 1.05 * cfg["fit"]["max_rel_err"] * O.energy_scale(xyz, z)
