@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the RS potential path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+One step = one whole solve of the workload (sinc factors, particle snapping, long-range
+Gram matrices, RHOSVD eigen stage, Tucker core, full-grid reconstruction with the
+short-range windows, interaction energy) with the particles already resident in HBM.
+The metric is grid points per second (n^3 per solve).  For N > 1 (torchrun) every rank
+solves its own seeded replica (independent problems, weak scaling, no data-path
+collective); the reported value is the whole-job rate over the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle (full-rank canonical sum at sampled grid
+points) on the host cores, on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RS potential grid pts/s vs plain GPU path at 1e-6 rel err; served p50/p99 ms"
+UNIT = "grid_pts/s"
+DEFAULT_WORKLOAD = "c2_protein1000_n513"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+# FP32 FMA units: 152 SMs x 128 lanes x 2 flop at the 2070 MHz maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["source"] = "measured"
+        return d
+    return dict(FALLBACK_PEAKS)
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.fn = None
+
+    def start(self):
+        try:
+            fd, self.fn = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.fn, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.fn):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), reasons=parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.fn)
+        if not rows:
+            return None
+        names = ["active_mask", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in rows:
+            for nm, v in zip(names[1:], r["reasons"][1:]):
+                if v.lower().startswith("active"):
+                    seen.add(nm)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(seen), "samples": len(rows)}
+
+
+def kernel_hash() -> str:
+    """Hash of the reconstruction kernel sources: the recorded ncu traffic applies only to
+    the code it was captured from."""
+    h = hashlib.sha1()
+    for fn in ("rs_tucker.cu", "rs_eigen.cu", "rs_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1606_09218_gb300", "csrc", fn), "rb").read())
+    return h.hexdigest()[:12]
+
+
+# DRAM bytes of one reconstruction launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by the source hash it was captured from; see profiles/.
+NCU_TRAFFIC = {}
+
+
+def oracle_rate(cfg, parts, seconds: float, seed: int = 0):
+    """Grid points per second of the CPU oracle's full-rank canonical sum on a random sample
+    of grid points (bounded to about ``seconds`` of work)."""
+    import numpy as np
+    from oracle import rs_oracle as O
+    pr = O.Problem(cfg, parts.xyz, parts.Z)
+    rng = np.random.default_rng(seed)
+    m = 64
+    t0 = time.perf_counter()
+    pr.P0_points(rng.integers(0, pr.n, (m, 3)))
+    dt = max(time.perf_counter() - t0, 1e-4)
+    M = int(max(64, min(2_000_000, m * seconds / dt)))
+    idx = rng.integers(0, pr.n, (M, 3))
+    t0 = time.perf_counter()
+    pr.P0_points(idx)
+    dt = time.perf_counter() - t0
+    return M / dt, M, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from workloads import load_config, make_particles
+    cfg = load_config(args.workload)
+    parts = make_particles(cfg)
+    n = int(cfg["n"])
+    per_step = float(os.environ.get("RS_REF_STEP_S", "2.0"))
+    rates = []
+    for _ in range(args.warmup):
+        oracle_rate(cfg, parts, 0.2)
+    t_total, pts_total, M_last = 0.0, 0, 0
+    for s in range(args.steps):
+        r, M, dt = oracle_rate(cfg, parts, per_step, seed=s + 1)
+        rates.append(r)
+        t_total += dt
+        pts_total += M
+        M_last = M
+    value = pts_total / t_total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": int(len(parts.Z)), "n": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{M_last} random grid points per step, full-rank canonical sum "
+                                       f"(N*R terms per point), numpy FP64, one thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1606_09218_gb300 import RSContext, config_from_workload
+    from workloads import load_config, make_particles
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = load_config(args.workload)
+    parts = make_particles(cfg, seed=None if rank == 0 else 160609218 + 1000 * rank + int(cfg["index"]))
+    n = int(cfg["n"])
+    N = int(len(parts.Z))
+    ccfg = config_from_workload(cfg, max_particles=N)
+    ctx = RSContext(ccfg)
+    stream = torch.cuda.current_stream()
+    xyz = torch.tensor(parts.xyz, device="cuda")
+    Z = torch.tensor(parts.Z, device="cuda")
+    pot = ctx.new_potential()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        ctx.solve(xyz, Z, potential=pot, energy=True)
+    E = ctx.energy()
+    rep = ctx.report()
+    # timed region: device time of K solves, L2 flushed before each
+    ctx.profile(True)
+    ctx.profile_read()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for s in range(args.steps):
+        flush.zero_()
+        starts[s].record(stream)
+        ctx.solve(xyz, Z, potential=pot, energy=True)
+        ends[s].record(stream)
+    barrier()
+    clocks = sampler.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    stages, nsolves = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.report()["kernel_launches"] * args.steps
+    t_max = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    t_ms = float(t_max.item())
+    value = n ** 3 * args.steps * world / (t_ms * 1e-3)
+
+    # end to end through the C ABI with host buffers (pinned), energy read back each step
+    hx = torch.tensor(parts.xyz).pin_memory()
+    hz = torch.tensor(parts.Z).pin_memory()
+    hxn, hzn = hx.numpy(), hz.numpy()
+    e2e_steps = max(3, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.solve(hxn, hzn, potential=pot, energy=True)
+        ctx.energy()
+    t_e2e = time.perf_counter() - t0
+    t_e = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+    e2e_value = n ** 3 * e2e_steps * world / float(t_e.item())
+
+    # plain RS path on the same GPU: every stage in FP64
+    plain = None
+    if rank == 0 and not args.no_plain:
+        pcfg = dict(cfg)
+        pcfg["precision"] = "fp64"
+        pctx = RSContext(config_from_workload(pcfg, max_particles=N))
+        ppot = pctx.new_potential()
+        for _ in range(2):
+            pctx.solve(xyz, Z, potential=ppot, energy=True)
+        torch.cuda.synchronize()
+        ps = max(3, min(args.steps, 10))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        tp = 0.0
+        for _ in range(ps):
+            flush.zero_()
+            a.record(stream)
+            pctx.solve(xyz, Z, potential=ppot, energy=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tp += a.elapsed_time(b)
+        plain = {"value": n ** 3 * ps / (tp * 1e-3), "unit": UNIT, "ms_per_step": tp / ps,
+                 "path": "same RS pipeline with every stage in FP64 (Tucker core, mode products, output)"}
+        pctx.close()
+        del ppot
+
+    if rank != 0:
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (reconstruction GEMM: one launch per step)
+    pk = peaks()
+    r1 = rep["ranks"][0]
+    ts = 4
+    per_launch_ms = stages["reconstruct"] / max(nsolves, 1)
+    bytes_alg = ts * (n ** 3 + r1 * n * n + n * r1)
+    flops_alg = 2.0 * r1 * n ** 3
+    ai = flops_alg / bytes_alg
+    ridge = FP32_PEAK_TFLOPS * 1e12 / (pk["hbm_gbs"] * 1e9)
+    if ai > ridge:
+        ach = flops_alg / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS}
+    else:
+        ach = bytes_alg / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"]}
+    roof.update({"kernel": "reconstruction (last mode product, gemm_kernel<float>)",
+                 "traffic": NCU_TRAFFIC.get(kernel_hash()), "peak_source": pk["source"],
+                 "ms_per_launch": per_launch_ms, "algorithmic_bytes": bytes_alg,
+                 "algorithmic_flops": flops_alg})
+
+    cpu = None
+    if not args.no_cpu:
+        r, M, dt = oracle_rate(cfg, parts, float(os.environ.get("RS_CPU_SAMPLE_S", "12")))
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{M} random grid points, full-rank canonical sum (N*R terms per point), "
+                         f"numpy FP64, one thread, {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "n": n, "R": int(cfg["R"]), "R_s": int(cfg["R_s"]),
+                   "eps": cfg["eps"], "precision": cfg.get("precision"), "ranks": rep["ranks"],
+                   "gamma": rep["gamma"], "l2": "256 MiB written before every timed step",
+                   "replicas": "one independent seeded problem per rank"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * 4 * 8),
+                "d2h_bytes_per_step": 184, "steps": e2e_steps},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "stages_ms_per_step": {k: v / max(nsolves, 1) for k, v in stages.items()},
+        "plain_gpu": plain,
+        "energy": E,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain-path comparison")
+    args = ap.parse_args()
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * rs.h — C ABI of the range-separated (RS) canonical/Tucker Newton-potential library.
+ *
+ * The library assembles and evaluates the N-particle Newton potential sum
+ *     P(x) = sum_nu Z_nu / |x - x_nu|,      x, x_nu in [-b, b]^3            (Sec. 1, Eq. (1.1))
+ * on an n x n x n grid with the range-separated tensor format of Benner, Khoromskaia and
+ * Khoromskij (arXiv:1606.09218):
+ *   - a sinc-quadrature Gaussian sum gives the rank-R reference canonical tensor P_R
+ *     (Sec. 2.2, Eqs. (2.5)-(2.10));
+ *   - P_R is split into R_l long-range and R_s short-range terms (Sec. 2.3, Eqs. (2.11)-(2.12));
+ *   - the long-range sum of the N shifted references (Sec. 3.2, Eq. (3.5)) is compressed to a
+ *     Tucker tensor by the reduced HOSVD (Sec. 6, Def. 6.1, Eqs. (6.1)-(6.3));
+ *   - the short-range part is kept as a cumulated canonical tensor of local windows
+ *     (Sec. 3.3, Defs. 3.4 and 3.6);
+ *   - the RS-Tucker tensor (Def. 3.9, Eq. (3.11)) is evaluated on the full grid and at the
+ *     particles, giving the interaction energy of Sec. 4.2, Eq. (4.7) / Lemma 4.1.
+ *
+ * Conventions common to every call:
+ *   - Grid: vertex grid x_i = -b + i*h, i = 0..n-1, h = 2b/(n-1); n must be odd.
+ *   - Output grid layout: C order, P[i1][i2][i3] at offset (i1*n + i2)*n + i3 (i3 fastest).
+ *   - Every call returns an rs_status; nothing aborts or exits.  Negative values are errors,
+ *     RS_OK is success, positive values are warnings whose results are valid.
+ *   - Work is asynchronous on the stream given to rs_create, except where a call says it
+ *     synchronises.  Device pointers belong to the caller unless stated otherwise.
+ *   - A context is not thread-safe; use one context per host thread or serialise calls.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RS_OK = 0,
+    RS_RANK_CAPPED = 1,        /* warning: rank_cap (or the subspace width) bound before eps was met;
+                                  the result is valid and rs_report gives the achieved error */
+    RS_ERR_INVALID_ARG = -1,   /* bad size, null pointer, even n, R_s >= R, ... */
+    RS_ERR_OUTSIDE_BOX = -2,   /* a centre outside [-b,b]^3 or a non-finite coordinate/charge */
+    RS_ERR_SEPARATION = -3,    /* RS_VALIDATE_SEPARATION: two centres closer than min_sep */
+    RS_ERR_OOM = -4,           /* device allocation failed */
+    RS_ERR_CUDA = -5,          /* a CUDA runtime call failed; rs_last_error has the message */
+    RS_ERR_TIMEOUT = -6,       /* a bounded device wait ran out */
+    RS_ERR_NOT_READY = -7,     /* result requested before a successful rs_solve */
+    RS_ERR_CAPACITY = -8       /* N above the context's max_particles, or more than 256 windows
+                                  per round reach one 8x16x64 output tile */
+} rs_status;
+
+typedef enum {
+    RS_FP64 = 0,        /* every stage in FP64 (the plain RS path) */
+    RS_FP32_SPLIT = 1,  /* FP64 eigen stage; FP32 bulk contractions with FP64 chunk accumulation */
+    RS_FP32 = 2         /* as RS_FP32_SPLIT (serving tolerance 1e-4 against the oracle) */
+} rs_precision;
+
+/* Method parameters (Sec. 2.2-2.3, Sec. 6).  All lengths in the units of the coordinates. */
+typedef struct {
+    double b;            /* half-width of the box [-b,b]^3 */
+    int    n;            /* grid points per axis (odd, >= 5) */
+    int    R;            /* rank of the reference canonical tensor P_R (number of sinc nodes) */
+    int    R_s;          /* short-range terms; the long part has R_l = R - R_s */
+    double h_q;          /* sinc step: t_k = exp(u0 + k*h_q), a_k = (2/sqrt(pi)) h_q t_k */
+    double u0;           /* sinc offset */
+    double eps;          /* Tucker tolerance (relative Frobenius error of the long-range part) */
+    int    rank_cap;     /* 0: none; otherwise the maximal Tucker rank per mode */
+    int    max_rank;     /* 0: default 128; upper bound on Tucker ranks (sets workspace size) */
+    double delta_rel;    /* window cut-off delta = delta_rel * P_R(0) (Sec. 2.3, criterion (A)) */
+    int    precision;    /* rs_precision */
+    int    snap;         /* 1: centres are moved to their nearest grid point (Sec. 3.2) */
+    int    max_particles;/* capacity of the context */
+} rs_config;
+
+/* rs_solve flags */
+#define RS_INPUT_HOST          1   /* xyz and Z are host pointers (copied in on the stream) */
+#define RS_POTENTIAL           2   /* write the full-grid potential into potential_out */
+#define RS_ENERGY              4   /* compute the interaction energy (read with rs_energy) */
+#define RS_VALIDATE_SEPARATION 16  /* check that no two centres are closer than min_sep */
+
+typedef struct rs_ctx rs_ctx;
+
+/* Per-solve report (rs_report synchronises). */
+typedef struct {
+    int    N, N_nonzero;
+    int    ranks[3];            /* Tucker ranks r_1, r_2, r_3 */
+    int    subspace[3];         /* width of the subspace the ranks were chosen from */
+    int    gamma;               /* window half-width in grid steps (n_s = 2*gamma + 1) */
+    double tail_rel[3];         /* discarded side-matrix energy / total, per mode */
+    double eps_bound;           /* sqrt(sum_l tail_rel[l]): the error bound used for eps */
+    double P_R0, P_Rl0;         /* P_R and P_{R_l} at the origin (self-interaction terms) */
+    double energy;              /* last energy (if computed) */
+    int    status;              /* status of the last solve (rs_status) */
+    int    kernel_launches;     /* CUDA kernels the last rs_solve enqueued */
+} rs_stats;
+
+/* Pipeline stages timed by rs_profile_read (in this order). */
+#define RS_NSTAGE 9
+/* 0 factors (Sec. 2.2)       1 particles (snap, aggregate)  2 gram (Sec. 3.2 / Sec. 6 (I))
+ * 3 eigen (Sec. 6 (I))       4 core (Sec. 6 (II))           5 bins (window lists)
+ * 6 reconstruct (Eq. (2.3))  7 windows (Defs. 3.4, 3.6)     8 energy (Eq. (4.7)) */
+
+/* Create a context bound to a CUDA stream (cudaStream_t passed as void*; NULL = default
+ * stream).  Allocates all device workspace for cfg (sizes grow with n^2, max_rank^3,
+ * max_particles).  Errors: RS_ERR_INVALID_ARG, RS_ERR_OOM, RS_ERR_CUDA. */
+rs_status rs_create(const rs_config* cfg, void* cuda_stream, rs_ctx** out);
+
+/* Free the context and all its device memory.  Safe on NULL. */
+void rs_destroy(rs_ctx* ctx);
+
+/* Workspace bytes a context for cfg would allocate (no allocation). */
+size_t rs_workspace_bytes(const rs_config* cfg);
+
+/* Run the whole method for N particles (Sec. 3.2-3.3 and Sec. 6):
+ *   xyz (N x 3, row-major, float64) and Z (N, float64): device pointers, or host pointers
+ *   with RS_INPUT_HOST;
+ *   potential_out: with RS_POTENTIAL a device buffer of n^3 elements (double for RS_FP64,
+ *   float otherwise), written in C order; ignored otherwise.
+ * Enqueues the work on the context stream and returns without waiting (inputs must stay
+ * valid until the stream reaches the solve).  Device-side input errors (outside the box,
+ * non-finite values) are reported by rs_report / rs_energy.  min_sep is used only with
+ * RS_VALIDATE_SEPARATION. */
+rs_status rs_solve(rs_ctx* ctx, int N, const double* xyz, const double* Z, int flags,
+                   double min_sep, void* potential_out);
+
+/* Interaction energy of the last solve (Eq. (4.7) applied to the RS-Tucker tensor:
+ * E = 1/2 sum_j z_j (A(x_j) - z_j P_R(0)), A the RS tensor at the particle's grid point).
+ * Synchronises the stream.  RS_ERR_NOT_READY if the last solve did not ask for RS_ENERGY. */
+rs_status rs_energy(rs_ctx* ctx, double* E);
+
+/* Synchronise and fill *st for the last solve; returns that solve's status. */
+rs_status rs_report(rs_ctx* ctx, rs_stats* st);
+
+/* Device pointers to the RS-Tucker long-range part of the last solve (valid until the next
+ * rs_solve or rs_destroy; synchronises to read the ranks):
+ *   V[l]: n x ld_V column block, row-major (V[l][i*ld_V + a], a < ranks[l]), orthonormal columns;
+ *   beta: core, beta[(a*ld_b + b)*ld_b + c];  dtype double for RS_FP64, float otherwise. */
+rs_status rs_get_tucker(rs_ctx* ctx, int ranks[3], int* ld_V, int* ld_b,
+                        const void* V[3], const void** beta);
+
+/* Evaluate the RS-Tucker tensor of the last solve at M grid multi-indices (Lemma 3.10):
+ * idx: device int32 array (M x 3), out: device double array (M).  Asynchronous. */
+rs_status rs_eval_points(rs_ctx* ctx, int M, const int* idx, double* out);
+
+/* Stage timing (tracing): with enable != 0, each rs_solve records one CUDA event per stage
+ * boundary on the context stream (ring of 512 solves).  Errors: RS_ERR_CUDA. */
+rs_status rs_profile_enable(rs_ctx* ctx, int enable);
+
+/* Synchronise and return, per stage, the device time in milliseconds summed over the solves
+ * recorded since the last read (ms: RS_NSTAGE doubles), and how many solves that was
+ * (*nsolves); then restart the accumulation.  RS_ERR_NOT_READY if profiling is off. */
+rs_status rs_profile_read(rs_ctx* ctx, double* ms, int* nsolves);
+
+/* Inspection hook for tests: device pointer and size in bytes of an internal buffer of the
+ * last solve ("pk64" factors R x (2n-1), "F", "G" Gram matrices 3 x n x n, "C" aggregated
+ * weights 3 x n, "Q" subspace 3 x n x ksub, "T" Rayleigh quotients 3 x ksub x ksub, "Z64"
+ * Tucker bases, "beta64", "Qp", "T1", "T2").  Synchronises.  RS_ERR_INVALID_ARG for an
+ * unknown name.  The buffers stay owned by the context. */
+rs_status rs_debug_buffer(rs_ctx* ctx, const char* name, void** ptr, size_t* bytes);
+
+/* Static name of a stage (NULL outside [0, RS_NSTAGE)). */
+const char* rs_stage_name(int stage);
+
+/* Text of the last error of this context (or of rs_create when ctx is NULL). */
+const char* rs_last_error(rs_ctx* ctx);
+
+/* Library version string. */
+const char* rs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RS_H */

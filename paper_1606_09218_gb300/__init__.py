@@ -1,0 +1,194 @@
+"""GB300-native range-separated (RS) canonical/Tucker tensor method for the N-particle
+Newton potential (Benner, Khoromskaia, Khoromskij, arXiv:1606.09218).
+
+The computation runs in ``librs_gb300.so`` (hand-written CUDA for sm_103a behind the C ABI of
+``include/rs.h``).  This module only marshals arguments: PyTorch supplies device memory
+and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _lib
+from ._lib import (RS_ENERGY, RS_FP32, RS_FP32_SPLIT, RS_FP64, RS_INPUT_HOST,  # noqa: F401
+                   RS_POTENTIAL, RS_VALIDATE_SEPARATION, RSError)
+
+PRECISIONS = {"fp64": RS_FP64, "fp32_split": RS_FP32_SPLIT, "fp32": RS_FP32}
+
+
+def config_from_workload(cfg: dict, n: int | None = None, max_particles: int | None = None,
+                         max_rank: int = 0) -> _lib.RSConfigC:
+    """Build the C config from a workload parameter dictionary."""
+    c = _lib.RSConfigC()
+    nn = int(n if n is not None else cfg["n"])
+    if "quad_by_n" in cfg:
+        q = cfg["quad_by_n"][str(nn)]
+        hq, u0 = q["h_q"], q["u0"]
+    else:
+        hq, u0 = cfg["h_q"], cfg["u0"]
+    c.b = float(cfg["b"])
+    c.n = nn
+    c.R = int(cfg["R"])
+    c.R_s = int(cfg["R_s"])
+    c.h_q = float(hq)
+    c.u0 = float(u0)
+    c.eps = float(cfg["eps"])
+    c.rank_cap = int(cfg.get("rank_cap", 0))
+    c.max_rank = int(max_rank or cfg.get("max_rank", 0))
+    c.delta_rel = float(cfg["delta_rel"])
+    c.precision = PRECISIONS[cfg.get("precision", "fp32_split")]
+    c.snap = 1 if cfg.get("snap", True) else 0
+    if max_particles is None:
+        max_particles = int(cfg.get("particles", {}).get("N", 0)) or 1
+        if cfg.get("particles", {}).get("kind") == "nacl_lattice":
+            max_particles = int(cfg["particles"]["side"]) ** 3
+    c.max_particles = int(max_particles)
+    return c
+
+
+class _DevArray:
+    """Exposes a library-owned device buffer through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape, typestr: str, strides=None):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 3, "strides": strides}
+
+
+class RSContext:
+    """One device context of the library (workspace sized for ``cfg``)."""
+
+    def __init__(self, cfg: _lib.RSConfigC, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = _lib.load()
+        self.cfg = cfg
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        st = self.lib.rs_create(C.byref(cfg), C.c_void_p(stream.cuda_stream), C.byref(h))
+        _lib.check(st, None)
+        self.h = h
+        self.n = cfg.n
+        self.fp64 = cfg.precision == RS_FP64
+        self.dtype = torch.float64 if self.fp64 else torch.float32
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_potential(self):
+        n = self.n
+        return self._torch.empty((n, n, n), dtype=self.dtype, device="cuda")
+
+    def solve(self, xyz, Z, potential=None, energy: bool = True, want_potential: bool = True,
+              min_sep: float = 0.0) -> int:
+        """Enqueue one solve.  ``xyz`` (N,3) and ``Z`` (N,) float64: CUDA tensors, or host
+        (CPU tensors / numpy) which the library copies in.  Returns the launch status."""
+        torch = self._torch
+        flags = 0
+        if isinstance(xyz, torch.Tensor) and xyz.is_cuda:
+            assert xyz.dtype == torch.float64 and Z.dtype == torch.float64
+            xyz = xyz.contiguous()
+            Z = Z.contiguous()
+            pxyz, pZ = xyz.data_ptr(), Z.data_ptr()
+            N = int(Z.numel())
+            self._keep = (xyz, Z)
+        else:
+            import numpy as np
+            xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64))
+            Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64))
+            pxyz, pZ = xyz.ctypes.data, Z.ctypes.data
+            N = int(Z.size)
+            flags |= RS_INPUT_HOST
+            self._keep = (xyz, Z)
+        out = 0
+        if want_potential:
+            if potential is None:
+                potential = self.new_potential()
+            assert potential.dtype == self.dtype and potential.is_cuda and potential.numel() == self.n ** 3
+            out = potential.data_ptr()
+            flags |= RS_POTENTIAL
+        if energy:
+            flags |= RS_ENERGY
+        if min_sep > 0:
+            flags |= RS_VALIDATE_SEPARATION
+        st = self.lib.rs_solve(self.h, N, C.c_void_p(pxyz), C.c_void_p(pZ), flags, float(min_sep),
+                               C.c_void_p(out))
+        _lib.check(st, self.h)
+        self.potential = potential
+        return st
+
+    def energy(self) -> float:
+        E = C.c_double()
+        _lib.check(self.lib.rs_energy(self.h, C.byref(E)), self.h)
+        return float(E.value)
+
+    def report(self) -> dict:
+        s = _lib.RSStatsC()
+        st = self.lib.rs_report(self.h, C.byref(s))
+        _lib.check(st, self.h)
+        return dict(N=s.N, N_nonzero=s.N_nonzero, ranks=list(s.ranks), subspace=list(s.subspace),
+                    gamma=s.gamma, tail_rel=list(s.tail_rel), eps_bound=s.eps_bound, P_R0=s.P_R0,
+                    P_Rl0=s.P_Rl0, energy=s.energy, status=s.status, kernel_launches=s.kernel_launches)
+
+    def profile(self, enable: bool = True):
+        """Turn per-stage CUDA-event timing on or off."""
+        _lib.check(self.lib.rs_profile_enable(self.h, 1 if enable else 0), self.h)
+
+    def profile_read(self) -> tuple[dict, int]:
+        """Per-stage device milliseconds summed over the solves since the last read."""
+        ms = (C.c_double * _lib.RS_NSTAGE)()
+        cnt = C.c_int()
+        _lib.check(self.lib.rs_profile_read(self.h, ms, C.byref(cnt)), self.h)
+        names = [self.lib.rs_stage_name(i).decode() for i in range(_lib.RS_NSTAGE)]
+        return {nm: ms[i] for i, nm in enumerate(names)}, cnt.value
+
+    def tucker(self):
+        """(ranks, [V1, V2, V3], beta) as torch views of the library's buffers (valid until
+        the next solve); V_l is n x r_l, beta is r1 x r2 x r3."""
+        torch = self._torch
+        ranks = (C.c_int * 3)()
+        ldV, ldb = C.c_int(), C.c_int()
+        V = (C.c_void_p * 3)()
+        beta = C.c_void_p()
+        _lib.check(self.lib.rs_get_tucker(self.h, ranks, C.byref(ldV), C.byref(ldb), V, C.byref(beta)),
+                   self.h)
+        ts = "<f8" if self.fp64 else "<f4"
+        es = 8 if self.fp64 else 4
+        n = self.n
+        Vs = []
+        for l in range(3):
+            full = torch.as_tensor(_DevArray(V[l], (n, ldV.value), ts), device="cuda")
+            Vs.append(full[:, : ranks[l]])
+        bfull = torch.as_tensor(_DevArray(beta.value, (ldb.value,) * 3, ts), device="cuda")
+        del es
+        return list(ranks), Vs, bfull[: ranks[0], : ranks[1], : ranks[2]]
+
+    def debug_buffer(self, name: str, dtype=None):
+        """A torch (uint8 or ``dtype``) view of an internal device buffer (inspection hook)."""
+        torch = self._torch
+        ptr, nb = C.c_void_p(), C.c_size_t()
+        _lib.check(self.lib.rs_debug_buffer(self.h, name.encode(), C.byref(ptr), C.byref(nb)), self.h)
+        raw = torch.as_tensor(_DevArray(ptr.value, (nb.value,), "|u1"), device="cuda")
+        return raw if dtype is None else raw.view(dtype)
+
+    def eval_points(self, idx):
+        """RS-Tucker entries (Lemma 3.10) at grid multi-indices idx (M,3) int32 CUDA tensor."""
+        torch = self._torch
+        idx = idx.to(device="cuda", dtype=torch.int32).contiguous()
+        out = torch.empty(idx.shape[0], dtype=torch.float64, device="cuda")
+        _lib.check(self.lib.rs_eval_points(self.h, int(idx.shape[0]), C.c_void_p(idx.data_ptr()),
+                                           C.c_void_p(out.data_ptr())), self.h)
+        return out
+
+
+def version() -> str:
+    return _lib.load().rs_version().decode()

@@ -1,0 +1,434 @@
+// C ABI of the RS library: context lifetime, workspace, and the per-solve pipeline
+// (Sec. 2.2 factors -> Sec. 3.2 long-range Gram -> Sec. 6 RHOSVD -> Def. 3.9 RS-Tucker
+// reconstruction with the windows of Def. 3.4 -> Sec. 4.2 energy).
+#include "rs_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace rs;
+
+struct rs_ctx {
+  Ctx c;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+struct Sizes {
+  int n, R, R_l, L, ks, rmax, nbin, maxN;
+  bool fp64;
+  size_t tsz;
+  std::vector<std::pair<void**, size_t>> list;
+};
+
+bool derive(const rs_config& cfg, Ctx& c, std::string& err) {
+  if (!(cfg.b > 0.0) || !std::isfinite(cfg.b)) { err = "b must be positive"; return false; }
+  if (cfg.n < 5 || (cfg.n % 2) == 0) { err = "n must be odd and >= 5"; return false; }
+  if (cfg.n > 4097) { err = "n above 4097 is not supported"; return false; }
+  if (cfg.R < 2 || cfg.R > 64) { err = "R must be in [2, 64]"; return false; }
+  if (cfg.R_s < 0 || cfg.R_s >= cfg.R || cfg.R_s > 16) { err = "need 0 <= R_s < R and R_s <= 16"; return false; }
+  if (!(cfg.h_q > 0.0) || !std::isfinite(cfg.u0)) { err = "h_q must be positive and u0 finite"; return false; }
+  if (!(cfg.eps > 0.0) || cfg.eps >= 1.0) { err = "eps must be in (0, 1)"; return false; }
+  if (cfg.rank_cap < 0 || cfg.max_rank < 0) { err = "rank_cap and max_rank must be >= 0"; return false; }
+  if (!(cfg.delta_rel >= 0.0)) { err = "delta_rel must be >= 0"; return false; }
+  if (cfg.precision < RS_FP64 || cfg.precision > RS_FP32) { err = "unknown precision"; return false; }
+  if (cfg.snap != 1) { err = "only snapped centres (snap = 1) are supported by this build"; return false; }
+  if (cfg.max_particles < 1) { err = "max_particles must be >= 1"; return false; }
+  c.cfg = cfg;
+  c.n = cfg.n;
+  c.R = cfg.R;
+  c.R_s = cfg.R_s;
+  c.R_l = cfg.R - cfg.R_s;
+  c.L = 2 * cfg.n - 1;
+  c.h = 2.0 * cfg.b / (cfg.n - 1);
+  c.fp64 = (cfg.precision == RS_FP64);
+  int want = cfg.max_rank > 0 ? cfg.max_rank : 128;
+  if (want > RMAX_LIMIT) want = RMAX_LIMIT;
+  int ks = ((want + 16 + KB - 1) / KB) * KB;
+  if (ks > KSUB_MAX) ks = KSUB_MAX;
+  int nfloor = (cfg.n / KB) * KB;
+  if (ks > nfloor) ks = nfloor;
+  c.ksub = ks;
+  c.rmax = want < ks ? want : ks;
+  c.nbin = (cfg.n + BIN - 1) / BIN;
+  c.maxN = cfg.max_particles;
+  return true;
+}
+
+template <typename P>
+void add(std::vector<std::pair<void**, size_t>>& v, P*& p, size_t bytes) {
+  v.push_back({(void**)&p, bytes});
+}
+
+std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
+  std::vector<std::pair<void**, size_t>> v;
+  const size_t n = c.n, L = c.L, ks = c.ksub, rm = c.rmax, N = c.maxN, R = c.R, Rl = c.R_l;
+  const size_t ts = c.fp64 ? 8 : 4;
+  const size_t nbins = (size_t)c.nbin * c.nbin * c.nbin;
+  add(v, c.pk64, 8 * R * L);
+  add(v, c.pk32, 4 * R * L);
+  add(v, c.xyz, 8 * 3 * N);
+  add(v, c.Z, 8 * N);
+  add(v, c.j, 4 * 3 * N);
+  add(v, c.nz_idx, 4 * N);
+  add(v, c.C, 8 * 3 * n);
+  add(v, c.nzj, 4 * 3 * n);
+  add(v, c.F, 8 * L * L);
+  add(v, c.G, 8 * 3 * n * n);
+  add(v, c.X, 8 * 3 * n * ks);
+  add(v, c.Q, 8 * 3 * n * ks);
+  add(v, c.Y, 8 * 3 * n * ks);
+  add(v, c.T, 8 * 3 * ks * ks);
+  add(v, c.T2k, 8 * 3 * ks * ks);
+  add(v, c.W, 8 * 3 * ks * ks);
+  add(v, c.part, 8 * 2 * 3 * NBC * (ks * KB + KB * KB));
+  add(v, c.order, 4 * 3 * ks);
+  add(v, c.ev, 8 * 3 * ks);
+  add(v, c.Z64, 8 * 3 * n * rm);
+  add(v, c.Z32, 4 * 3 * n * rm);
+  add(v, c.Qp, ts * 3 * n * Rl * rm);
+  add(v, c.beta64, 8 * rm * rm * rm);
+  add(v, c.beta, ts * rm * rm * rm);
+  add(v, c.T1, ts * rm * rm * n);
+  add(v, c.T2, ts * rm * n * n);
+  add(v, c.bin_count, 4 * (nbins + 1));
+  add(v, c.bin_start, 4 * (nbins + 1));
+  add(v, c.bin_items, 4 * N);
+  add(v, c.Epart, 8 * ((N + 7) / 8 + 1));
+  add(v, c.adims, 4 * rm);
+  add(v, c.kdims, 4 * rm);
+  add(v, c.sc, sizeof(DevScalars));
+  return v;
+}
+
+void free_profile(Ctx& c) {
+  if (c.prof_ev) {
+    for (int i = 0; i < PROF_RING * (NSTAGE + 1); ++i) cudaEventDestroy(c.prof_ev[i]);
+    delete[] c.prof_ev;
+    c.prof_ev = nullptr;
+  }
+  c.profile = false;
+  c.prof_count = 0;
+}
+
+void free_all(Ctx& c) {
+  free_profile(c);
+  auto v = buffer_list(c);
+  for (auto& e : v) {
+    if (*e.first) cudaFree(*e.first);
+    *e.first = nullptr;
+  }
+  if (c.h_sc) cudaFreeHost(c.h_sc);
+  c.h_sc = nullptr;
+}
+
+rs_status fail(Ctx& c, rs_status s, const std::string& msg) {
+  c.err = msg;
+  return s;
+}
+
+rs_status check_launch(Ctx& c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    c.err = std::string(where) + ": " + cudaGetErrorString(e);
+    return RS_ERR_CUDA;
+  }
+  return RS_OK;
+}
+
+rs_status sync_scalars(Ctx& c) {
+  cudaError_t e = cudaMemcpyAsync(c.h_sc, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    c.err = std::string("synchronise: ") + cudaGetErrorString(e);
+    return RS_ERR_CUDA;
+  }
+  return RS_OK;
+}
+
+rs_status status_of(const DevScalars& s) {
+  if (s.flags & FLAG_TIMEOUT) return RS_ERR_TIMEOUT;
+  if (s.flags & FLAG_OUTSIDE) return RS_ERR_OUTSIDE_BOX;
+  if (s.flags & FLAG_WINDOWS) return RS_ERR_CAPACITY;
+  if (s.flags & FLAG_SEPARATION) return RS_ERR_SEPARATION;
+  if (s.flags & (FLAG_RANK_CAPPED | FLAG_CHOL)) return RS_RANK_CAPPED;
+  return RS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rs_version(void) { return "rs-gb300 0.1 (sm_103a)"; }
+
+size_t rs_workspace_bytes(const rs_config* cfg) {
+  if (!cfg) return 0;
+  Ctx c;
+  std::string err;
+  if (!derive(*cfg, c, err)) return 0;
+  size_t tot = 0;
+  for (auto& e : buffer_list(c)) tot += (e.second + 255) / 256 * 256;
+  return tot;
+}
+
+rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
+  if (!cfg || !out) { g_create_err = "null argument"; return RS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  rs_ctx* h = new (std::nothrow) rs_ctx();
+  if (!h) { g_create_err = "host allocation failed"; return RS_ERR_OOM; }
+  Ctx& c = h->c;
+  std::string err;
+  if (!derive(*cfg, c, err)) {
+    g_create_err = err;
+    delete h;
+    return RS_ERR_INVALID_ARG;
+  }
+  c.stream = (cudaStream_t)stream;
+  // RS_DEBUG_POISON=1 fills every workspace buffer with 0xFF bytes (NaN / -1) so that a
+  // read of memory the current solve did not write shows up in the results.
+  const char* poison = std::getenv("RS_DEBUG_POISON");
+  const bool do_poison = poison && poison[0] == '1';
+  for (auto& e : buffer_list(c)) {
+    cudaError_t st = cudaMalloc(e.first, e.second > 0 ? e.second : 1);
+    if (st != cudaSuccess) {
+      cudaGetLastError();
+      g_create_err = std::string("device allocation failed: ") + cudaGetErrorString(st);
+      free_all(c);
+      delete h;
+      return st == cudaErrorMemoryAllocation ? RS_ERR_OOM : RS_ERR_CUDA;
+    }
+    if (do_poison) cudaMemset(*e.first, 0xFF, e.second);
+  }
+  if (cudaMallocHost((void**)&c.h_sc, sizeof(DevScalars)) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = "pinned host allocation failed";
+    free_all(c);
+    delete h;
+    return RS_ERR_OOM;
+  }
+  std::memset(c.h_sc, 0, sizeof(DevScalars));
+  cudaMemsetAsync(c.sc, 0, sizeof(DevScalars), c.stream);
+  *out = h;
+  return RS_OK;
+}
+
+void rs_destroy(rs_ctx* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->c.stream);
+  free_all(h->c);
+  delete h;
+}
+
+rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int flags,
+                   double min_sep, void* potential_out) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  c.solved = false;
+  if (N < 0) return fail(c, RS_ERR_INVALID_ARG, "N must be >= 0");
+  if (N > c.maxN) return fail(c, RS_ERR_CAPACITY, "N above max_particles of this context");
+  if (N > 0 && (!xyz || !Z)) return fail(c, RS_ERR_INVALID_ARG, "null particle arrays");
+  if ((flags & RS_POTENTIAL) && !potential_out)
+    return fail(c, RS_ERR_INVALID_ARG, "RS_POTENTIAL needs potential_out");
+  if ((flags & RS_VALIDATE_SEPARATION) && !(min_sep > 0.0))
+    return fail(c, RS_ERR_INVALID_ARG, "RS_VALIDATE_SEPARATION needs min_sep > 0");
+  if (flags & RS_INPUT_HOST) {
+    // cheap host-side check before any device work
+    for (long long i = 0; i < 3ll * N; ++i)
+      if (!std::isfinite(xyz[i]) || std::fabs(xyz[i]) > c.cfg.b * (1.0 + 1e-12))
+        return fail(c, RS_ERR_OUTSIDE_BOX, "particle outside [-b,b]^3 or non-finite coordinate");
+    for (int i = 0; i < N; ++i)
+      if (!std::isfinite(Z[i])) return fail(c, RS_ERR_OUTSIDE_BOX, "non-finite charge");
+  }
+  cudaStream_t s = c.stream;
+  cudaEvent_t* ev = nullptr;
+  if (c.profile) ev = c.prof_ev + (size_t)(c.prof_count % PROF_RING) * (NSTAGE + 1);
+  auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
+  int k = 0;
+  cudaMemsetAsync(c.sc, 0, sizeof(DevScalars), s);
+  if (N > 0) {
+    cudaMemcpyKind kind = (flags & RS_INPUT_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaMemcpyAsync(c.xyz, xyz, sizeof(double) * 3 * N, kind, s);
+    cudaMemcpyAsync(c.Z, Z, sizeof(double) * N, kind, s);
+  }
+  mark(0);
+  k += launch_factors(c);                  // a1, a2: quadrature, factors, split, window width
+  mark(1);
+  k += launch_prepare_particles(c, N, min_sep, (flags & RS_VALIDATE_SEPARATION) != 0);
+  mark(2);
+  k += launch_gram(c);                     // a3, a4: Gram matrices of the long-range side matrices
+  mark(3);
+  k += launch_subspace(c);                 // a4: dominant subspaces, ranks
+  mark(4);
+  k += launch_projection_core(c);          // a5: projection and core
+  mark(5);
+  k += launch_bins(c);                     // window lists
+  mark(6);
+  rs_status st = check_launch(c, "solve");
+  if (st != RS_OK) return st;
+  if (flags & RS_POTENTIAL) k += launch_recon_gemm(c, potential_out);   // a7
+  mark(7);
+  if (flags & RS_POTENTIAL) k += launch_windows(c, potential_out);      // a6
+  mark(8);
+  if (flags & RS_ENERGY) k += launch_energy(c, N);                      // a8
+  mark(9);
+  st = check_launch(c, "solve");
+  if (st != RS_OK) return st;
+  if (ev) ++c.prof_count;
+  c.launches = k;
+  c.last_flags = flags;
+  c.last_N = N;
+  c.solved = true;
+  return RS_OK;
+}
+
+rs_status rs_energy(rs_ctx* h, double* E) {
+  if (!h || !E) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.solved || !(c.last_flags & RS_ENERGY)) return fail(c, RS_ERR_NOT_READY, "no energy computed");
+  rs_status st = sync_scalars(c);
+  if (st != RS_OK) return st;
+  *E = c.h_sc->energy;
+  rs_status s2 = status_of(*c.h_sc);
+  return s2 < 0 ? s2 : RS_OK;
+}
+
+rs_status rs_report(rs_ctx* h, rs_stats* out) {
+  if (!h || !out) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.solved) return fail(c, RS_ERR_NOT_READY, "no solve");
+  rs_status st = sync_scalars(c);
+  if (st != RS_OK) return st;
+  const DevScalars& s = *c.h_sc;
+  std::memset(out, 0, sizeof(*out));
+  out->N = c.last_N;
+  out->N_nonzero = s.n_nz;
+  double eb = 0.0;
+  for (int l = 0; l < 3; ++l) {
+    out->ranks[l] = s.rank[l];
+    out->subspace[l] = s.k_eff[l];
+    out->tail_rel[l] = s.tail_rel[l];
+    eb += s.tail_rel[l];
+  }
+  out->eps_bound = std::sqrt(eb);
+  out->gamma = s.gamma;
+  out->P_R0 = s.P_R0;
+  out->P_Rl0 = s.P_Rl0;
+  out->energy = s.energy;
+  out->status = status_of(s);
+  out->kernel_launches = c.launches;
+  return (rs_status)out->status;
+}
+
+rs_status rs_get_tucker(rs_ctx* h, int ranks[3], int* ld_V, int* ld_b, const void* V[3],
+                        const void** beta) {
+  if (!h || !ranks || !ld_V || !ld_b || !V || !beta) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.solved) return fail(c, RS_ERR_NOT_READY, "no solve");
+  rs_status st = sync_scalars(c);
+  if (st != RS_OK) return st;
+  for (int l = 0; l < 3; ++l) {
+    ranks[l] = c.h_sc->rank[l];
+    V[l] = c.fp64 ? (const void*)(c.Z64 + (size_t)l * c.n * c.rmax)
+                  : (const void*)(c.Z32 + (size_t)l * c.n * c.rmax);
+  }
+  *ld_V = c.rmax;
+  *ld_b = c.rmax;
+  *beta = c.beta;
+  return RS_OK;
+}
+
+rs_status rs_eval_points(rs_ctx* h, int M, const int* idx, double* out) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.solved) return fail(c, RS_ERR_NOT_READY, "no solve");
+  if (M < 0 || (M > 0 && (!idx || !out))) return fail(c, RS_ERR_INVALID_ARG, "bad point list");
+  launch_eval_points(c, M, idx, out);
+  return check_launch(c, "eval_points");
+}
+
+rs_status rs_profile_enable(rs_ctx* h, int enable) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!enable) {
+    cudaStreamSynchronize(c.stream);
+    free_profile(c);
+    return RS_OK;
+  }
+  if (c.profile) return RS_OK;
+  c.prof_ev = new (std::nothrow) cudaEvent_t[PROF_RING * (NSTAGE + 1)];
+  if (!c.prof_ev) return fail(c, RS_ERR_OOM, "profile events");
+  for (int i = 0; i < PROF_RING * (NSTAGE + 1); ++i) {
+    if (cudaEventCreate(&c.prof_ev[i]) != cudaSuccess) {
+      cudaGetLastError();
+      for (int q = 0; q < i; ++q) cudaEventDestroy(c.prof_ev[q]);
+      delete[] c.prof_ev;
+      c.prof_ev = nullptr;
+      return fail(c, RS_ERR_CUDA, "cudaEventCreate failed");
+    }
+  }
+  c.profile = true;
+  c.prof_count = 0;
+  return RS_OK;
+}
+
+rs_status rs_profile_read(rs_ctx* h, double* ms, int* nsolves) {
+  if (!h || !ms || !nsolves) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.profile) return fail(c, RS_ERR_NOT_READY, "profiling is off");
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess) {
+    c.err = std::string("synchronise: ") + cudaGetErrorString(cudaGetLastError());
+    return RS_ERR_CUDA;
+  }
+  for (int q = 0; q < NSTAGE; ++q) ms[q] = 0.0;
+  long long cnt = c.prof_count < PROF_RING ? c.prof_count : PROF_RING;
+  for (long long sidx = 0; sidx < cnt; ++sidx) {
+    cudaEvent_t* ev = c.prof_ev + (size_t)sidx * (NSTAGE + 1);
+    for (int q = 0; q < NSTAGE; ++q) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[q], ev[q + 1]) == cudaSuccess) ms[q] += t;
+      else cudaGetLastError();
+    }
+  }
+  *nsolves = (int)cnt;
+  c.prof_count = 0;
+  return RS_OK;
+}
+
+rs_status rs_debug_buffer(rs_ctx* h, const char* name, void** ptr, size_t* bytes) {
+  if (!h || !name || !ptr || !bytes) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  cudaStreamSynchronize(c.stream);
+  struct { const char* nm; void* p; } tab[] = {
+      {"pk64", c.pk64}, {"F", c.F}, {"G", c.G}, {"C", c.C}, {"Q", c.Q}, {"X", c.X}, {"T", c.T},
+      {"Z64", c.Z64}, {"beta64", c.beta64}, {"Qp", c.Qp}, {"T1", c.T1}, {"T2", c.T2}};
+  for (auto& e : buffer_list(c)) {
+    for (auto& t : tab) {
+      if (std::strcmp(t.nm, name) == 0 && *e.first == t.p) {
+        *ptr = t.p;
+        *bytes = e.second;
+        return RS_OK;
+      }
+    }
+  }
+  return fail(c, RS_ERR_INVALID_ARG, std::string("unknown buffer ") + name);
+}
+
+const char* rs_stage_name(int stage) {
+  static const char* names[NSTAGE] = {"factors", "particles", "gram", "eigen", "core",
+                                      "bins", "reconstruct", "windows", "energy"};
+  return (stage >= 0 && stage < NSTAGE) ? names[stage] : nullptr;
+}
+
+const char* rs_last_error(rs_ctx* h) {
+  if (!h) return g_create_err.c_str();
+  return h->c.err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,766 @@
+// Eigen stage of the RHOSVD (Sec. 6, step (I)): dominant left singular subspace of each
+// long-range side matrix U^(l), computed from its Gram matrix G_l = U^(l) U^(l)^T.
+//
+//   X = G * Omega                      FP64, Omega a seeded Gaussian block (range finder)
+//   Q = orth(X)                        FP64 block Gram-Schmidt (8 columns, two passes, Cholesky
+//                                      QR inside blocks); stops where a block falls to rounding
+//   T = Q^T G Q                        FP64 Rayleigh quotient
+//   T -> W^T T W  (twice)              FP32 two-sided Jacobi on the graded T, rotations applied
+//                                      and re-orthonormalised (Newton-Schulz) in FP64
+//   ranks from diag(T) and trace(G)    tail(r) = trace(G) - trace(T) + sum_{i>=r} lambda_i
+//
+// FP64 keeps the small eigenvalues (down to eps^2 * trace) that the truncation needs; the
+// FP32 Jacobi is accurate in the relative sense because T is graded after the FP64 steps.
+#include "rs_internal.cuh"
+
+#include <cstdio>
+#include <cstdlib>
+
+namespace rs {
+
+// ------------------------------------------------------------------ generic GEMM
+template <typename T>
+__global__ void __launch_bounds__(256)
+gemm_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __restrict__ A, int lda,
+            long long sA, const T* __restrict__ B, int ldb, long long sB, T beta, T* C, int ldc,
+            long long sC, int splitK, const int* dynM, const int* dynN, const int* dynK) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int bz = blockIdx.z / splitK, kz = blockIdx.z % splitK;
+  int m = M, nn = N, kk = K;
+  if (dynM) m = min(m, dynM[bz]);
+  if (dynN) nn = min(nn, dynN[bz]);
+  if (dynK) kk = min(kk, dynK[bz]);
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  if (row0 >= m || col0 >= nn) return;
+  const int chunk = ((kk + splitK - 1) / splitK + BK - 1) / BK * BK;
+  const int kbeg = kz * chunk, kend = min(kk, kbeg + chunk);
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = T(0);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int idx = tid + e * 256;
+      int r, k;
+      if (!tA) { r = idx / BK; k = idx % BK; } else { k = idx / BM; r = idx % BM; }
+      int gr = row0 + r, gk = k0 + k;
+      T v = T(0);
+      if (gr < m && gk < kend) v = tA ? A[(long long)gk * lda + gr] : A[(long long)gr * lda + gk];
+      As[k][r] = v;
+      int c;
+      if (!tB) { k = idx / BN; c = idx % BN; } else { c = idx / BK; k = idx % BK; }
+      int gc = col0 + c;
+      gk = k0 + k;
+      T w = T(0);
+      if (gc < nn && gk < kend) w = tB ? B[(long long)gc * ldb + gk] : B[(long long)gk * ldb + gc];
+      Bs[k][c] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      T a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) bb[jj] = Bs[k][tx + 16 * jj];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], bb[jj], acc[i][jj]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gr = row0 + ty + 16 * i;
+    if (gr >= m) continue;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      int gc = col0 + tx + 16 * jj;
+      if (gc >= nn) continue;
+      T* p = C + (long long)gr * ldc + gc;
+      if (splitK > 1) {
+        atomicAdd(p, alpha * acc[i][jj]);
+      } else {
+        T v = alpha * acc[i][jj];
+        if (beta != T(0)) v += beta * *p;
+        *p = v;
+      }
+    }
+  }
+}
+
+template <typename T>
+void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha,
+                  const T* A, int lda, long long sA, const T* B, int ldb, long long sB, T beta,
+                  T* C, int ldc, long long sC, int batch, int splitK, const int* dynM,
+                  const int* dynN, const int* dynK) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (splitK < 1) splitK = 1;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch * splitK);
+  gemm_kernel<T><<<grid, 256, 0, s>>>(transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB,
+                                      beta, C, ldc, sC, splitK, dynM, dynN, dynK);
+}
+
+template void gemm_batched<double>(cudaStream_t, bool, bool, int, int, int, double, const double*,
+                                   int, long long, const double*, int, long long, double, double*,
+                                   int, long long, int, int, const int*, const int*, const int*);
+template void gemm_batched<float>(cudaStream_t, bool, bool, int, int, int, float, const float*,
+                                  int, long long, const float*, int, long long, float, float*,
+                                  int, long long, int, int, const int*, const int*, const int*);
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// Seeded standard normal block Omega (Box-Muller on a counter hash).
+__global__ void omega_kernel(double* Om, int n, int ks, int total) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  uint64_t h1 = splitmix64(0x1606092180000000ull + 2ull * (uint64_t)t);
+  uint64_t h2 = splitmix64(0x1606092180000001ull + 2ull * (uint64_t)t);
+  double u1 = ((h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  double u2 = ((h2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  Om[t] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x + 31) / 32) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// trace(G_l) and ||X_l||_F^2 per mode (one CTA per mode).
+__global__ void traces_kernel(const double* G, const double* X, int n, int ks, DevScalars* sc) {
+  __shared__ double red[32];
+  int l = blockIdx.x;
+  const double* g = G + (long long)l * n * n;
+  const double* x = X + (long long)l * n * ks;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += g[(long long)i * n + i];
+  for (long long i = threadIdx.x; i < (long long)n * ks; i += blockDim.x) b += x[i] * x[i];
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  if (threadIdx.x == 0) {
+    sc->trG[l] = a;
+    sc->xnorm2[l] = b;
+  }
+}
+
+// ------------------------------------------------------------------ block Gram-Schmidt
+// Cooperative kernel: gridDim.x = 3 * NBC CTAs, CTA c of mode l owns rows
+// [c*rows, (c+1)*rows).  Every CTA executes the same sequence of grid barriers.
+
+// Grid-wide barrier with a bounded wait (spins on a volatile load).  The kernel is launched cooperatively, so every CTA
+// is resident and the wait normally ends after a few microseconds; if it does not end within
+// ~1 s the CTA sets FLAG_TIMEOUT, stops waiting at this and every later barrier, and the host
+// reports RS_ERR_TIMEOUT.
+__device__ __forceinline__ void grid_barrier(DevScalars* sc, unsigned& gen, bool& poisoned) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    __threadfence();
+    unsigned arrived = atomicAdd(&sc->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&sc->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&sc->bar_gen, 1u);
+    } else if (!poisoned) {
+      volatile unsigned* g = &sc->bar_gen;
+      long long it = 0;
+      while (*g == gen) {
+        if (++it > 20000000ll) {   // about a second of polling
+          atomicOr(&sc->flags, (unsigned)FLAG_TIMEOUT);
+          poisoned = true;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  ++gen;
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool chol8(double* S, double piv_tol = 0.0) {
+  // in-place lower Cholesky of an 8x8 (row-major); returns false if a pivot is not above
+  // piv_tol times its diagonal entry (not positive definite, or too ill-conditioned for
+  // Cholesky QR)
+  for (int jc = 0; jc < KB; ++jc) {
+    double d = S[jc * KB + jc];
+    const double djj = d;
+    for (int k = 0; k < jc; ++k) d -= S[jc * KB + k] * S[jc * KB + k];
+    if (!(d > piv_tol * djj) || !(d > 0.0)) return false;
+    d = sqrt(d);
+    S[jc * KB + jc] = d;
+    for (int i = jc + 1; i < KB; ++i) {
+      double v = S[i * KB + jc];
+      for (int k = 0; k < jc; ++k) v -= S[i * KB + k] * S[jc * KB + k];
+      S[i * KB + jc] = v / d;
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(256)
+bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int ks,
+             DevScalars* sc) {
+  unsigned bar_gen = 0;
+  bool poisoned = false;   // meaningful in thread 0 only
+  const int l = blockIdx.x / NBC, c = blockIdx.x % NBC;
+  const int rows = (n + NBC - 1) / NBC;
+  const int r0 = min(n, c * rows), r1 = min(n, r0 + rows);
+  const double* Xl = X + (long long)l * n * ks;
+  double* Ql = Q + (long long)l * n * ks;
+  // part layout: [2][3][NBC][ks*KB + KB*KB].  Partials written by other SMs are read with
+  // __ldcg (L2, bypassing the non-coherent L1) after the grid barrier.
+  const long long pstride = (long long)ks * KB + KB * KB;
+  auto pbuf = [&](int phase, int mode, int cta) {
+    return part + (((long long)(phase & 1) * 3 + mode) * NBC + cta) * pstride;
+  };
+  __shared__ double h[KSUB_MAX * KB];
+  __shared__ double S[KB * KB];
+  __shared__ int s_stop;
+  const double xn2 = sc->xnorm2[l];
+  const double guard2 = 1e6 * 4.93e-32 * xn2;   // (1e3 * 2.22e-16)^2 * ||X||^2
+  int kq = 0;
+  bool stop = !(xn2 > 0.0);
+  bool fallback = false;
+  if (stop && c == 0 && threadIdx.x == 0) atomicOr(&sc->stopmask, 1u << l);
+  int phase = 0;
+  const int tid = threadIdx.x;
+  auto row = [&](int i) { return Ql + (long long)i * ks; };
+  // reads of Q go through L2: rows may have been written by another CTA (fallback path)
+  auto q = [&](int i, int col) { return __ldcg(Ql + (long long)i * ks + col); };
+
+  for (long long e = (long long)r0 * ks + tid; e < (long long)r1 * ks; e += blockDim.x) Ql[e] = 0.0;
+  __syncthreads();
+
+  // per-row helpers on the working block B = Q[:, kq:kq+KB]
+  auto partial_h = [&](double* P) {           // P[a*KB+jc] = sum_{own rows} Q[i][a] B[i][jc]
+    for (int e = tid; e < kq * KB; e += blockDim.x) {
+      int a = e / KB, jc = e % KB;
+      double v = 0.0;
+      for (int i = r0; i < r1; ++i) v += q(i, a) * q(i, kq + jc);
+      P[e] = v;
+    }
+  };
+  auto partial_S = [&](double* P) {           // P[a*KB+b] = sum_{own rows} B[i][a] B[i][b]
+    for (int e = tid; e < KB * KB; e += blockDim.x) {
+      int a = e / KB, b = e % KB;
+      double v = 0.0;
+      for (int i = r0; i < r1; ++i) v += q(i, kq + a) * q(i, kq + b);
+      P[e] = v;
+    }
+  };
+  auto reduce_h = [&](int ph) {
+    for (int e = tid; e < kq * KB; e += blockDim.x) {
+      double v = 0.0;
+      for (int cc = 0; cc < NBC; ++cc) v += __ldcg(pbuf(ph, l, cc) + e);
+      h[e] = v;
+    }
+  };
+  auto reduce_S = [&](int ph, int off) {
+    if (tid < KB * KB) {
+      double v = 0.0;
+      for (int cc = 0; cc < NBC; ++cc) v += __ldcg(pbuf(ph, l, cc) + off + tid);
+      S[tid] = v;
+    }
+  };
+  auto subtract_Qh = [&]() {                  // B -= Q[:, :kq] h on own rows
+    for (int e = tid; e < (r1 - r0) * KB; e += blockDim.x) {
+      int i = r0 + e / KB, jc = e % KB;
+      double v = q(i, kq + jc);
+      for (int a = 0; a < kq; ++a) v -= q(i, a) * h[a * KB + jc];
+      row(i)[kq + jc] = v;
+    }
+  };
+  auto solve_LT = [&]() {                     // B <- B L^{-T} on own rows (L in S)
+    for (int i = r0 + tid; i < r1; i += blockDim.x) {
+      double y[KB];
+      for (int jc = 0; jc < KB; ++jc) {
+        double v = q(i, kq + jc);
+        for (int k = 0; k < jc; ++k) v -= S[jc * KB + k] * y[k];
+        y[jc] = v / S[jc * KB + jc];
+      }
+      for (int jc = 0; jc < KB; ++jc) row(i)[kq + jc] = y[jc];
+    }
+  };
+  // Fallback for a block too ill-conditioned for Cholesky QR (fast-decaying spectra): CTA 0
+  // of the mode orthonormalises the 8 columns one by one (classical Gram-Schmidt, two
+  // passes, against the block's accepted columns; the two projections against the earlier
+  // blocks were already done in parallel), drops columns that fall below the noise guard,
+  // compacts the accepted ones to the front and publishes their count.
+  __shared__ double fred[8][KB];
+  __shared__ double fd[KB];
+  __shared__ int s_acc;
+  auto fallback_block = [&]() {
+    if (tid == 0) s_acc = 0;
+    __syncthreads();
+    for (int jc = 0; jc < KB; ++jc) {
+      const int acc = s_acc;
+      for (int pass = 0; pass < 2 && acc > 0; ++pass) {
+        double d[KB];
+        for (int a = 0; a < KB; ++a) d[a] = 0.0;
+        for (int i = tid; i < n; i += blockDim.x) {
+          double v = q(i, kq + jc);
+          for (int a = 0; a < acc; ++a) d[a] += q(i, kq + a) * v;
+        }
+        for (int a = 0; a < acc; ++a) {
+          double v = d[a];
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+          if ((tid & 31) == 0) fred[tid >> 5][a] = v;
+        }
+        __syncthreads();
+        if (tid < acc) {
+          double v = 0.0;
+          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += fred[w][tid];
+          fd[tid] = v;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += blockDim.x) {
+          double v = q(i, kq + jc);
+          for (int a = 0; a < acc; ++a) v -= fd[a] * q(i, kq + a);
+          row(i)[kq + jc] = v;
+        }
+        __syncthreads();
+      }
+      double nv = 0.0;
+      for (int i = tid; i < n; i += blockDim.x) { double v = q(i, kq + jc); nv += v * v; }
+      for (int o = 16; o > 0; o >>= 1) nv += __shfl_down_sync(0xffffffffu, nv, o);
+      if ((tid & 31) == 0) fred[tid >> 5][0] = nv;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += fred[w][0];
+        fd[0] = t;
+      }
+      __syncthreads();
+      const double nv2 = fd[0];
+      if (nv2 >= guard2 && nv2 > 0.0) {
+        const double sc1 = 1.0 / sqrt(nv2);
+        for (int i = tid; i < n; i += blockDim.x) row(i)[kq + acc] = q(i, kq + jc) * sc1;
+        __syncthreads();
+        if (tid == 0) s_acc = acc + 1;
+      }
+      __syncthreads();
+    }
+    const int acc = s_acc;
+    for (int e = tid; e < n * (KB - acc); e += blockDim.x) {
+      int i = e / (KB - acc), jc = acc + e % (KB - acc);
+      row(i)[kq + jc] = 0.0;
+    }
+    if (tid == 0) sc->blk_acc[l] = acc;
+  };
+
+  auto mark_stop = [&](unsigned flag) {
+    stop = true;
+    if (c == 0 && tid == 0) {
+      atomicOr(&sc->stopmask, 1u << l);
+      if (flag) atomicOr(&sc->flags, flag);
+    }
+  };
+
+  for (int s = 0; s < ks; s += KB) {
+    if (!stop)
+      for (int e = tid; e < (r1 - r0) * KB; e += blockDim.x) {
+        int i = r0 + e / KB, jc = e % KB;
+        row(i)[kq + jc] = Xl[(long long)i * ks + s + jc];
+      }
+    __syncthreads();   // the partial products below read rows written by other threads
+    // (A) first projection against the accepted columns
+    if (!stop && kq > 0) partial_h(pbuf(phase, l, c));
+    grid_barrier(sc, bar_gen, poisoned);
+    if (*(volatile unsigned*)&sc->stopmask == 7u) break;   // every mode finished (same view in all CTAs)
+    if (!stop && kq > 0) { reduce_h(phase); __syncthreads(); subtract_Qh(); }
+    __syncthreads();
+    ++phase;
+    // (B) second projection
+    if (!stop && kq > 0) partial_h(pbuf(phase, l, c));
+    grid_barrier(sc, bar_gen, poisoned);
+    if (!stop && kq > 0) { reduce_h(phase); __syncthreads(); subtract_Qh(); }
+    __syncthreads();
+    ++phase;
+    // (C) Gram of the block: norm test and first Cholesky QR
+    if (!stop) partial_S(pbuf(phase, l, c));
+    grid_barrier(sc, bar_gen, poisoned);
+    if (!stop) {
+      reduce_S(phase, 0);
+      __syncthreads();
+      if (tid == 0) {
+        double tr = 0.0;
+        for (int a = 0; a < KB; ++a) tr += S[a * KB + a];
+        s_stop = (tr < guard2) ? 1 : (chol8(S, 1e-10) ? 0 : 3);
+      }
+      __syncthreads();
+      if (s_stop == 1) mark_stop(0u);
+      else if (s_stop == 3) { fallback = true; if (c == 0) fallback_block(); }
+      else solve_LT();
+    }
+    __syncthreads();
+    ++phase;
+    // (D) reprojection and second Cholesky QR from one reduction:
+    //     h = Q^T B, S = B^T B, (B - Q h)^T (B - Q h) = S - h^T h
+    if (!stop && !fallback) {
+      double* P = pbuf(phase, l, c);
+      if (kq > 0) partial_h(P);
+      partial_S(P + (long long)ks * KB);
+    }
+    grid_barrier(sc, bar_gen, poisoned);
+    if (!stop && !fallback) {
+      if (kq > 0) reduce_h(phase);
+      reduce_S(phase, ks * KB);
+      __syncthreads();
+      if (tid < KB * KB && kq > 0) {
+        int a = tid / KB, b = tid % KB;
+        double v = 0.0;
+        for (int m = 0; m < kq; ++m) v += h[m * KB + a] * h[m * KB + b];
+        S[tid] -= v;
+      }
+      __syncthreads();
+      if (kq > 0) subtract_Qh();
+      __syncthreads();
+      if (tid == 0) s_stop = chol8(S) ? 0 : 2;
+      __syncthreads();
+      if (s_stop) mark_stop((unsigned)FLAG_CHOL);
+      else solve_LT();
+    }
+    __syncthreads();
+    ++phase;
+    if (!stop && fallback) {
+      const int acc = (int)__ldcg(&sc->blk_acc[l]);
+      kq += acc;
+      fallback = false;
+      if (acc == 0) mark_stop(0u);
+      if (kq + KB > ks && !stop) mark_stop(0u);
+    } else if (!stop) {
+      kq += KB;
+      if (kq + KB > ks) mark_stop(0u);
+    } else {
+      for (int e = tid; e < (r1 - r0) * KB; e += blockDim.x) {
+        int i = r0 + e / KB, jc = e % KB;
+        if (kq + jc < ks) row(i)[kq + jc] = 0.0;
+      }
+    }
+  }
+  if (c == 0 && tid == 0) sc->k_eff[l] = kq;
+}
+
+// ------------------------------------------------------------------ FP32 Jacobi
+// One CTA per mode: A (ke x ke, FP32, scaled by 1/max diag) in shared memory, V accumulated.
+// Parallel (round-robin) ordering: each round applies ke/2 disjoint rotations.
+__global__ void __launch_bounds__(1024)
+jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* sc, int max_sweeps) {
+  extern __shared__ float smem[];
+  const int l = blockIdx.x;
+  const int ke0 = sc->k_eff[l];
+  const int ke = (ke0 + 1) & ~1;               // even size (padding row/column is zero)
+  const int ld = ke + 1;
+  float* A = smem;                              // ke x ld
+  float* V = smem + ke * ld;                    // ke x ld
+  __shared__ float cs[KSUB_MAX / 2], sn[KSUB_MAX / 2], dpp[KSUB_MAX / 2], dqq[KSUB_MAX / 2];
+  __shared__ int pp[KSUB_MAX / 2], qq[KSUB_MAX / 2];
+  __shared__ int s_rot;
+  __shared__ double s_scale;
+  const double* T = Tm + (long long)l * ks * ks;
+  double* W = Wm + (long long)l * ks * ks;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < ke0; ++i) m = fmax(m, fabs(T[(long long)i * ks + i]));
+    s_scale = (m > 0.0) ? 1.0 / m : 1.0;
+  }
+  __syncthreads();
+  const double scl = s_scale;
+  for (int e = tid; e < ke * ke; e += nt) {
+    int i = e / ke, jc = e % ke;
+    double v = (i < ke0 && jc < ke0) ? T[(long long)i * ks + jc] * scl : 0.0;
+    A[i * ld + jc] = (float)v;
+    V[i * ld + jc] = (i == jc) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int half = ke / 2;
+  for (int sweep = 0; sweep < max_sweeps && ke > 1; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < ke - 1; ++round) {
+      // round-robin pairing: position 0 fixed, the others rotate
+      for (int m = tid; m < half; m += nt) {
+        int a = (m == 0) ? 0 : 1 + (m - 1 + round) % (ke - 1);
+        int b = 1 + (ke - 2 - m + round) % (ke - 1);
+        int p = min(a, b), q = max(a, b);
+        pp[m] = p;
+        qq[m] = q;
+        float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+        float c = 1.f, s = 0.f, t = 0.f;
+        if (apq != 0.f && fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq))) {
+          float theta = (aqq - app) / (2.f * apq);
+          t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
+          c = rsqrtf(1.f + t * t);
+          s = t * c;
+          s_rot = 1;
+        }
+        cs[m] = c;
+        sn[m] = s;
+        dpp[m] = app - t * apq;     // graded-accurate diagonal of the rotated pair
+        dqq[m] = aqq + t * apq;
+      }
+      __syncthreads();
+      // rows: A[p,:], A[q,:]  (skip the 2x2 blocks of the pairs, fixed below)
+      for (int e = tid; e < half * ke; e += nt) {
+        int m = e / ke, col = e % ke;
+        float s = sn[m];
+        if (s == 0.f) continue;
+        int p = pp[m], q = qq[m];
+        float c = cs[m];
+        float ap = A[p * ld + col], aq = A[q * ld + col];
+        A[p * ld + col] = c * ap - s * aq;
+        A[q * ld + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A[:,p], A[:,q] and V[:,p], V[:,q]
+      for (int e = tid; e < half * ke; e += nt) {
+        int m = e / ke, row = e % ke;
+        float s = sn[m];
+        if (s == 0.f) continue;
+        int p = pp[m], q = qq[m];
+        float c = cs[m];
+        float ap = A[row * ld + p], aq = A[row * ld + q];
+        A[row * ld + p] = c * ap - s * aq;
+        A[row * ld + q] = s * ap + c * aq;
+        float vp = V[row * ld + p], vq = V[row * ld + q];
+        V[row * ld + p] = c * vp - s * vq;
+        V[row * ld + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      // exact 2x2 results for the rotated pairs
+      for (int m = tid; m < half; m += nt) {
+        if (sn[m] == 0.f) continue;
+        int p = pp[m], q = qq[m];
+        A[p * ld + p] = dpp[m];
+        A[q * ld + q] = dqq[m];
+        A[p * ld + q] = 0.f;
+        A[q * ld + p] = 0.f;
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+  // W (ks x ks, FP64): eigenvectors in the leading ke0 x ke0 block, zero elsewhere
+  for (long long e = tid; e < (long long)ks * ks; e += nt) {
+    int i = (int)(e / ks), jc = (int)(e % ks);
+    W[e] = (i < ke0 && jc < ke0) ? (double)V[i * ld + jc] : 0.0;
+  }
+}
+
+// M = I - E/2 + 3/8 E^2 (Newton-Schulz step for (Q^T Q)^{-1/2}) from E = Q^T Q - I and
+// E2 = E^2 on the leading ke block; zero elsewhere.  In place on E is allowed.
+__global__ void ns_matrix_kernel(const double* E, const double* E2, double* M, int ks,
+                                 const DevScalars* sc) {
+  int l = blockIdx.y;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ks * ks) return;
+  int i = e / ks, jc = e % ks;
+  int ke = sc->k_eff[l];
+  long long o = (long long)l * ks * ks + e;
+  double v = 0.0;
+  if (i < ke && jc < ke) v = (i == jc ? 1.0 : 0.0) - 0.5 * E[o] + 0.375 * E2[o];
+  M[o] = v;
+}
+
+// E = Q^T Q - I in place (leading ke block only; zero outside)
+__global__ void sub_identity_kernel(double* A, int ks, const DevScalars* sc) {
+  int l = blockIdx.y;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ks * ks) return;
+  int i = e / ks, jc = e % ks;
+  int ke = sc->k_eff[l];
+  long long o = (long long)l * ks * ks + e;
+  A[o] = (i < ke && jc < ke) ? A[o] - (i == jc ? 1.0 : 0.0) : 0.0;
+}
+
+// ------------------------------------------------------------------ rank selection
+// One CTA per mode: sort diag(T) descending, tail(r) = (trG - trT) + sum_{i>=r} lambda_i,
+// r = min{r >= 1 : tail(r) <= eps^2/3 * trG}, bounded by rank_cap and rmax.
+__global__ void rank_select_kernel(const double* Tm, int ks, double eps, int cap, int rmax,
+                                   int* order, double* ev, DevScalars* sc) {
+  const int l = blockIdx.x;
+  const int ke = sc->k_eff[l];
+  const double* T = Tm + (long long)l * ks * ks;
+  __shared__ double d[KSUB_MAX];
+  __shared__ int ord[KSUB_MAX];
+  for (int i = threadIdx.x; i < ke; i += blockDim.x) d[i] = T[(long long)i * ks + i];
+  __syncthreads();
+  // rank sort (ties broken by index)
+  for (int i = threadIdx.x; i < ke; i += blockDim.x) {
+    int pos = 0;
+    for (int jc = 0; jc < ke; ++jc)
+      if (d[jc] > d[i] || (d[jc] == d[i] && jc < i)) ++pos;
+    ord[pos] = i;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ks; i += blockDim.x) {
+    order[l * ks + i] = (i < ke) ? ord[i] : -1;
+    ev[l * ks + i] = (i < ke) ? d[ord[i]] : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    double trG = sc->trG[l];
+    double trT = 0.0;
+    for (int i = 0; i < ke; ++i) trT += d[i];
+    sc->trT[l] = trT;
+    int r = 0;
+    double tail_r = 0.0;
+    if (trG > 0.0 && ke > 0) {
+      double outside = fmax(trG - trT, 0.0);
+      double budget = eps * eps / 3.0 * trG;
+      // tail(r) for r = ke .. 1
+      double tail = outside;
+      int found = -1;
+      double tail_found = 0.0;
+      for (int rr = ke; rr >= 1; --rr) {
+        // tail currently = tail(rr)
+        if (tail <= budget) { found = rr; tail_found = tail; }
+        else break;
+        tail += fmax(d[ord[rr - 1]], 0.0);
+      }
+      bool capped = false;
+      if (found < 0) { found = ke; tail_found = outside; capped = true; }
+      r = found;
+      int lim = rmax;
+      if (cap > 0 && cap < lim) lim = cap;
+      if (r > lim) {
+        capped = true;
+        double t2 = outside;
+        for (int i = lim; i < ke; ++i) t2 += fmax(d[ord[i]], 0.0);
+        r = lim;
+        tail_found = t2;
+      }
+      tail_r = tail_found / trG;
+      if (capped) atomicOr(&sc->flags, (unsigned)FLAG_RANK_CAPPED);
+    }
+    sc->rank[l] = r;
+    sc->tail_rel[l] = tail_r;
+  }
+}
+
+// Z[l][i][a] = Q[l][i][order[a]] for a < r_l, 0 otherwise (FP64 and FP32 copies)
+__global__ void gather_Z_kernel(const double* Q, const int* order, int n, int ks, int rmax,
+                                const DevScalars* sc, double* Z64, float* Z32) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long tot = 3ll * n * rmax;
+  if (e >= tot) return;
+  int l = (int)(e / ((long long)n * rmax));
+  int rem = (int)(e % ((long long)n * rmax));
+  int i = rem / rmax, a = rem % rmax;
+  double v = 0.0;
+  if (a < sc->rank[l]) v = Q[((long long)l * n + i) * ks + order[l * ks + a]];
+  Z64[e] = v;
+  Z32[e] = (float)v;
+}
+
+// ------------------------------------------------------------------ driver
+static int jacobi_pass(Ctx& c, double*& Qa, double*& Qb, int sweeps) {
+  const int n = c.n, ks = c.ksub;
+  const long long sQ = (long long)n * ks, sK = (long long)ks * ks;
+  const int* ke = c.sc->k_eff;
+  size_t shm = 2ull * ks * (ks + 1) * sizeof(float);
+  cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, sweeps);
+  // Qb = Qa W ; T2k = T W ; T = W^T T2k
+  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, c.W, ks, sK, 0.0, Qb,
+                       ks, sQ, 3, 1, nullptr, ke, ke);
+  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.T, ks, sK, c.W, ks, sK, 0.0,
+                       c.T2k, ks, sK, 3, 1, ke, ke, ke);
+  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.W, ks, sK, c.T2k, ks, sK, 0.0,
+                       c.T, ks, sK, 3, 1, ke, ke, ke);
+  // Newton-Schulz: E = Qb^T Qb - I ; M = I - E/2 + 3/8 E^2 ; Qa = Qb M ; T = M^T T M
+  cudaMemsetAsync(c.W, 0, sizeof(double) * 3 * sK, c.stream);
+  gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, Qb, ks, sQ, Qb, ks, sQ, 0.0, c.W,
+                       ks, sK, 3, 8, ke, ke, nullptr);
+  dim3 g2((ks * ks + 255) / 256, 3);
+  sub_identity_kernel<<<g2, 256, 0, c.stream>>>(c.W, ks, c.sc);
+  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W, ks, sK, 0.0,
+                       c.T2k, ks, sK, 3, 1, ke, ke, ke);
+  // W holds E, T2k holds E^2: W <- M = I - E/2 + 3/8 E^2
+  ns_matrix_kernel<<<g2, 256, 0, c.stream>>>(c.W, c.T2k, c.W, ks, c.sc);
+  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qb, ks, sQ, c.W, ks, sK, 0.0, Qa,
+                       ks, sQ, 3, 1, nullptr, ke, ke);
+  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.T, ks, sK, c.W, ks, sK, 0.0,
+                       c.T2k, ks, sK, 3, 1, ke, ke, ke);
+  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.W, ks, sK, c.T2k, ks, sK, 0.0,
+                       c.T, ks, sK, 3, 1, ke, ke, ke);
+  return 11;
+}
+
+int launch_subspace(Ctx& c) {
+  const int n = c.n, ks = c.ksub;
+  const long long sQ = (long long)n * ks, sK = (long long)ks * ks, sG = (long long)n * n;
+  // X = G * Omega  (Omega stored in Y)
+  int tot = 3 * n * ks;
+  omega_kernel<<<(tot + 255) / 256, 256, 0, c.stream>>>(c.Y, n, ks, tot);
+  cudaMemsetAsync(c.X, 0, sizeof(double) * 3 * sQ, c.stream);
+  gemm_batched<double>(c.stream, false, false, n, ks, n, 1.0, c.G, n, sG, c.Y, ks, sQ, 0.0, c.X,
+                       ks, sQ, 3, 4);
+  traces_kernel<<<3, 256, 0, c.stream>>>(c.G, c.X, n, ks, c.sc);
+  // block Gram-Schmidt (cooperative)
+  {
+    void* args[] = {(void*)&c.X, (void*)&c.Q, (void*)&c.part, (void*)&n, (void*)&ks, (void*)&c.sc};
+    cudaLaunchCooperativeKernel((void*)bcgs2_kernel, dim3(3 * NBC), dim3(256), args, 0, c.stream);
+  }
+  const int* ke = c.sc->k_eff;
+  // RS_DEBUG_SUBSPACE_STEPS=s stops the eigen stage after s sub-steps (inspection only)
+  static const int dbg_steps = [] {
+    const char* e = std::getenv("RS_DEBUG_SUBSPACE_STEPS");
+    return e ? std::atoi(e) : 99;
+  }();
+  if (dbg_steps <= 1) return 5;
+  // Y = G Q ; T = Q^T Y
+  cudaMemsetAsync(c.Y, 0, sizeof(double) * 3 * sQ, c.stream);
+  gemm_batched<double>(c.stream, false, false, n, ks, n, 1.0, c.G, n, sG, c.Q, ks, sQ, 0.0, c.Y,
+                       ks, sQ, 3, 4, nullptr, ke, nullptr);
+  cudaMemsetAsync(c.T, 0, sizeof(double) * 3 * sK, c.stream);
+  gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, c.Q, ks, sQ, c.Y, ks, sQ, 0.0, c.T,
+                       ks, sK, 3, 8, ke, ke, nullptr);
+  // two Jacobi passes; Q alternates between c.Q and c.X
+  double* Qa = c.Q;
+  double* Qb = c.X;
+  int k = 6;
+  if (dbg_steps <= 2) return k;
+  k += jacobi_pass(c, Qa, Qb, 10);
+  if (dbg_steps <= 3) return k;
+  k += jacobi_pass(c, Qa, Qb, 3);
+  // Qa holds the final basis (c.Q)
+  rank_select_kernel<<<3, 128, 0, c.stream>>>(c.T, ks, c.cfg.eps, c.cfg.rank_cap, c.rmax, c.order,
+                                              c.ev, c.sc);
+  long long totZ = 3ll * n * c.rmax;
+  gather_Z_kernel<<<(unsigned)((totZ + 255) / 256), 256, 0, c.stream>>>(Qa, c.order, n, ks, c.rmax,
+                                                                        c.sc, c.Z64, c.Z32);
+  return k + 2;
+}
+
+}  // namespace rs

@@ -1,0 +1,159 @@
+// Internal declarations of the RS library (CUDA path only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+
+#include "../../include/rs.h"
+
+namespace rs {
+
+// Width of the column blocks of the block Gram-Schmidt orthonormalisation.
+constexpr int KB = 8;
+// CTAs per mode of the cooperative block Gram-Schmidt kernel.
+constexpr int NBC = 16;
+// Largest Tucker rank the projection kernel supports.
+constexpr int RMAX_LIMIT = 160;
+// Largest subspace width the one-CTA Jacobi kernel holds in shared memory.
+constexpr int KSUB_MAX = 160;
+// Side of the particle bins used to find the windows that touch a grid tile.
+constexpr int BIN = 16;
+
+// Device-side status bits (accumulated with atomicOr, read by rs_report).
+enum : unsigned {
+  FLAG_OUTSIDE = 1u,      // centre outside the box or non-finite input
+  FLAG_SEPARATION = 2u,   // two centres closer than min_sep
+  FLAG_RANK_CAPPED = 4u,  // eps not met within the rank limit
+  FLAG_CHOL = 8u,         // a Cholesky factor of a Gram-Schmidt block was not positive
+  FLAG_TIMEOUT = 16u,     // a bounded grid-barrier wait ran out
+  FLAG_WINDOWS = 32u      // more than 256 windows per round reached one output tile
+};
+
+// Scalars shared by the kernels of one solve (device memory).
+struct DevScalars {
+  double P_R0, P_Rl0, delta;
+  double trG[3], trT[3], xnorm2[3], tail_rel[3];
+  double energy;
+  int gamma;
+  int n_nz;                 // particles with nonzero charge
+  int nzj_count[3];         // distinct grid coordinates carrying charge, per mode
+  int k_eff[3];             // accepted Gram-Schmidt columns per mode
+  int rank[3];              // Tucker ranks
+  unsigned flags;
+  unsigned bar_count, bar_gen;   // grid barrier of the cooperative Gram-Schmidt kernel
+  unsigned stopmask;             // modes whose Gram-Schmidt has finished
+  int blk_acc[3];                // columns accepted by the one-CTA fallback of the current block
+};
+
+struct Ctx {
+  rs_config cfg;
+  cudaStream_t stream = nullptr;
+  int n = 0, R = 0, R_l = 0, R_s = 0, L = 0;   // L = 2n - 1
+  int ksub = 0;        // subspace width (multiple of KB)
+  int rmax = 0;        // rank bound = leading dimension of Tucker factors
+  int nbin = 0;        // bins per axis
+  int maxN = 0;
+  bool fp64 = true;
+  double h = 0.0;
+  int last_flags = 0;
+  int last_N = 0;
+  bool solved = false;
+  std::string err;
+
+  // device buffers
+  double* pk64 = nullptr;   // R x L
+  float*  pk32 = nullptr;   // R x L
+  double* xyz = nullptr;    // maxN x 3 (copy of host input)
+  double* Z = nullptr;      // maxN
+  int*    j = nullptr;      // maxN x 3 grid indices
+  int*    nz_idx = nullptr; // maxN, particles with nonzero charge (ascending)
+  double* C = nullptr;      // 3 x n aggregated squared column weights
+  int*    nzj = nullptr;    // 3 x n distinct coordinates with C > 0
+  double* F = nullptr;      // L x L
+  double* G = nullptr;      // 3 x n x n
+  double* X = nullptr;      // 3 x n x ksub
+  double* Q = nullptr;      // 3 x n x ksub
+  double* Y = nullptr;      // 3 x n x ksub
+  double* T = nullptr;      // 3 x ksub x ksub
+  double* T2k = nullptr;    // 3 x ksub x ksub (scratch)
+  double* W = nullptr;      // 3 x ksub x ksub
+  double* part = nullptr;   // partial sums of the Gram-Schmidt kernel
+  int*    order = nullptr;  // 3 x ksub eigenvalue order
+  double* ev = nullptr;     // 3 x ksub sorted eigenvalues
+  double* Z64 = nullptr;    // 3 x n x rmax Tucker bases
+  float*  Z32 = nullptr;
+  void*   Qp = nullptr;     // 3 x n x R_l x rmax projected factors (T)
+  double* beta64 = nullptr; // rmax^3 FP64 accumulator
+  void*   beta = nullptr;   // rmax^3 (T)
+  void*   T1 = nullptr;     // rmax x rmax x n (T)
+  void*   T2 = nullptr;     // rmax x n x n (T)
+  int*    bin_count = nullptr;  // nbin^3 + 1
+  int*    bin_start = nullptr;  // nbin^3 + 1
+  int*    bin_items = nullptr;  // maxN (indices into nz list order)
+  double* Epart = nullptr;      // energy partial sums
+  int*    adims = nullptr;      // rmax: per-batch row counts of the mode-2 product
+  int*    kdims = nullptr;      // rmax: per-batch inner sizes of the mode-2 product
+  DevScalars* sc = nullptr;
+  DevScalars* h_sc = nullptr;   // pinned host copy
+
+  // stage profiling (CUDA events on c.stream, ring of PROF_RING solves)
+  int launches = 0;             // kernels launched by the last solve
+  bool profile = false;
+  cudaEvent_t* prof_ev = nullptr;
+  long long prof_count = 0;     // solves recorded since the last read
+};
+
+constexpr int NSTAGE = 9;
+constexpr int PROF_RING = 512;
+
+// Plain-data view of a context for kernels that evaluate the RS tensor at points.
+struct DevView {
+  int n, rmax, R, R_l, nbin;
+  const DevScalars* sc;
+  const int* bin_start;
+  const int* bin_items;
+  const int* j;
+  const double* pk64;
+  const double* Z;
+  const int* nz_idx;
+};
+
+inline DevView make_view(const Ctx& c) {
+  DevView v;
+  v.n = c.n; v.rmax = c.rmax; v.R = c.R; v.R_l = c.R_l; v.nbin = c.nbin;
+  v.sc = c.sc; v.bin_start = c.bin_start; v.bin_items = c.bin_items; v.j = c.j;
+  v.pk64 = c.pk64; v.Z = c.Z; v.nz_idx = c.nz_idx;
+  return v;
+}
+
+// ---------------------------------------------------------------- launchers
+// Each launcher enqueues its kernels on c.stream and returns how many kernels it launched.
+// setup (rs_setup.cu)
+int launch_factors(Ctx& c);
+int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep);
+int launch_gram(Ctx& c);                 // F matrix + Gram matrices
+// eigen stage (rs_eigen.cu)
+int launch_subspace(Ctx& c);
+// Tucker stage (rs_tucker.cu)
+int launch_projection_core(Ctx& c);
+int launch_bins(Ctx& c);
+int launch_recon_gemm(Ctx& c, void* out);
+int launch_windows(Ctx& c, void* out);
+int launch_energy(Ctx& c, int N);
+int launch_eval_points(Ctx& c, int M, const int* idx, double* out);
+
+// generic batched GEMM on row-major matrices:
+//   C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b]
+// op(A) is M x K (A stored M x K with lda, or K x M when transA), op(B) is K x N.
+template <typename T>
+void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K,
+                  T alpha, const T* A, int lda, long long sA,
+                  const T* B, int ldb, long long sB, T beta, T* C, int ldc, long long sC,
+                  int batch, int splitK, const int* dynM = nullptr, const int* dynN = nullptr,
+                  const int* dynK = nullptr);
+
+}  // namespace rs
+
+#define RS_CUDA_OK(expr) (cudaSuccess == (expr))

@@ -1,0 +1,257 @@
+// Setup stage: sinc quadrature and reference factors (Sec. 2.2), range split and window
+// width (Sec. 2.3), particle snapping and aggregation, and the Gram matrices of the
+// long-range side matrices (Sec. 3.2, Eq. (3.5); Sec. 6, step (I)).
+#include "rs_internal.cuh"
+
+namespace rs {
+
+// ------------------------------------------------------------------ factors (a1, a2)
+// p_k[d] = a_k^{1/3} * (1/h) int_{dh-h/2}^{dh+h/2} exp(-t_k^2 x^2) dx,  d = -(n-1)..(n-1)
+// with t_k = exp(u0 + k h_q), a_k = (2/sqrt(pi)) h_q t_k (exponential sinc rule of the
+// Laplace-Gauss transform of 1/z, Eqs. (2.6)-(2.8); Galerkin cell averages, Eq. (2.5)).
+__global__ void factors_kernel(double* pk64, float* pk32, int R, int n, double h, double hq,
+                               double u0) {
+  const int L = 2 * n - 1;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= R * L) return;
+  int k = e / L, di = e % L;
+  double t = exp(u0 + k * hq);
+  double a = 1.1283791670955126 * hq * t;          // 2/sqrt(pi)
+  double c = fabs((double)(di - (n - 1))) * h;
+  double lo = t * (c - 0.5 * h), hi = t * (c + 0.5 * h);
+  double diff = (lo > 0.5) ? (erfc(lo) - erfc(hi)) : (erf(hi) - erf(lo));
+  double v = cbrt(a) * (0.88622692545275801 / (t * h)) * diff;   // sqrt(pi)/2
+  pk64[e] = v;
+  pk32[e] = (float)v;
+}
+
+// P_R(0), P_{R_l}(0), delta and the window half-width gamma (one CTA).
+// gamma = #{g in [0, n-2] : sum_{k short} p_k[g+1] p_k[0]^2 > delta}  (the sum decreases in g)
+__global__ void scalars_kernel(const double* pk64, int R, int R_l, int n, double delta_rel,
+                               DevScalars* sc) {
+  const int L = 2 * n - 1, c0 = n - 1;
+  __shared__ double sPR0, sPRl0;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < R; ++k) {
+      double v = pk64[k * L + c0];
+      a += v * v * v;
+      if (k < R_l) b += v * v * v;
+    }
+    sPR0 = a;
+    sPRl0 = b;
+    cnt = 0;
+  }
+  __syncthreads();
+  const double delta = delta_rel * sPR0;
+  int local = 0;
+  for (int g = threadIdx.x; g <= n - 2; g += blockDim.x) {
+    double v = 0.0;
+    for (int k = R_l; k < R; ++k) {
+      double p0 = pk64[k * L + c0];
+      v += pk64[k * L + c0 + g + 1] * p0 * p0;
+    }
+    if (v > delta) ++local;
+  }
+  atomicAdd(&cnt, local);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sc->P_R0 = sPR0;
+    sc->P_Rl0 = sPRl0;
+    sc->delta = delta;
+    sc->gamma = min(cnt, n - 1);
+  }
+}
+
+int launch_factors(Ctx& c) {
+  int tot = c.R * c.L;
+  factors_kernel<<<(tot + 255) / 256, 256, 0, c.stream>>>(c.pk64, c.pk32, c.R, c.n, c.h,
+                                                          c.cfg.h_q, c.cfg.u0);
+  scalars_kernel<<<1, 256, 0, c.stream>>>(c.pk64, c.R, c.R_l, c.n, c.cfg.delta_rel, c.sc);
+  return 2;
+}
+
+// ------------------------------------------------------------------ particles
+// Snap each centre to its nearest grid point (ties away from zero; Sec. 3.2 places the
+// centres on grid points), flag centres outside the box, and aggregate the squared column
+// weights w^2 = |z|^{2/3} per grid coordinate (columns at equal shifts add in U U^T).
+__global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n, double b,
+                               double h, int* j, double* C, DevScalars* sc) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  double z = Z[p];
+  bool bad = !isfinite(z);
+  int jj[3];
+  for (int l = 0; l < 3; ++l) {
+    double x = xyz[3 * p + l];
+    if (!isfinite(x) || fabs(x) > b * (1.0 + 1e-12)) bad = true;
+    double s = (x + b) / h;
+    int q = isfinite(s) ? (int)floor(s + 0.5) : 0;
+    jj[l] = min(max(q, 0), n - 1);
+    j[3 * p + l] = jj[l];
+  }
+  if (bad) {
+    atomicOr(&sc->flags, (unsigned)FLAG_OUTSIDE);
+    return;
+  }
+  if (z != 0.0) {
+    double w2 = pow(fabs(z), 2.0 / 3.0);
+    for (int l = 0; l < 3; ++l) atomicAdd(&C[l * n + jj[l]], w2);
+  }
+}
+
+// Deterministic compaction of the particles with nonzero charge (one CTA, chunked scan).
+__global__ void compact_nz_kernel(const double* Z, int N, int* nz_idx, DevScalars* sc) {
+  __shared__ int scan[1024];
+  const int T = blockDim.x, t = threadIdx.x;
+  const int per = (N + T - 1) / T;
+  const int b0 = min(N, t * per), b1 = min(N, b0 + per);
+  int cnt = 0;
+  for (int p = b0; p < b1; ++p) cnt += (Z[p] != 0.0 && isfinite(Z[p])) ? 1 : 0;
+  scan[t] = cnt;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {
+    int v = (t >= o) ? scan[t - o] : 0;
+    __syncthreads();
+    scan[t] += v;
+    __syncthreads();
+  }
+  int pos = scan[t] - cnt;
+  for (int p = b0; p < b1; ++p)
+    if (Z[p] != 0.0 && isfinite(Z[p])) nz_idx[pos++] = p;
+  if (t == T - 1) sc->n_nz = scan[t];
+}
+
+// Distinct coordinates with nonzero aggregated weight, per mode (one CTA per mode).
+__global__ void compact_nzj_kernel(const double* C, int n, int* nzj, DevScalars* sc) {
+  __shared__ int scan[1024];
+  const int l = blockIdx.x, T = blockDim.x, t = threadIdx.x;
+  const double* Cl = C + l * n;
+  const int per = (n + T - 1) / T;
+  const int b0 = min(n, t * per), b1 = min(n, b0 + per);
+  int cnt = 0;
+  for (int i = b0; i < b1; ++i) cnt += (Cl[i] > 0.0) ? 1 : 0;
+  scan[t] = cnt;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {
+    int v = (t >= o) ? scan[t - o] : 0;
+    __syncthreads();
+    scan[t] += v;
+    __syncthreads();
+  }
+  int pos = scan[t] - cnt;
+  for (int i = b0; i < b1; ++i)
+    if (Cl[i] > 0.0) nzj[l * n + pos++] = i;
+  if (t == T - 1) sc->nzj_count[l] = scan[t];
+}
+
+// Optional input check: any pair closer than min_sep (O(N^2), input coordinates).
+__global__ void separation_kernel(const double* xyz, int N, double min_sep2, DevScalars* sc) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  double x = xyz[3 * p], y = xyz[3 * p + 1], z = xyz[3 * p + 2];
+  for (int q = p + 1; q < N; ++q) {
+    double dx = xyz[3 * q] - x, dy = xyz[3 * q + 1] - y, dz = xyz[3 * q + 2] - z;
+    if (dx * dx + dy * dy + dz * dz < min_sep2) {
+      atomicOr(&sc->flags, (unsigned)FLAG_SEPARATION);
+      return;
+    }
+  }
+}
+
+int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep) {
+  int k = 2;
+  cudaMemsetAsync(c.C, 0, sizeof(double) * 3 * c.n, c.stream);
+  if (N > 0) {
+    prepare_kernel<<<(N + 255) / 256, 256, 0, c.stream>>>(c.xyz, c.Z, N, c.n, c.cfg.b, c.h, c.j,
+                                                          c.C, c.sc);
+    ++k;
+  }
+  compact_nz_kernel<<<1, 1024, 0, c.stream>>>(c.Z, N, c.nz_idx, c.sc);
+  compact_nzj_kernel<<<3, 1024, 0, c.stream>>>(c.C, c.n, c.nzj, c.sc);
+  if (check_sep && N > 1) {
+    separation_kernel<<<(N + 127) / 128, 128, 0, c.stream>>>(c.xyz, N, min_sep * min_sep, c.sc);
+    ++k;
+  }
+  return k;
+}
+
+// ------------------------------------------------------------------ F and Gram (a3, a4)
+// F[a][b] = sum_{k long} p_k[a] p_k[b] over the doubled index range (L x L, FP64).
+__global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  int a = blockIdx.y;
+  if (b >= L) return;
+  double v = 0.0;
+  for (int k = 0; k < R_l; ++k) v += pk64[k * L + a] * pk64[k * L + b];
+  F[(long long)a * L + b] = v;
+}
+
+static void launch_fmatrix(Ctx& c) {
+  dim3 grid((c.L + 255) / 256, c.L);
+  fmatrix_kernel<<<grid, 256, 0, c.stream>>>(c.pk64, c.R_l, c.L, c.F);
+}
+
+// G_l[i][i'] = sum_j C_l[j] F[i - j + n - 1][i' - j + n - 1]  (= U^(l) U^(l)^T with the columns
+// of equal shift aggregated).  Upper-triangular 32x32 tiles; the transpose is mirrored.
+__global__ void __launch_bounds__(256)
+gram_kernel(const double* __restrict__ F, const double* __restrict__ C, const int* __restrict__ nzj,
+            const DevScalars* sc, int n, double* G) {
+  const int l = blockIdx.y;
+  const int nt = (n + 31) / 32;
+  // map blockIdx.x -> (ti <= tj)
+  int t = blockIdx.x, ti = 0;
+  while (t >= nt - ti) { t -= nt - ti; ++ti; }
+  const int tj = ti + t;
+  const int I0 = ti * 32, J0 = tj * 32;
+  const int L = 2 * n - 1;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 8 rows of threads
+  __shared__ double sw[256];
+  __shared__ int sj[256];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int cnt = sc->nzj_count[l];
+  const double* Cl = C + l * n;
+  const int* nl = nzj + l * n;
+  const int ip = J0 + tx;
+  for (int m0 = 0; m0 < cnt; m0 += 256) {
+    int m = m0 + threadIdx.x;
+    if (m < cnt) {
+      int jv = nl[m];
+      sj[threadIdx.x] = jv;
+      sw[threadIdx.x] = Cl[jv];
+    }
+    __syncthreads();
+    int mm = min(256, cnt - m0);
+    for (int q = 0; q < mm; ++q) {
+      int jv = sj[q];
+      double w = sw[q];
+      const double* Fr = F + (long long)(I0 + ty - jv + n - 1) * L + (ip - jv + n - 1);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int i = I0 + ty + 8 * r;
+        if (i < n && ip < n) acc[r] = fma(w, Fr[(long long)(8 * r) * L], acc[r]);
+      }
+    }
+    __syncthreads();
+  }
+  double* Gl = G + (long long)l * n * n;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int i = I0 + ty + 8 * r;
+    if (i < n && ip < n) {
+      Gl[(long long)i * n + ip] = acc[r];
+      if (ti != tj) Gl[(long long)ip * n + i] = acc[r];
+    }
+  }
+}
+
+int launch_gram(Ctx& c) {
+  launch_fmatrix(c);
+  int nt = (c.n + 31) / 32;
+  dim3 grid(nt * (nt + 1) / 2, 3);
+  gram_kernel<<<grid, 256, 0, c.stream>>>(c.F, c.C, c.nzj, c.sc, c.n, c.G);
+  return 2;
+}
+
+}  // namespace rs

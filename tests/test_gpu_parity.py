@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the same
+seeded inputs.
+
+Tolerances (relative Frobenius norms unless stated):
+* same ranks, FP64 path vs the oracle's RS-Tucker tensor: 1e-7 (the two eigensolvers agree
+  on the retained subspaces to ~1e-8; rounding of the FP64 contractions is ~1e-14);
+* same ranks, FP32 path vs the oracle's RS-Tucker tensor: 1e-6 (FP32 products, FP64-combined
+  chunk sums in the core, FP32 storage of the output: ~1e-7 per stage);
+* against the full-rank canonical sum P_0 of the oracle: eps * ||P_l|| / ||P_0|| (Tucker
+  truncation) + the window cut-off (each window loses at most delta*|z| per point) + the
+  rounding budget above;
+* energy: 1e-8 (FP64) / 1e-6 (FP32) of sum_{j<k} |z_j z_k| / r_jk against the oracle's energy
+  of the same RS tensor (Eq. (4.7)).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import rs_oracle as O  # noqa: E402
+from workloads import load_config, make_particles  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(cfg, N):
+    from paper_1606_09218_gb300 import RSContext, config_from_workload
+    return RSContext(config_from_workload(cfg, max_particles=max(1, N)))
+
+
+def _solve(cfg, xyz, Z, energy=True):
+    ctx = _ctx(cfg, len(Z))
+    ctx.solve(torch.tensor(xyz, device="cuda"), torch.tensor(Z, device="cuda"), energy=energy)
+    torch.cuda.synchronize()
+    return ctx
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    cfg = dict(load_config("c1_box64_n129"))
+    cfg["rank_cap"] = 0
+    p = make_particles(cfg)
+    pr = O.Problem(cfg, p.xyz, p.Z)
+    return cfg, p, pr
+
+
+def test_c1_fp64_grid_matches_oracle_rs_tucker(c1):
+    cfg, p, pr = c1
+    ctx = _solve(cfg, p.xyz, p.Z)
+    rep = ctx.report()
+    P = ctx.potential.cpu().numpy()
+    _, _, rk_or, _, _, _ = pr.tucker()
+    assert all(abs(a - b) <= 1 for a, b in zip(rep["ranks"], rk_or)), (rep["ranks"], rk_or)
+    assert rep["gamma"] == pr.gamma
+    assert abs(rep["P_R0"] - pr.PR0) <= 1e-13 * pr.PR0
+    Z0s, beta, _, _, _, _ = pr.tucker(ranks=rep["ranks"])
+    ref = O.tucker_full(beta, Z0s) + pr.windows_grid()
+    assert _rel(P, ref) < 1e-7
+    # against the untruncated canonical sum P_0
+    P0 = pr.P0_grid()
+    Pl = pr.Pl_grid()
+    bound = cfg["eps"] * np.linalg.norm(Pl) / np.linalg.norm(P0) + \
+        pr.delta * np.sum(np.abs(pr.z)) * np.sqrt(P0.size) / np.linalg.norm(P0) + 1e-9
+    assert _rel(P, P0) <= bound
+    # energy of the same RS tensor (Eq. (4.7))
+    E = ctx.energy()
+    A = O.tucker_points(beta, Z0s, pr.j) + pr.windows_points(pr.j)
+    Eref = O.energy_from_potential(A, pr.z, pr.PR0)
+    scale = O.energy_scale(pr.xyz_snapped, pr.z)
+    assert abs(E - Eref) <= 1e-8 * scale
+    assert abs(E - pr.energy_P0()) <= 3 * cfg["eps"] * scale + 1e-6 * scale
+    ctx.close()
+
+
+def test_c1_rank_cap_reports_and_matches(c1):
+    cfg, p, pr = c1
+    cfg2 = dict(cfg)
+    cfg2["rank_cap"] = 16
+    ctx = _solve(cfg2, p.xyz, p.Z)
+    rep = ctx.report()
+    assert rep["status"] == 1 and rep["ranks"] == [16, 16, 16]
+    Z0s, beta, _, _, _, _ = pr.tucker(ranks=[16, 16, 16])
+    ref = O.tucker_full(beta, Z0s) + pr.windows_grid()
+    assert _rel(ctx.potential.cpu().numpy(), ref) < 1e-7
+    ctx.close()
+
+
+def test_tucker_factors_orthonormal_and_core(c1):
+    cfg, p, pr = c1
+    ctx = _solve(cfg, p.xyz, p.Z, energy=False)
+    ranks, Vs, beta = ctx.tucker()
+    for V in Vs:
+        V = V.cpu().numpy()
+        assert np.abs(V.T @ V - np.eye(V.shape[1])).max() < 1e-12
+    # projection identity: ||beta|| <= ||P_l|| and the gap is the Tucker error^2
+    Pl = pr.Pl_grid()
+    b = beta.cpu().numpy()
+    gap = np.linalg.norm(Pl) ** 2 - np.sum(b * b)
+    assert gap >= -1e-10 * np.linalg.norm(Pl) ** 2
+    assert np.sqrt(max(gap, 0)) <= cfg["eps"] * np.linalg.norm(Pl)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
+def test_small_random_problems(prec):
+    """Several tiles with ragged edges (n = 37, 45), windows that overlap and touch the
+    boundary, mixed signs and a zero charge."""
+    rng = np.random.default_rng(5)
+    for n, N in ((37, 7), (45, 19)):
+        cfg = dict(b=4.0, n=n, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0,
+                   delta_rel=1e-8, precision=prec, snap=True)
+        xyz = rng.uniform(-4.0, 4.0, (N, 3))
+        xyz[0] = [-4.0, 4.0, 0.0]
+        Z = rng.uniform(-1, 1, N)
+        Z[1] = 0.0
+        pr = O.Problem(cfg, xyz, Z)
+        ctx = _solve(cfg, xyz, Z)
+        rep = ctx.report()
+        Z0s, beta, _, _, _, _ = pr.tucker(ranks=rep["ranks"])
+        ref = O.tucker_full(beta, Z0s) + pr.windows_grid()
+        tol = 1e-7 if prec == "fp64" else 1e-6
+        assert _rel(ctx.potential.double().cpu().numpy(), ref) < tol, (n, N)
+        A = O.tucker_points(beta, Z0s, pr.j) + pr.windows_points(pr.j)
+        Eref = O.energy_from_potential(A, pr.z, pr.PR0)
+        assert abs(ctx.energy() - Eref) <= (1e-8 if prec == "fp64" else 1e-6) * O.energy_scale(pr.xyz_snapped, pr.z)
+        ctx.close()
+
+
+def test_eval_points_matches_grid(c1):
+    cfg, p, pr = c1
+    ctx = _solve(cfg, p.xyz, p.Z, energy=False)
+    rng = np.random.default_rng(2)
+    idx = rng.integers(0, pr.n, (500, 3))
+    v = ctx.eval_points(torch.tensor(idx, dtype=torch.int32)).cpu().numpy()
+    P = ctx.potential.cpu().numpy()
+    g = P[idx[:, 0], idx[:, 1], idx[:, 2]]
+    assert np.max(np.abs(v - g)) <= 1e-10 * np.max(np.abs(P))
+    ctx.close()
+
+
+def test_edge_cases_empty_zero_and_single():
+    cfg = dict(b=4.0, n=33, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8,
+               precision="fp64", snap=True)
+    from paper_1606_09218_gb300 import RSContext, config_from_workload
+    ctx = RSContext(config_from_workload(cfg, max_particles=4))
+    # empty input
+    ctx.solve(torch.zeros((0, 3), dtype=torch.float64, device="cuda"),
+              torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert float(ctx.potential.abs().max()) == 0.0 and ctx.energy() == 0.0
+    # all charges zero
+    ctx.solve(torch.tensor([[0.5, 0.5, 0.5]], dtype=torch.float64, device="cuda"),
+              torch.zeros(1, dtype=torch.float64, device="cuda"))
+    assert float(ctx.potential.abs().max()) == 0.0 and ctx.energy() == 0.0
+    # a single charge: no interaction energy; potential equals the oracle
+    xyz = np.array([[1.0, -2.0, 0.25]])
+    Z = np.array([0.8])
+    ctx.solve(torch.tensor(xyz, device="cuda"), torch.tensor(Z, device="cuda"))
+    pr = O.Problem(cfg, xyz, Z)
+    rep = ctx.report()
+    Z0s, beta, _, _, _, _ = pr.tucker(ranks=rep["ranks"])
+    ref = O.tucker_full(beta, Z0s) + pr.windows_grid()
+    assert _rel(ctx.potential.cpu().numpy(), ref) < 1e-7
+    Eref = O.energy_from_potential(O.tucker_points(beta, Z0s, pr.j) + pr.windows_points(pr.j), pr.z, pr.PR0)
+    assert abs(ctx.energy() - Eref) <= 1e-9 * pr.PR0 * Z[0] ** 2
+    # host input path gives the same result (FP64 split-K sums use atomics, so the summation
+    # order may differ between runs: compare at 1e-9, far inside the oracle tolerance)
+    P1 = ctx.potential.clone()
+    ctx.solve(xyz, Z)
+    torch.cuda.synchronize()
+    d = float((P1 - ctx.potential).norm() / P1.norm())
+    assert d < 1e-9, d
+    ctx.close()
+
+
+def test_invalid_inputs_raise():
+    from paper_1606_09218_gb300 import RSContext, RSError, config_from_workload
+    cfg = dict(b=4.0, n=33, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8,
+               precision="fp64", snap=True)
+    ctx = RSContext(config_from_workload(cfg, max_particles=2))
+    with pytest.raises(RSError):
+        ctx.solve(np.array([[5.0, 0.0, 0.0]]), np.array([1.0]))          # outside the box
+    with pytest.raises(RSError):
+        ctx.solve(np.zeros((3, 3)), np.ones(3))                           # above capacity
+    # device-side detection of an outside centre
+    ctx.solve(torch.tensor([[0.0, 0.0, 9.0]], dtype=torch.float64, device="cuda"),
+              torch.ones(1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(RSError):
+        ctx.energy()
+    # separation check
+    ctx.solve(np.array([[0.0, 0.0, 0.0], [0.1, 0.0, 0.0]]), np.array([1.0, -1.0]), min_sep=0.5)
+    with pytest.raises(RSError):
+        ctx.report()
+    ctx.close()
+    bad = config_from_workload(dict(cfg, n=32), max_particles=2)
+    with pytest.raises(RSError):
+        RSContext(bad)
+
+
+def test_c2_full_size_sampled_against_canonical_sum():
+    """Config 2 at full size (n = 513, N = 1000, FP32 bulk): the grid against the oracle's
+    full-rank canonical sum on sampled points (all particle sites plus random points)."""
+    cfg = load_config("c2_protein1000_n513")
+    p = make_particles(cfg)
+    pr = O.Problem(cfg, p.xyz, p.Z)
+    ctx = _solve(cfg, p.xyz, p.Z)
+    rep = ctx.report()
+    assert rep["status"] == 0
+    P = ctx.potential
+    rng = np.random.default_rng(17)
+    idx = np.concatenate([pr.j, rng.integers(0, pr.n, (3000, 3))])
+    it = torch.tensor(idx, device="cuda", dtype=torch.long)
+    g = P[it[:, 0], it[:, 1], it[:, 2]].double().cpu().numpy()
+    ref = pr.P0_points(idx)
+    # Tucker eps on the long part + window cut-off + FP32 rounding
+    err = _rel(g, ref)
+    assert err < 3e-6, err
+    E = ctx.energy()
+    scale = O.energy_scale(pr.xyz_snapped, pr.z)
+    assert abs(E - pr.energy_P0()) <= 3e-6 * scale
+    ctx.close()
