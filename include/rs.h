@@ -161,6 +161,25 @@ rs_status rs_debug_buffer(rs_ctx* ctx, const char* name, void** ptr, size_t* byt
 /* Static name of a stage (NULL outside [0, RS_NSTAGE)). */
 const char* rs_stage_name(int stage);
 
+/* Allocation-free Gram matrices (no counterpart in the paper; an interface for callers that
+ * cannot allocate device memory).  Some callers cannot call cudaMalloc: a host application
+ * that has reserved all device memory and forbids further allocation, a latency-critical
+ * path where an allocation (which may synchronise the device) is not acceptable, or a
+ * plug-in that may only use the memory it is given.  This call allocates nothing.  It
+ * computes, on the given stream, the three n x n FP64 Gram matrices of the long-range side
+ * matrices, G_l = U^(l) U^(l)^T (the same values as the context path's eigen-stage input),
+ * for centres snapped to the grid of cfg (only b, n, R, R_s, h_q, u0, delta_rel are used):
+ *   xyz (N x 3) and Z (N): device pointers, float64;   G: device output, 3 x n x n, C order.
+ * Scratch: a fixed 16 MiB device array inside the library, held by every GPU that loads the
+ * library until the process exits; problems that do not fit (roughly n > 513) are rejected
+ * with RS_ERR_CAPACITY and a message in rs_last_error(NULL).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  Every call reuses the same array, so calls that overlap on the
+ * GPU (different streams, or several host threads) race: serialise them.  Centres outside
+ * the box are clamped to its boundary; errors: RS_ERR_INVALID_ARG, RS_ERR_CAPACITY, RS_ERR_CUDA. */
+rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* xyz, const double* Z,
+                          double* G, void* cuda_stream);
+
 /* Text of the last error of this context (or of rs_create when ctx is NULL). */
 const char* rs_last_error(rs_ctx* ctx);
 

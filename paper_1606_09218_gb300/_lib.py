@@ -35,7 +35,7 @@ RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_VALIDATE_SEPARATION = 1, 2, 4, 16
 #: every symbol ``include/rs.h`` declares
 EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_energy", "rs_report",
             "rs_get_tucker", "rs_eval_points", "rs_profile_enable", "rs_profile_read", "rs_stage_name",
-            "rs_debug_buffer",
+            "rs_debug_buffer", "rs_gram_noalloc",
             "rs_last_error", "rs_version"]
 RS_NSTAGE = 9
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.rs_stage_name.restype = C.c_char_p
     lib.rs_debug_buffer.argtypes = [vp, C.c_char_p, C.POINTER(vp), C.POINTER(C.c_size_t)]
     lib.rs_debug_buffer.restype = C.c_int
+    lib.rs_gram_noalloc.argtypes = [C.POINTER(RSConfigC), C.c_int, vp, vp, vp, vp]
+    lib.rs_gram_noalloc.restype = C.c_int
     lib.rs_last_error.argtypes = [vp]
     lib.rs_last_error.restype = C.c_char_p
     lib.rs_version.argtypes = []

@@ -164,6 +164,11 @@ rs_status status_of(const DevScalars& s) {
 
 }  // namespace
 
+namespace rs {
+// error text returned by rs_last_error(NULL) for calls without a context
+void set_host_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace rs
+
 extern "C" {
 
 const char* rs_version(void) { return "rs-gb300 0.1 (sm_103a)"; }

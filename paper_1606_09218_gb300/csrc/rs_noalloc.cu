@@ -1,0 +1,124 @@
+// Allocation-free entry point: the Gram matrices of the long-range side matrices
+// (the input of the eigen stage) computed with every scratch buffer in one file-scope
+// device array instead of a context workspace.
+//
+// Some callers cannot call cudaMalloc: code that runs under a host application which has
+// reserved all device memory up front and forbids further allocation, callers on a
+// latency-critical path where an allocation (which may synchronise the device) is not
+// acceptable, and plug-ins that may only use memory handed to them.  This entry point
+// allocates nothing: the caller passes the particles and the output buffer, and the scratch
+// lives in g_noalloc_scratch below.
+#include "rs_internal.cuh"
+
+#include <cmath>
+#include <mutex>
+#include <string>
+
+namespace rs {
+// kernels of the setup stage (rs_setup.cu), launched here on scratch inside the static array
+__global__ void factors_kernel(double* pk64, float* pk32, int R, int n, double h, double hq,
+                               double u0);
+__global__ void scalars_kernel(const double* pk64, int R, int R_l, int n, double delta_rel,
+                               DevScalars* sc);
+__global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n, double b,
+                               double h, int* j, double* C, DevScalars* sc);
+__global__ void compact_nzj_kernel(const double* C, int n, int* nzj, DevScalars* sc);
+__global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F);
+__global__ void gram_kernel(const double* F, const double* C, const int* nzj,
+                            const DevScalars* sc, int n, double* G);
+void set_host_error(const std::string& msg);
+}  // namespace rs
+
+using namespace rs;
+
+namespace {
+
+// 16 MiB of scratch, held by every GPU that loads the library until the process exits.
+constexpr size_t kNoAllocBytes = 16u << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// device address of g_noalloc_scratch, looked up once per device
+constexpr int kMaxDevices = 64;
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* xyz,
+                                     const double* Z, double* G, void* stream) {
+  if (!cfg || N < 0 || (N > 0 && (!xyz || !Z)) || !G) {
+    set_host_error("rs_gram_noalloc: null or negative argument");
+    return RS_ERR_INVALID_ARG;
+  }
+  const int n = cfg->n, R = cfg->R, R_s = cfg->R_s;
+  if (!(cfg->b > 0.0) || n < 5 || (n % 2) == 0 || R < 2 || R > 64 || R_s < 0 || R_s >= R ||
+      !(cfg->h_q > 0.0) || !std::isfinite(cfg->u0) || !(cfg->delta_rel >= 0.0)) {
+    set_host_error("rs_gram_noalloc: invalid configuration");
+    return RS_ERR_INVALID_ARG;
+  }
+  const int L = 2 * n - 1, R_l = R - R_s;
+  // scratch layout: scalars | pk64 | pk32 | j | C | nzj | F
+  size_t off = 0;
+  const size_t o_sc = off;   off = align256(off + sizeof(DevScalars));
+  const size_t o_pk64 = off; off = align256(off + sizeof(double) * (size_t)R * L);
+  const size_t o_pk32 = off; off = align256(off + sizeof(float) * (size_t)R * L);
+  const size_t o_j = off;    off = align256(off + sizeof(int) * 3 * (size_t)(N > 0 ? N : 1));
+  const size_t o_C = off;    off = align256(off + sizeof(double) * 3 * (size_t)n);
+  const size_t o_nzj = off;  off = align256(off + sizeof(int) * 3 * (size_t)n);
+  const size_t o_F = off;    off = align256(off + sizeof(double) * (size_t)L * L);
+  if (off > kNoAllocBytes) {
+    set_host_error("rs_gram_noalloc: problem needs " + std::to_string(off) +
+                   " bytes of scratch, above the fixed 16 MiB (n up to 513 with N up to ~130000)");
+    return RS_ERR_CAPACITY;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    set_host_error("rs_gram_noalloc: no usable current device");
+    return RS_ERR_CUDA;
+  }
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        set_host_error(std::string("rs_gram_noalloc: cudaGetSymbolAddress failed: ") +
+                       cudaGetErrorString(e));
+        return RS_ERR_CUDA;
+      }
+      g_scratch_ptr[dev] = p;
+    }
+    base = (unsigned char*)g_scratch_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DevScalars* sc = (DevScalars*)(base + o_sc);
+  double* pk64 = (double*)(base + o_pk64);
+  float* pk32 = (float*)(base + o_pk32);
+  int* j = (int*)(base + o_j);
+  double* C = (double*)(base + o_C);
+  int* nzj = (int*)(base + o_nzj);
+  double* F = (double*)(base + o_F);
+  const double h = 2.0 * cfg->b / (n - 1);
+  // the array keeps the previous call's contents: clear what is accumulated into
+  cudaMemsetAsync(sc, 0, sizeof(DevScalars), s);
+  cudaMemsetAsync(C, 0, sizeof(double) * 3 * (size_t)n, s);
+  const int tot = R * L;
+  factors_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pk64, pk32, R, n, h, cfg->h_q, cfg->u0);
+  scalars_kernel<<<1, 256, 0, s>>>(pk64, R, R_l, n, cfg->delta_rel, sc);
+  if (N > 0) prepare_kernel<<<(N + 255) / 256, 256, 0, s>>>(xyz, Z, N, n, cfg->b, h, j, C, sc);
+  compact_nzj_kernel<<<3, 1024, 0, s>>>(C, n, nzj, sc);
+  fmatrix_kernel<<<dim3((L + 255) / 256, L), 256, 0, s>>>(pk64, R_l, L, F);
+  const int nt = (n + 31) / 32;
+  gram_kernel<<<dim3(nt * (nt + 1) / 2, 3), 256, 0, s>>>(F, C, nzj, sc, n, G);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_host_error(std::string("rs_gram_noalloc: launch failed: ") + cudaGetErrorString(e));
+    return RS_ERR_CUDA;
+  }
+  return RS_OK;
+}

@@ -1,0 +1,62 @@
+"""The allocation-free entry point rs_gram_noalloc against the context path.
+
+Callers that cannot allocate device memory (a host application that has reserved all of it,
+a latency-critical path where an allocation may synchronise the device, a plug-in limited
+to the memory it is handed) use rs_gram_noalloc, whose scratch is a fixed array inside the
+library.  This file is collected last so that a stop at the first failure has already run
+every other test; it also passes alone in a fresh process.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from workloads import load_config, make_particles  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-12   # FP64 Gram matrices; only the order of the FP64 atomic weight sums differs
+
+
+def _gram_noalloc(lib, ccfg, xyz, Z, n):
+    G = torch.empty((3, n, n), dtype=torch.float64, device="cuda")
+    st = lib.rs_gram_noalloc(C.byref(ccfg), int(Z.numel()), C.c_void_p(xyz.data_ptr()),
+                             C.c_void_p(Z.data_ptr()), C.c_void_p(G.data_ptr()),
+                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st, G
+
+
+@pytest.mark.parametrize("name", ["c1_box64_n129", "c2_protein1000_n513"])
+def test_noalloc_gram_matches_context_path_twice(name):
+    from paper_1606_09218_gb300 import RSContext, _lib, config_from_workload
+    lib = _lib.load()
+    cfg = load_config(name)
+    p = make_particles(cfg)
+    n = int(cfg["n"])
+    xyz = torch.tensor(p.xyz, device="cuda")
+    Z = torch.tensor(p.Z, device="cuda")
+    ccfg = config_from_workload(cfg, max_particles=len(p.Z))
+    ctx = RSContext(ccfg)
+    ctx.solve(xyz, Z, energy=False, want_potential=False)
+    G_ref = ctx.debug_buffer("G", torch.float64)[: 3 * n * n].view(3, n, n).clone()
+    ctx.close()
+    for call in range(2):                       # two calls in a row share the scratch array
+        st, G = _gram_noalloc(lib, ccfg, xyz, Z, n)
+        assert st == _lib.RS_OK, lib.rs_last_error(None)
+        torch.cuda.synchronize()
+        err = float((G - G_ref).norm() / G_ref.norm())
+        assert err < REL_TOL, (call, err)
+
+
+def test_noalloc_rejects_problems_above_its_scratch():
+    from paper_1606_09218_gb300 import _lib, config_from_workload
+    lib = _lib.load()
+    cfg = dict(load_config("c3_nacl28_n1025"))        # n = 1025 needs more than 16 MiB
+    ccfg = config_from_workload(cfg, max_particles=4)
+    xyz = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+    Z = torch.ones(4, dtype=torch.float64, device="cuda")
+    st, _ = _gram_noalloc(lib, ccfg, xyz, Z, 5)
+    assert st == _lib.RS_ERR_CAPACITY
+    assert b"16 MiB" in lib.rs_last_error(None)
