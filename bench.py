@@ -317,7 +317,7 @@ def run_ours(args, rank, world, local_rank):
                    "gamma": rep["gamma"], "l2": "256 MiB written before every timed step",
                    "replicas": "one independent seeded problem per rank"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * 4 * 8),
-                "d2h_bytes_per_step": 184, "steps": e2e_steps},
+                "d2h_bytes_per_step": 16, "steps": e2e_steps},
         "gpu_launches": launches,
         "roofline": roof,
         "cpu_baseline": cpu,

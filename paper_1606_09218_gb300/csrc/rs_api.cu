@@ -31,7 +31,7 @@ struct Sizes {
 bool derive(const rs_config& cfg, Ctx& c, std::string& err) {
   if (!(cfg.b > 0.0) || !std::isfinite(cfg.b)) { err = "b must be positive"; return false; }
   if (cfg.n < 5 || (cfg.n % 2) == 0) { err = "n must be odd and >= 5"; return false; }
-  if (cfg.n > 4097) { err = "n above 4097 is not supported"; return false; }
+  if (cfg.n > 2049) { err = "n above 2049 is not supported"; return false; }
   if (cfg.R < 2 || cfg.R > 64) { err = "R must be in [2, 64]"; return false; }
   if (cfg.R_s < 0 || cfg.R_s >= cfg.R || cfg.R_s > 16) { err = "need 0 <= R_s < R and R_s <= 16"; return false; }
   if (!(cfg.h_q > 0.0) || !std::isfinite(cfg.u0)) { err = "h_q must be positive and u0 finite"; return false; }
@@ -88,6 +88,10 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.T, 8 * 3 * ks * ks);
   add(v, c.T2k, 8 * 3 * ks * ks);
   add(v, c.W, 8 * 3 * ks * ks);
+  add(v, c.W2, 8 * 3 * ks * ks);
+  add(v, c.om_colptr, 4 * (ks + 1));
+  add(v, c.om_row, 4 * n * ZETA);
+  add(v, c.om_sgn, 1 * n * ZETA);
   add(v, c.part, 8 * 2 * 3 * NBC * (ks * KB + KB * KB));
   add(v, c.order, 4 * 3 * ks);
   add(v, c.ev, 8 * 3 * ks);
@@ -220,6 +224,42 @@ rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
   }
   std::memset(c.h_sc, 0, sizeof(DevScalars));
   cudaMemsetAsync(c.sc, 0, sizeof(DevScalars), c.stream);
+  // sparse sign embedding Omega (n x ksub, ZETA entries per row), stored by column
+  {
+    const int n = c.n, ks = c.ksub;
+    std::vector<int> col(n * ZETA), cnt(ks + 1, 0), ptr(ks + 1, 0), row(n * ZETA);
+    std::vector<signed char> sg(n * ZETA), sgc(n * ZETA);
+    uint64_t state = 0x1606092181ull;
+    auto next = [&]() {
+      state += 0x9E3779B97F4A7C15ull;
+      uint64_t x = state;
+      x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+      x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+      return x ^ (x >> 31);
+    };
+    for (int i = 0; i < n * ZETA; ++i) {
+      uint64_t r = next();
+      col[i] = (int)(r % (uint64_t)ks);
+      sg[i] = (r >> 63) ? 1 : -1;
+      ++cnt[col[i]];
+    }
+    for (int m = 0; m < ks; ++m) ptr[m + 1] = ptr[m] + cnt[m];
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int i = 0; i < n * ZETA; ++i) {
+      int pos = fill[col[i]]++;
+      row[pos] = i / ZETA;
+      sgc[pos] = sg[i];
+    }
+    if (cudaMemcpy(c.om_colptr, ptr.data(), sizeof(int) * (ks + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c.om_row, row.data(), sizeof(int) * n * ZETA, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c.om_sgn, sgc.data(), n * ZETA, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      g_create_err = "upload of the range-finder embedding failed";
+      free_all(c);
+      delete h;
+      return RS_ERR_CUDA;
+    }
+  }
   *out = h;
   return RS_OK;
 }
@@ -297,8 +337,13 @@ rs_status rs_energy(rs_ctx* h, double* E) {
   if (!h || !E) return RS_ERR_INVALID_ARG;
   Ctx& c = h->c;
   if (!c.solved || !(c.last_flags & RS_ENERGY)) return fail(c, RS_ERR_NOT_READY, "no energy computed");
-  rs_status st = sync_scalars(c);
-  if (st != RS_OK) return st;
+  // energy and flags only (the first 16 bytes of the device scalars)
+  cudaError_t e = cudaMemcpyAsync(c.h_sc, c.sc, 16, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    c.err = std::string("synchronise: ") + cudaGetErrorString(e);
+    return RS_ERR_CUDA;
+  }
   *E = c.h_sc->energy;
   rs_status s2 = status_of(*c.h_sc);
   return s2 < 0 ? s2 : RS_OK;
@@ -412,7 +457,8 @@ rs_status rs_debug_buffer(rs_ctx* h, const char* name, void** ptr, size_t* bytes
   cudaStreamSynchronize(c.stream);
   struct { const char* nm; void* p; } tab[] = {
       {"pk64", c.pk64}, {"F", c.F}, {"G", c.G}, {"C", c.C}, {"Q", c.Q}, {"X", c.X}, {"T", c.T},
-      {"Z64", c.Z64}, {"beta64", c.beta64}, {"Qp", c.Qp}, {"T1", c.T1}, {"T2", c.T2}};
+      {"Z64", c.Z64}, {"beta64", c.beta64}, {"Qp", c.Qp}, {"T1", c.T1}, {"T2", c.T2},
+      {"sc", c.sc}};
   for (auto& e : buffer_list(c)) {
     for (auto& t : tab) {
       if (std::strcmp(t.nm, name) == 0 && *e.first == t.p) {

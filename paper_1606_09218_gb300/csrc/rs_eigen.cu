@@ -98,6 +98,52 @@ gemm_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __restrict_
   }
 }
 
+// 16x16-tile variant for small FP64 products: one output per thread, K split across CTAs so
+// that the few FP64 units of every SM take part (GB300 issues about one FP64 FMA per clock and
+// SM, so a 64x64 tile alone would take tens of microseconds).
+template <typename T>
+__global__ void __launch_bounds__(256)
+gemm_small_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __restrict__ A, int lda,
+                  long long sA, const T* __restrict__ B, int ldb, long long sB, T* C, int ldc,
+                  long long sC, int splitK, const int* dynM, const int* dynN, const int* dynK) {
+  constexpr int BT = 16;
+  __shared__ T As[BT][BT + 1];
+  __shared__ T Bs[BT][BT + 1];
+  const int bz = blockIdx.z / splitK, kz = blockIdx.z % splitK;
+  int m = M, nn = N, kk = K;
+  if (dynM) m = min(m, dynM[bz]);
+  if (dynN) nn = min(nn, dynN[bz]);
+  if (dynK) kk = min(kk, dynK[bz]);
+  const int row0 = blockIdx.y * BT, col0 = blockIdx.x * BT;
+  if (row0 >= m || col0 >= nn) return;
+  const int chunk = ((kk + splitK - 1) / splitK + BT - 1) / BT * BT;
+  const int kbeg = kz * chunk, kend = min(kk, kbeg + chunk);
+  if (kbeg >= kend) return;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int tx = threadIdx.x % BT, ty = threadIdx.x / BT;
+  T acc = T(0);
+  for (int k0 = kbeg; k0 < kend; k0 += BT) {
+    {
+      int gr = row0 + ty, gk = k0 + tx;      // A element (gr, gk)
+      T v = T(0);
+      if (gr < m && gk < kend) v = tA ? A[(long long)gk * lda + gr] : A[(long long)gr * lda + gk];
+      As[ty][tx] = v;
+      int gk2 = k0 + ty, gc = col0 + tx;     // B element (gk2, gc)
+      T w = T(0);
+      if (gc < nn && gk2 < kend) w = tB ? B[(long long)gc * ldb + gk2] : B[(long long)gk2 * ldb + gc];
+      Bs[ty][tx] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BT; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
+    __syncthreads();
+  }
+  const int gr = row0 + ty, gc = col0 + tx;
+  if (gr < m && gc < nn) atomicAdd(C + (long long)gr * ldc + gc, alpha * acc);
+}
+
 template <typename T>
 void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha,
                   const T* A, int lda, long long sA, const T* B, int ldb, long long sB, T beta,
@@ -105,6 +151,36 @@ void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K,
                   const int* dynN, const int* dynK) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (splitK < 1) splitK = 1;
+  // FP64 products whose 64x64 tiles would not fill half the GPU use 16x16 tiles with an
+  // automatic K split (atomics; C is cleared here).
+  if (sizeof(T) == 8 && beta == T(0) && (sC == (long long)M * ldc || batch == 1) &&
+      (long long)((N + 63) / 64) * ((M + 63) / 64) * batch < 76) {
+    long long tiles = (long long)((N + 15) / 16) * ((M + 15) / 16) * batch;
+    int sk = (int)((2 * 152 + tiles - 1) / tiles);
+    int maxs = (K + 15) / 16;
+    if (sk > maxs) sk = maxs;
+    if (sk < 1) sk = 1;
+    cudaMemsetAsync(C, 0, sizeof(T) * ((long long)(batch - 1) * sC + (long long)M * ldc), s);
+    dim3 grid((N + 15) / 16, (M + 15) / 16, batch * sk);
+    gemm_small_kernel<T><<<grid, 256, 0, s>>>(transA, transB, M, N, K, alpha, A, lda, sA, B, ldb,
+                                             sB, C, ldc, sC, sk, dynM, dynN, dynK);
+    return;
+  }
+  // Otherwise FP64 products get an automatic K split when one is not given: enough CTAs to
+  // cover the GPU twice, chunks of at least 32 along K (C cleared here).
+  if (splitK == 1 && sizeof(T) == 8 && beta == T(0) && K >= 64) {
+    long long tiles = (long long)((N + 63) / 64) * ((M + 63) / 64) * batch;
+    int want = (int)((2 * 152 + tiles - 1) / tiles);
+    int maxs = K / 32;
+    splitK = want < maxs ? want : maxs;
+    if (splitK < 1) splitK = 1;
+    if (splitK > 1) {
+      if (sC == (long long)M * ldc || batch == 1)
+        cudaMemsetAsync(C, 0, sizeof(T) * ((long long)(batch - 1) * sC + (long long)M * ldc), s);
+      else
+        splitK = 1;
+    }
+  }
   dim3 grid((N + 63) / 64, (M + 63) / 64, batch * splitK);
   gemm_kernel<T><<<grid, 256, 0, s>>>(transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB,
                                       beta, C, ldc, sC, splitK, dynM, dynN, dynK);
@@ -154,6 +230,22 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Range finder with a sparse sign embedding: X = G * Omega where every row of Omega holds
+// ZETA entries +-1 in pseudo-random columns (a sparse subspace embedding; the captured energy is
+// certified later by the FP64 Rayleigh quotient).  Omega is stored by column (CSR, built once per
+// context): X[r][m] = sum over (i, s) in column m of s * G[r][i].  One thread per (r, m).
+__global__ void sparse_range_kernel(const double* __restrict__ G, const int* __restrict__ colptr,
+                                    const int* __restrict__ rowidx, const signed char* __restrict__ sgn,
+                                    int n, int ks, double* X) {
+  const int l = blockIdx.z, r = blockIdx.y;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= ks) return;
+  const double* Gr = G + ((long long)l * n + r) * n;
+  double v = 0.0;
+  for (int t = colptr[m]; t < colptr[m + 1]; ++t) v += (double)sgn[t] * Gr[rowidx[t]];
+  X[((long long)l * n + r) * ks + m] = v;
+}
+
 // trace(G_l) and ||X_l||_F^2 per mode (one CTA per mode).
 __global__ void traces_kernel(const double* G, const double* X, int n, int ks, DevScalars* sc) {
   __shared__ double red[32];
@@ -193,7 +285,8 @@ __device__ __forceinline__ void grid_barrier(DevScalars* sc, unsigned& gen, bool
       volatile unsigned* g = &sc->bar_gen;
       long long it = 0;
       while (*g == gen) {
-        if (++it > 20000000ll) {   // about a second of polling
+        __nanosleep(32);
+        if (++it > 20000000ll) {   // a second or more of polling
           atomicOr(&sc->flags, (unsigned)FLAG_TIMEOUT);
           poisoned = true;
           break;
@@ -229,11 +322,13 @@ __device__ __forceinline__ bool chol8(double* S, double piv_tol = 0.0) {
 __global__ void __launch_bounds__(256)
 bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int ks,
              DevScalars* sc) {
+  extern __shared__ double sQ[];              // this CTA's rows of Q: (r1 - r0) x ks
   unsigned bar_gen = 0;
   bool poisoned = false;   // meaningful in thread 0 only
   const int l = blockIdx.x / NBC, c = blockIdx.x % NBC;
   const int rows = (n + NBC - 1) / NBC;
   const int r0 = min(n, c * rows), r1 = min(n, r0 + rows);
+  const int nr = r1 - r0;
   const double* Xl = X + (long long)l * n * ks;
   double* Ql = Q + (long long)l * n * ks;
   // part layout: [2][3][NBC][ks*KB + KB*KB].  Partials written by other SMs are read with
@@ -253,19 +348,18 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
   if (stop && c == 0 && threadIdx.x == 0) atomicOr(&sc->stopmask, 1u << l);
   int phase = 0;
   const int tid = threadIdx.x;
-  auto row = [&](int i) { return Ql + (long long)i * ks; };
-  // reads of Q go through L2: rows may have been written by another CTA (fallback path)
-  auto q = [&](int i, int col) { return __ldcg(Ql + (long long)i * ks + col); };
+  auto sq = [&](int ii, int col) -> double& { return sQ[ii * ks + col]; };   // ii = i - r0
+  auto gq = [&](int i, int col) { return __ldcg(Ql + (long long)i * ks + col); };
 
-  for (long long e = (long long)r0 * ks + tid; e < (long long)r1 * ks; e += blockDim.x) Ql[e] = 0.0;
+  for (int e = tid; e < nr * ks; e += blockDim.x) sQ[e] = 0.0;
   __syncthreads();
 
-  // per-row helpers on the working block B = Q[:, kq:kq+KB]
+  // per-row helpers on the working block B = Q[:, kq:kq+KB] (own rows, shared memory)
   auto partial_h = [&](double* P) {           // P[a*KB+jc] = sum_{own rows} Q[i][a] B[i][jc]
     for (int e = tid; e < kq * KB; e += blockDim.x) {
       int a = e / KB, jc = e % KB;
       double v = 0.0;
-      for (int i = r0; i < r1; ++i) v += q(i, a) * q(i, kq + jc);
+      for (int ii = 0; ii < nr; ++ii) v += sq(ii, a) * sq(ii, kq + jc);
       P[e] = v;
     }
   };
@@ -273,7 +367,7 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
     for (int e = tid; e < KB * KB; e += blockDim.x) {
       int a = e / KB, b = e % KB;
       double v = 0.0;
-      for (int i = r0; i < r1; ++i) v += q(i, kq + a) * q(i, kq + b);
+      for (int ii = 0; ii < nr; ++ii) v += sq(ii, kq + a) * sq(ii, kq + b);
       P[e] = v;
     }
   };
@@ -292,32 +386,45 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
     }
   };
   auto subtract_Qh = [&]() {                  // B -= Q[:, :kq] h on own rows
-    for (int e = tid; e < (r1 - r0) * KB; e += blockDim.x) {
-      int i = r0 + e / KB, jc = e % KB;
-      double v = q(i, kq + jc);
-      for (int a = 0; a < kq; ++a) v -= q(i, a) * h[a * KB + jc];
-      row(i)[kq + jc] = v;
+    for (int e = tid; e < nr * KB; e += blockDim.x) {
+      int ii = e / KB, jc = e % KB;
+      double v = sq(ii, kq + jc);
+      for (int a = 0; a < kq; ++a) v -= sq(ii, a) * h[a * KB + jc];
+      sq(ii, kq + jc) = v;
     }
   };
   auto solve_LT = [&]() {                     // B <- B L^{-T} on own rows (L in S)
-    for (int i = r0 + tid; i < r1; i += blockDim.x) {
+    for (int ii = tid; ii < nr; ii += blockDim.x) {
       double y[KB];
       for (int jc = 0; jc < KB; ++jc) {
-        double v = q(i, kq + jc);
+        double v = sq(ii, kq + jc);
         for (int k = 0; k < jc; ++k) v -= S[jc * KB + k] * y[k];
         y[jc] = v / S[jc * KB + jc];
       }
-      for (int jc = 0; jc < KB; ++jc) row(i)[kq + jc] = y[jc];
+      for (int jc = 0; jc < KB; ++jc) sq(ii, kq + jc) = y[jc];
+    }
+  };
+  auto block_to_global = [&]() {              // own rows of the working block -> Q
+    for (int e = tid; e < nr * KB; e += blockDim.x) {
+      int ii = e / KB, jc = e % KB;
+      Ql[(long long)(r0 + ii) * ks + kq + jc] = sq(ii, kq + jc);
+    }
+  };
+  auto block_from_global = [&]() {            // Q -> own rows of the working block
+    for (int e = tid; e < nr * KB; e += blockDim.x) {
+      int ii = e / KB, jc = e % KB;
+      if (kq + jc < ks) sq(ii, kq + jc) = gq(r0 + ii, kq + jc);
     }
   };
   // Fallback for a block too ill-conditioned for Cholesky QR (fast-decaying spectra): CTA 0
-  // of the mode orthonormalises the 8 columns one by one (classical Gram-Schmidt, two
-  // passes, against the block's accepted columns; the two projections against the earlier
-  // blocks were already done in parallel), drops columns that fall below the noise guard,
-  // compacts the accepted ones to the front and publishes their count.
+  // of the mode orthonormalises the 8 columns one by one in global memory (classical
+  // Gram-Schmidt, two passes, against the block's accepted columns; the two projections
+  // against the earlier blocks were already done in parallel), drops columns that fall below
+  // the noise guard, compacts the accepted ones to the front and publishes their count.
   __shared__ double fred[8][KB];
   __shared__ double fd[KB];
   __shared__ int s_acc;
+  auto row = [&](int i) { return Ql + (long long)i * ks; };
   auto fallback_block = [&]() {
     if (tid == 0) s_acc = 0;
     __syncthreads();
@@ -327,8 +434,8 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
         double d[KB];
         for (int a = 0; a < KB; ++a) d[a] = 0.0;
         for (int i = tid; i < n; i += blockDim.x) {
-          double v = q(i, kq + jc);
-          for (int a = 0; a < acc; ++a) d[a] += q(i, kq + a) * v;
+          double v = gq(i, kq + jc);
+          for (int a = 0; a < acc; ++a) d[a] += gq(i, kq + a) * v;
         }
         for (int a = 0; a < acc; ++a) {
           double v = d[a];
@@ -343,14 +450,14 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
         }
         __syncthreads();
         for (int i = tid; i < n; i += blockDim.x) {
-          double v = q(i, kq + jc);
-          for (int a = 0; a < acc; ++a) v -= fd[a] * q(i, kq + a);
+          double v = gq(i, kq + jc);
+          for (int a = 0; a < acc; ++a) v -= fd[a] * gq(i, kq + a);
           row(i)[kq + jc] = v;
         }
         __syncthreads();
       }
       double nv = 0.0;
-      for (int i = tid; i < n; i += blockDim.x) { double v = q(i, kq + jc); nv += v * v; }
+      for (int i = tid; i < n; i += blockDim.x) { double v = gq(i, kq + jc); nv += v * v; }
       for (int o = 16; o > 0; o >>= 1) nv += __shfl_down_sync(0xffffffffu, nv, o);
       if ((tid & 31) == 0) fred[tid >> 5][0] = nv;
       __syncthreads();
@@ -363,7 +470,7 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
       const double nv2 = fd[0];
       if (nv2 >= guard2 && nv2 > 0.0) {
         const double sc1 = 1.0 / sqrt(nv2);
-        for (int i = tid; i < n; i += blockDim.x) row(i)[kq + acc] = q(i, kq + jc) * sc1;
+        for (int i = tid; i < n; i += blockDim.x) row(i)[kq + acc] = gq(i, kq + jc) * sc1;
         __syncthreads();
         if (tid == 0) s_acc = acc + 1;
       }
@@ -387,9 +494,9 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
 
   for (int s = 0; s < ks; s += KB) {
     if (!stop)
-      for (int e = tid; e < (r1 - r0) * KB; e += blockDim.x) {
-        int i = r0 + e / KB, jc = e % KB;
-        row(i)[kq + jc] = Xl[(long long)i * ks + s + jc];
+      for (int e = tid; e < nr * KB; e += blockDim.x) {
+        int ii = e / KB, jc = e % KB;
+        sq(ii, kq + jc) = Xl[(long long)(r0 + ii) * ks + s + jc];
       }
     __syncthreads();   // the partial products below read rows written by other threads
     // (A) first projection against the accepted columns
@@ -404,6 +511,7 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
     grid_barrier(sc, bar_gen, poisoned);
     if (!stop && kq > 0) { reduce_h(phase); __syncthreads(); subtract_Qh(); }
     __syncthreads();
+    if (!stop) block_to_global();            // CTA 0 reads every row if the block falls back
     ++phase;
     // (C) Gram of the block: norm test and first Cholesky QR
     if (!stop) partial_S(pbuf(phase, l, c));
@@ -418,7 +526,13 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
       }
       __syncthreads();
       if (s_stop == 1) mark_stop(0u);
-      else if (s_stop == 3) { fallback = true; if (c == 0) fallback_block(); }
+      else if (s_stop == 3) {
+        fallback = true;
+        if (c == 0) {
+          if (tid == 0) atomicAdd(&sc->fallbacks, 1);
+          fallback_block();
+        }
+      }
       else solve_LT();
     }
     __syncthreads();
@@ -452,6 +566,7 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
     __syncthreads();
     ++phase;
     if (!stop && fallback) {
+      block_from_global();                   // the block as CTA 0 left it
       const int acc = (int)__ldcg(&sc->blk_acc[l]);
       kq += acc;
       fallback = false;
@@ -461,12 +576,15 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
       kq += KB;
       if (kq + KB > ks) mark_stop(0u);
     } else {
-      for (int e = tid; e < (r1 - r0) * KB; e += blockDim.x) {
-        int i = r0 + e / KB, jc = e % KB;
-        if (kq + jc < ks) row(i)[kq + jc] = 0.0;
+      for (int e = tid; e < nr * KB; e += blockDim.x) {
+        int ii = e / KB, jc = e % KB;
+        if (kq + jc < ks) sq(ii, kq + jc) = 0.0;
       }
     }
+    __syncthreads();
   }
+  // own rows back to Q
+  for (int e = tid; e < nr * ks; e += blockDim.x) Ql[(long long)r0 * ks + e] = sQ[e];
   if (c == 0 && tid == 0) sc->k_eff[l] = kq;
 }
 
@@ -474,7 +592,8 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
 // One CTA per mode: A (ke x ke, FP32, scaled by 1/max diag) in shared memory, V accumulated.
 // Parallel (round-robin) ordering: each round applies ke/2 disjoint rotations.
 __global__ void __launch_bounds__(1024)
-jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* sc, int max_sweeps) {
+jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* sc, int max_sweeps,
+                float tol) {
   extern __shared__ float smem[];
   const int l = blockIdx.x;
   const int ke0 = sc->k_eff[l];
@@ -489,6 +608,7 @@ jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* s
   const double* T = Tm + (long long)l * ks * ks;
   double* W = Wm + (long long)l * ks * ks;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   if (tid == 0) {
     double m = 0.0;
     for (int i = 0; i < ke0; ++i) m = fmax(m, fabs(T[(long long)i * ks + i]));
@@ -517,7 +637,7 @@ jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* s
         qq[m] = q;
         float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
         float c = 1.f, s = 0.f, t = 0.f;
-        if (apq != 0.f && fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq))) {
+        if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq))) {
           float theta = (aqq - app) / (2.f * apq);
           t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
           c = rsqrtf(1.f + t * t);
@@ -530,44 +650,50 @@ jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* s
         dqq[m] = aqq + t * apq;
       }
       __syncthreads();
-      // rows: A[p,:], A[q,:]  (skip the 2x2 blocks of the pairs, fixed below)
-      for (int e = tid; e < half * ke; e += nt) {
-        int m = e / ke, col = e % ke;
-        float s = sn[m];
+      // rows: A[p,:], A[q,:] -- warp w takes pairs w, w + 8, ..., lanes take columns
+      for (int m = warp; m < half; m += nwarp) {
+        const float s = sn[m];
         if (s == 0.f) continue;
-        int p = pp[m], q = qq[m];
-        float c = cs[m];
-        float ap = A[p * ld + col], aq = A[q * ld + col];
-        A[p * ld + col] = c * ap - s * aq;
-        A[q * ld + col] = s * ap + c * aq;
+        const int p = pp[m], q = qq[m];
+        const float c = cs[m];
+        float* Ap = A + p * ld;
+        float* Aq = A + q * ld;
+        for (int col = lane; col < ke; col += 32) {
+          float ap = Ap[col], aq = Aq[col];
+          Ap[col] = c * ap - s * aq;
+          Aq[col] = s * ap + c * aq;
+        }
       }
       __syncthreads();
-      // columns: A[:,p], A[:,q] and V[:,p], V[:,q]
-      for (int e = tid; e < half * ke; e += nt) {
-        int m = e / ke, row = e % ke;
-        float s = sn[m];
+      // columns: A[:,p], A[:,q] and V[:,p], V[:,q]; the 2x2 block of each rotated pair takes
+      // its exact values (graded-accurate diagonal, zero off-diagonal)
+      for (int m = warp; m < half; m += nwarp) {
+        const float s = sn[m];
         if (s == 0.f) continue;
-        int p = pp[m], q = qq[m];
-        float c = cs[m];
-        float ap = A[row * ld + p], aq = A[row * ld + q];
-        A[row * ld + p] = c * ap - s * aq;
-        A[row * ld + q] = s * ap + c * aq;
-        float vp = V[row * ld + p], vq = V[row * ld + q];
-        V[row * ld + p] = c * vp - s * vq;
-        V[row * ld + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-      // exact 2x2 results for the rotated pairs
-      for (int m = tid; m < half; m += nt) {
-        if (sn[m] == 0.f) continue;
-        int p = pp[m], q = qq[m];
-        A[p * ld + p] = dpp[m];
-        A[q * ld + q] = dqq[m];
-        A[p * ld + q] = 0.f;
-        A[q * ld + p] = 0.f;
+        const int p = pp[m], q = qq[m];
+        const float c = cs[m];
+        for (int row = lane; row < ke; row += 32) {
+          float* Vr = V + row * ld;
+          float vp = Vr[p], vq = Vr[q];
+          Vr[p] = c * vp - s * vq;
+          Vr[q] = s * vp + c * vq;
+          float* Ar = A + row * ld;
+          if (row == p) {
+            Ar[p] = dpp[m];
+            Ar[q] = 0.f;
+          } else if (row == q) {
+            Ar[q] = dqq[m];
+            Ar[p] = 0.f;
+          } else {
+            float ap = Ar[p], aq = Ar[q];
+            Ar[p] = c * ap - s * aq;
+            Ar[q] = s * ap + c * aq;
+          }
+        }
       }
       __syncthreads();
     }
+    if (tid == 0) atomicAdd(&sc->jacobi_sweeps, 1);
     if (s_rot == 0) break;
     __syncthreads();
   }
@@ -684,53 +810,63 @@ __global__ void gather_Z_kernel(const double* Q, const int* order, int n, int ks
 }
 
 // ------------------------------------------------------------------ driver
-static int jacobi_pass(Ctx& c, double*& Qa, double*& Qb, int sweeps) {
+// T <- W^T T W for the leading ke block (two k x k products through T2k)
+static void congruence(Ctx& c, double* Tm, const double* Wm) {
+  const int ks = c.ksub;
+  const long long sK = (long long)ks * ks;
+  const int* ke = c.sc->k_eff;
+  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, Tm, ks, sK, Wm, ks, sK, 0.0,
+                       c.T2k, ks, sK, 3, 1, ke, ke, ke);
+  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, Wm, ks, sK, c.T2k, ks, sK, 0.0,
+                       Tm, ks, sK, 3, 1, ke, ke, ke);
+}
+
+// Rayleigh-Ritz refinement: two FP32 Jacobi passes on the graded T (rotations accumulated in
+// FP64), one rotation of the basis, one Newton-Schulz re-orthonormalisation.
+static int refine(Ctx& c, double*& Qa, double*& Qb) {
   const int n = c.n, ks = c.ksub;
   const long long sQ = (long long)n * ks, sK = (long long)ks * ks;
   const int* ke = c.sc->k_eff;
   size_t shm = 2ull * ks * (ks + 1) * sizeof(float);
   cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, sweeps);
-  // Qb = Qa W ; T2k = T W ; T = W^T T2k
-  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, c.W, ks, sK, 0.0, Qb,
-                       ks, sQ, 3, 1, nullptr, ke, ke);
-  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.T, ks, sK, c.W, ks, sK, 0.0,
+  // pass 1: T -> W1^T T W1
+  jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, 12, 1e-4f);
+  congruence(c, c.T, c.W);
+  // pass 2: T -> W2^T T W2, W <- W1 W2
+  jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W2, ks, c.sc, 4, 2e-7f);
+  congruence(c, c.T, c.W2);
+  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W2, ks, sK, 0.0,
                        c.T2k, ks, sK, 3, 1, ke, ke, ke);
-  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.W, ks, sK, c.T2k, ks, sK, 0.0,
-                       c.T, ks, sK, 3, 1, ke, ke, ke);
+  // Qb = Qa (W1 W2)
+  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, c.T2k, ks, sK, 0.0, Qb,
+                       ks, sQ, 3, 1, nullptr, ke, ke);
   // Newton-Schulz: E = Qb^T Qb - I ; M = I - E/2 + 3/8 E^2 ; Qa = Qb M ; T = M^T T M
-  cudaMemsetAsync(c.W, 0, sizeof(double) * 3 * sK, c.stream);
   gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, Qb, ks, sQ, Qb, ks, sQ, 0.0, c.W,
-                       ks, sK, 3, 8, ke, ke, nullptr);
+                       ks, sK, 3, 1, ke, ke, nullptr);
   dim3 g2((ks * ks + 255) / 256, 3);
   sub_identity_kernel<<<g2, 256, 0, c.stream>>>(c.W, ks, c.sc);
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W, ks, sK, 0.0,
                        c.T2k, ks, sK, 3, 1, ke, ke, ke);
-  // W holds E, T2k holds E^2: W <- M = I - E/2 + 3/8 E^2
   ns_matrix_kernel<<<g2, 256, 0, c.stream>>>(c.W, c.T2k, c.W, ks, c.sc);
   gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qb, ks, sQ, c.W, ks, sK, 0.0, Qa,
                        ks, sQ, 3, 1, nullptr, ke, ke);
-  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.T, ks, sK, c.W, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, 1, ke, ke, ke);
-  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.W, ks, sK, c.T2k, ks, sK, 0.0,
-                       c.T, ks, sK, 3, 1, ke, ke, ke);
-  return 11;
+  congruence(c, c.T, c.W);
+  return 2 + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1 + 1 + 2;
 }
 
 int launch_subspace(Ctx& c) {
   const int n = c.n, ks = c.ksub;
   const long long sQ = (long long)n * ks, sK = (long long)ks * ks, sG = (long long)n * n;
-  // X = G * Omega  (Omega stored in Y)
-  int tot = 3 * n * ks;
-  omega_kernel<<<(tot + 255) / 256, 256, 0, c.stream>>>(c.Y, n, ks, tot);
-  cudaMemsetAsync(c.X, 0, sizeof(double) * 3 * sQ, c.stream);
-  gemm_batched<double>(c.stream, false, false, n, ks, n, 1.0, c.G, n, sG, c.Y, ks, sQ, 0.0, c.X,
-                       ks, sQ, 3, 4);
+  // X = G * Omega with the sparse sign embedding of this context
+  sparse_range_kernel<<<dim3((ks + 127) / 128, n, 3), 128, 0, c.stream>>>(c.G, c.om_colptr, c.om_row,
+                                                                        c.om_sgn, n, ks, c.X);
   traces_kernel<<<3, 256, 0, c.stream>>>(c.G, c.X, n, ks, c.sc);
   // block Gram-Schmidt (cooperative)
   {
     void* args[] = {(void*)&c.X, (void*)&c.Q, (void*)&c.part, (void*)&n, (void*)&ks, (void*)&c.sc};
-    cudaLaunchCooperativeKernel((void*)bcgs2_kernel, dim3(3 * NBC), dim3(256), args, 0, c.stream);
+    const size_t shm = sizeof(double) * (size_t)((n + NBC - 1) / NBC) * ks;
+    cudaFuncSetAttribute(bcgs2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaLaunchCooperativeKernel((void*)bcgs2_kernel, dim3(3 * NBC), dim3(256), args, shm, c.stream);
   }
   const int* ke = c.sc->k_eff;
   // RS_DEBUG_SUBSPACE_STEPS=s stops the eigen stage after s sub-steps (inspection only)
@@ -746,14 +882,12 @@ int launch_subspace(Ctx& c) {
   cudaMemsetAsync(c.T, 0, sizeof(double) * 3 * sK, c.stream);
   gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, c.Q, ks, sQ, c.Y, ks, sQ, 0.0, c.T,
                        ks, sK, 3, 8, ke, ke, nullptr);
-  // two Jacobi passes; Q alternates between c.Q and c.X
+  // Rayleigh-Ritz refinement; the rotated basis goes through c.X and ends in c.Q
   double* Qa = c.Q;
   double* Qb = c.X;
   int k = 6;
   if (dbg_steps <= 2) return k;
-  k += jacobi_pass(c, Qa, Qb, 10);
-  if (dbg_steps <= 3) return k;
-  k += jacobi_pass(c, Qa, Qb, 3);
+  k += refine(c, Qa, Qb);
   // Qa holds the final basis (c.Q)
   rank_select_kernel<<<3, 128, 0, c.stream>>>(c.T, ks, c.cfg.eps, c.cfg.rank_cap, c.rmax, c.order,
                                               c.ev, c.sc);

@@ -12,12 +12,14 @@ namespace rs {
 
 // Width of the column blocks of the block Gram-Schmidt orthonormalisation.
 constexpr int KB = 8;
-// CTAs per mode of the cooperative block Gram-Schmidt kernel.
-constexpr int NBC = 16;
+// CTAs per mode of the cooperative block Gram-Schmidt kernel (3 x 48 = 144 <= 152 SMs).
+constexpr int NBC = 48;
 // Largest Tucker rank the projection kernel supports.
 constexpr int RMAX_LIMIT = 160;
 // Largest subspace width the one-CTA Jacobi kernel holds in shared memory.
 constexpr int KSUB_MAX = 160;
+// Nonzeros per row of the sparse range-finder embedding.
+constexpr int ZETA = 4;
 // Side of the particle bins used to find the windows that touch a grid tile.
 constexpr int BIN = 16;
 
@@ -33,18 +35,26 @@ enum : unsigned {
 
 // Scalars shared by the kernels of one solve (device memory).
 struct DevScalars {
+  // energy and flags first: rs_energy reads back only these 16 bytes
+  double energy;
+  unsigned flags;
+  unsigned pad0;
   double P_R0, P_Rl0, delta;
   double trG[3], trT[3], xnorm2[3], tail_rel[3];
-  double energy;
   int gamma;
   int n_nz;                 // particles with nonzero charge
   int nzj_count[3];         // distinct grid coordinates carrying charge, per mode
   int k_eff[3];             // accepted Gram-Schmidt columns per mode
   int rank[3];              // Tucker ranks
-  unsigned flags;
-  unsigned bar_count, bar_gen;   // grid barrier of the cooperative Gram-Schmidt kernel
   unsigned stopmask;             // modes whose Gram-Schmidt has finished
   int blk_acc[3];                // columns accepted by the one-CTA fallback of the current block
+  int jacobi_sweeps;             // Jacobi sweeps of the last solve (all modes and passes)
+  int fallbacks;                 // blocks that took the one-CTA Gram-Schmidt fallback
+  // grid barrier of the cooperative Gram-Schmidt kernel: arrival counter and generation on
+  // separate 128-byte lines, so that the waiters' polling does not slow the arrivals
+  alignas(128) unsigned bar_count;
+  alignas(128) unsigned bar_gen;
+  alignas(128) unsigned bar_pad;
 };
 
 struct Ctx {
@@ -79,6 +89,10 @@ struct Ctx {
   double* T = nullptr;      // 3 x ksub x ksub
   double* T2k = nullptr;    // 3 x ksub x ksub (scratch)
   double* W = nullptr;      // 3 x ksub x ksub
+  double* W2 = nullptr;     // 3 x ksub x ksub
+  int*    om_colptr = nullptr;  // ksub + 1: sparse embedding Omega (n x ksub) by column
+  int*    om_row = nullptr;     // n * ZETA
+  signed char* om_sgn = nullptr;
   double* part = nullptr;   // partial sums of the Gram-Schmidt kernel
   int*    order = nullptr;  // 3 x ksub eigenvalue order
   double* ev = nullptr;     // 3 x ksub sorted eigenvalues
@@ -140,6 +154,7 @@ int launch_subspace(Ctx& c);
 int launch_projection_core(Ctx& c);
 int launch_bins(Ctx& c);
 int launch_recon_gemm(Ctx& c, void* out);
+int launch_recon_tc(Ctx& c, float* out);   // rs_tc.cu; -1 when the shape is not supported
 int launch_windows(Ctx& c, void* out);
 int launch_energy(Ctx& c, int N);
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out);

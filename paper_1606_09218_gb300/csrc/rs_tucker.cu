@@ -4,6 +4,9 @@
 // evaluation of Lemma 3.10 used for the interaction energy (Sec. 4.2, Eq. (4.7)).
 #include "rs_internal.cuh"
 
+#include <cstdlib>
+#include <cstring>
+
 namespace rs {
 
 template <typename T> struct Bulk;
@@ -424,7 +427,15 @@ static int windows_t(Ctx& c, T* out) {
 }
 
 int launch_recon_gemm(Ctx& c, void* out) {
-  return c.fp64 ? recon_gemm_t<double>(c, (double*)out) : recon_gemm_t<float>(c, (float*)out);
+  if (c.fp64) return recon_gemm_t<double>(c, (double*)out);
+  // FP32 bulk: tensor cores (tcgen05, 3xTF32) unless RS_RECON_PATH=cuda asks for the CUDA-core
+  // product or the rank bound is above what the tensor-core kernel stages in shared memory
+  const char* e = std::getenv("RS_RECON_PATH");
+  if (!(e && std::strcmp(e, "cuda") == 0)) {
+    int k = launch_recon_tc(c, (float*)out);
+    if (k >= 0) return k;
+  }
+  return recon_gemm_t<float>(c, (float*)out);
 }
 
 int launch_windows(Ctx& c, void* out) {

@@ -2,10 +2,11 @@
 seeded inputs.
 
 Tolerances (relative Frobenius norms unless stated):
-* same ranks, FP64 path vs the oracle's RS-Tucker tensor: 1e-7 (the two eigensolvers agree
-  on the retained subspaces to ~1e-8; rounding of the FP64 contractions is ~1e-14);
-* same ranks, FP32 path vs the oracle's RS-Tucker tensor: 1e-6 (FP32 products, FP64-combined
-  chunk sums in the core, FP32 storage of the output: ~1e-7 per stage);
+* same ranks, against the oracle's RS-Tucker tensor: both long-range parts lie within
+  eps*||P_l|| of the untruncated P_l, and directions near the rank cut may mix differently in
+  the two eigensolvers, so they agree within 2*eps*||P_l|| (relative to the grid) plus rounding:
+  1e-9 for FP64, 1e-6 for FP32 (FP32 products, FP64-combined chunk sums in the core, FP32
+  output);
 * against the full-rank canonical sum P_0 of the oracle: eps * ||P_l|| / ||P_0|| (Tucker
   truncation) + the window cut-off (each window loses at most delta*|z| per point) + the
   rounding budget above;
@@ -39,6 +40,11 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def same_rank_tol(cfg, Pl, ref, rounding):
+    """2*eps*||P_l|| / ||ref|| + rounding (see the module docstring)."""
+    return 2 * cfg["eps"] * float(np.linalg.norm(Pl)) / float(np.linalg.norm(ref)) + rounding
+
+
 @pytest.fixture(scope="module")
 def c1():
     cfg = dict(load_config("c1_box64_n129"))
@@ -59,10 +65,10 @@ def test_c1_fp64_grid_matches_oracle_rs_tucker(c1):
     assert abs(rep["P_R0"] - pr.PR0) <= 1e-13 * pr.PR0
     Z0s, beta, _, _, _, _ = pr.tucker(ranks=rep["ranks"])
     ref = O.tucker_full(beta, Z0s) + pr.windows_grid()
-    assert _rel(P, ref) < 1e-7
-    # against the untruncated canonical sum P_0
     P0 = pr.P0_grid()
     Pl = pr.Pl_grid()
+    assert _rel(P, ref) < same_rank_tol(cfg, Pl, ref, 1e-9)
+    # against the untruncated canonical sum P_0
     bound = cfg["eps"] * np.linalg.norm(Pl) / np.linalg.norm(P0) + \
         pr.delta * np.sum(np.abs(pr.z)) * np.sqrt(P0.size) / np.linalg.norm(P0) + 1e-9
     assert _rel(P, P0) <= bound
@@ -85,6 +91,7 @@ def test_c1_rank_cap_reports_and_matches(c1):
     assert rep["status"] == 1 and rep["ranks"] == [16, 16, 16]
     Z0s, beta, _, _, _, _ = pr.tucker(ranks=[16, 16, 16])
     ref = O.tucker_full(beta, Z0s) + pr.windows_grid()
+    # at the cap the retained energy is ~1e-4 of the tail, far from the mixing regime
     assert _rel(ctx.potential.cpu().numpy(), ref) < 1e-7
     ctx.close()
 
@@ -122,8 +129,13 @@ def test_small_random_problems(prec):
         rep = ctx.report()
         Z0s, beta, _, _, _, _ = pr.tucker(ranks=rep["ranks"])
         ref = O.tucker_full(beta, Z0s) + pr.windows_grid()
-        tol = 1e-7 if prec == "fp64" else 1e-6
+        tol = same_rank_tol(cfg, pr.Pl_grid(), ref, 1e-9 if prec == "fp64" else 1e-6)
         assert _rel(ctx.potential.double().cpu().numpy(), ref) < tol, (n, N)
+        P0 = pr.P0_grid()
+        bound = cfg["eps"] * np.linalg.norm(pr.Pl_grid()) / np.linalg.norm(P0) + \
+            pr.delta * np.sum(np.abs(pr.z)) * np.sqrt(P0.size) / np.linalg.norm(P0) + \
+            (1e-9 if prec == "fp64" else 1e-6)
+        assert _rel(ctx.potential.double().cpu().numpy(), P0) <= bound, (n, N)
         A = O.tucker_points(beta, Z0s, pr.j) + pr.windows_points(pr.j)
         Eref = O.energy_from_potential(A, pr.z, pr.PR0)
         assert abs(ctx.energy() - Eref) <= (1e-8 if prec == "fp64" else 1e-6) * O.energy_scale(pr.xyz_snapped, pr.z)
@@ -163,7 +175,7 @@ def test_edge_cases_empty_zero_and_single():
     rep = ctx.report()
     Z0s, beta, _, _, _, _ = pr.tucker(ranks=rep["ranks"])
     ref = O.tucker_full(beta, Z0s) + pr.windows_grid()
-    assert _rel(ctx.potential.cpu().numpy(), ref) < 1e-7
+    assert _rel(ctx.potential.cpu().numpy(), ref) < same_rank_tol(cfg, pr.Pl_grid(), ref, 1e-9)
     Eref = O.energy_from_potential(O.tucker_points(beta, Z0s, pr.j) + pr.windows_points(pr.j), pr.z, pr.PR0)
     assert abs(ctx.energy() - Eref) <= 1e-9 * pr.PR0 * Z[0] ** 2
     # host input path gives the same result (FP64 split-K sums use atomics, so the summation
@@ -221,4 +233,32 @@ def test_c2_full_size_sampled_against_canonical_sum():
     E = ctx.energy()
     scale = O.energy_scale(pr.xyz_snapped, pr.z)
     assert abs(E - pr.energy_P0()) <= 3e-6 * scale
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["c2_protein1000_n513"])
+def test_tensor_core_reconstruction_matches_cuda_core_path(name, monkeypatch):
+    """The tcgen05 (3xTF32) last mode product against the FP32 CUDA-core product on the same
+    solve: both approximate the same FP32 contraction; the split products keep the difference at
+    the 1e-7 level (well inside the 1e-6 parity budget)."""
+    cfg = load_config(name)
+    p = make_particles(cfg)
+    xyz = torch.tensor(p.xyz, device="cuda")
+    Z = torch.tensor(p.Z, device="cuda")
+    ctx = _ctx(cfg, len(p.Z))
+    monkeypatch.setenv("RS_RECON_PATH", "cuda")
+    ctx.solve(xyz, Z, energy=False)
+    ref = ctx.potential.clone()
+    monkeypatch.setenv("RS_RECON_PATH", "tc")
+    ctx.solve(xyz, Z, energy=False)
+    torch.cuda.synchronize()
+    assert ctx.report()["status"] == 0
+    P = ctx.potential
+    d = float((P.double() - ref.double()).norm() / ref.double().norm())
+    assert d < 1e-6, d
+    # spot values at the grid corners and the last (ragged) row and column
+    n = ref.shape[0]
+    for i in ((0, 0, 0), (n - 1, n - 1, n - 1), (n - 1, 0, n - 1), (127, 255, 256), (128, 300, 5)):
+        a, b = float(P[i]), float(ref[i])
+        assert abs(a - b) <= 1e-5 * max(1.0, abs(b)), (i, a, b)
     ctx.close()
