@@ -59,6 +59,8 @@ bool derive(const rs_config& cfg, Ctx& c, std::string& err) {
   c.rmax = want < ks ? want : ks;
   c.nbin = (cfg.n + BIN - 1) / BIN;
   c.maxN = cfg.max_particles;
+  c.t2_ld = cfg.n;
+  c.use_tc = plan_assemble(c);             // may pad t2_ld for the TMA view of T2
   return true;
 }
 
@@ -101,7 +103,7 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.beta64, 8 * rm * rm * rm);
   add(v, c.beta, ts * rm * rm * rm);
   add(v, c.T1, ts * rm * rm * n);
-  add(v, c.T2, ts * rm * n * n);
+  add(v, c.T2, ts * rm * n * (size_t)c.t2_ld);
   add(v, c.bin_count, 4 * (nbins + 1));
   add(v, c.bin_start, 4 * (nbins + 1));
   add(v, c.bin_items, 4 * N);
@@ -109,6 +111,14 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.adims, 4 * rm);
   add(v, c.kdims, 4 * rm);
   add(v, c.sc, sizeof(DevScalars));
+  if (c.use_tc) {
+    const size_t nT = (size_t)c.tc_nt2 * c.tc_nt3;
+    add(v, c.wl_count, 4 * (nT + 1));
+    add(v, c.wl_start, 4 * (nT + 1));
+    add(v, c.wl_key, 8 * (size_t)c.wl_cap);
+    add(v, c.wl_rec, 16 * (size_t)c.wl_cap);
+    add(v, c.wl_rng, 8 * nT * c.tc_nch);
+  }
   return v;
 }
 
@@ -259,6 +269,12 @@ rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
       delete h;
       return RS_ERR_CUDA;
     }
+  }
+  if (c.use_tc) {
+    // the tensor-core assembly needs the TMA descriptor of T2; without it the CUDA-core
+    // product and window kernels serve (they accept the padded T2 rows)
+    std::string terr;
+    if (!encode_t2_map(c, terr)) c.use_tc = false;
   }
   *out = h;
   return RS_OK;

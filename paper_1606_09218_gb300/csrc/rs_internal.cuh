@@ -1,6 +1,7 @@
 // Internal declarations of the RS library (CUDA path only).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
@@ -30,7 +31,7 @@ enum : unsigned {
   FLAG_RANK_CAPPED = 4u,  // eps not met within the rank limit
   FLAG_CHOL = 8u,         // a Cholesky factor of a Gram-Schmidt block was not positive
   FLAG_TIMEOUT = 16u,     // a bounded grid-barrier wait ran out
-  FLAG_WINDOWS = 32u      // more than 256 windows per round reached one output tile
+  FLAG_WINDOWS = 32u      // a window list outgrew its capacity (see the list builders)
 };
 
 // Scalars shared by the kernels of one solve (device memory).
@@ -109,6 +110,22 @@ struct Ctx {
   double* Epart = nullptr;      // energy partial sums
   int*    adims = nullptr;      // rmax: per-batch row counts of the mode-2 product
   int*    kdims = nullptr;      // rmax: per-batch inner sizes of the mode-2 product
+  // tensor-core assembly of the FP32 output (rs_tc.cu), planned at create
+  bool use_tc = false;
+  int t2_ld = 0;                // i3 stride of T2 (n, or n rounded up to 4 for the TMA view)
+  int gamma_cap = 0;            // bound on the window half-width (host evaluation + 1)
+  int tc_nch = 0, tc_Nc = 0;    // i1 chunks and chunk width (N of the MMAs)
+  int tc_kpad = 0, tc_K8 = 0;   // K of the Tucker MMAs (rmax rounded to 8), of one window
+  int tc_nt2 = 0, tc_nt3 = 0;   // output tiles of 4 (i2) x 32 (i3) points
+  int tc_grid = 0;
+  size_t tc_smem = 0;           // dynamic shared memory of the assembly kernel
+  long long wl_cap = 0;         // capacity of the window lists (entries)
+  int*       wl_count = nullptr;   // nt2*nt3 + 1
+  int*       wl_start = nullptr;   // nt2*nt3 + 1
+  long long* wl_key = nullptr;     // wl_cap: (j1 << 32) | particle
+  int4*      wl_rec = nullptr;     // wl_cap: (j1, j2, j3, float bits of z)
+  int2*      wl_rng = nullptr;     // nt2*nt3*nch: entries of each tile column per i1 chunk
+  alignas(64) CUtensorMap tmap_T2;   // 3-D view (i3, i2, a) of T2 for the TMA loads
   DevScalars* sc = nullptr;
   DevScalars* h_sc = nullptr;   // pinned host copy
 
@@ -154,7 +171,11 @@ int launch_subspace(Ctx& c);
 int launch_projection_core(Ctx& c);
 int launch_bins(Ctx& c);
 int launch_recon_gemm(Ctx& c, void* out);
-int launch_recon_tc(Ctx& c, float* out);   // rs_tc.cu; -1 when the shape is not supported
+// tensor-core assembly (rs_tc.cu)
+bool plan_assemble(Ctx& c);              // host: fills the tc_* fields, false if unsupported
+int launch_window_lists(Ctx& c);         // per-tile-column window lists
+int launch_assemble(Ctx& c, float* out); // Tucker product + windows in one kernel
+bool encode_t2_map(Ctx& c, std::string& err);
 int launch_windows(Ctx& c, void* out);
 int launch_energy(Ctx& c, int N);
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out);

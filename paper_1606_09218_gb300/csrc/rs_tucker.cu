@@ -187,8 +187,8 @@ static int projection_core_t(Ctx& c) {
   // T2[a][i2][i3] = sum_b V2[i2][b] T1[a][b][i3]        (batch a < r1, K = r2)
   batch_dims_kernel<<<(rmax + 127) / 128, 128, 0, c.stream>>>(c.adims, c.kdims, rmax, n, c.sc);
   gemm_batched<T>(c.stream, false, false, n, n, rmax, T(1), Zb + sZ, rmax, 0, (const T*)c.T1, n,
-                  (long long)rmax * n, T(0), (T*)c.T2, n, (long long)n * n, rmax, 1, c.adims,
-                  nullptr, c.kdims);
+                  (long long)rmax * n, T(0), (T*)c.T2, c.t2_ld, (long long)n * c.t2_ld, rmax, 1,
+                  c.adims, nullptr, c.kdims);
   return 6;
 }
 
@@ -259,7 +259,9 @@ int launch_bins(Ctx& c) {
   bin_fill_kernel<<<grid, 256, 0, c.stream>>>(c.j, c.nz_idx, c.sc, nb, c.bin_start, c.bin_count,
                                               c.bin_items);
   bin_sort_kernel<<<(nbins + 255) / 256, 256, 0, c.stream>>>(c.bin_start, nbins, c.bin_items);
-  return 4;
+  int k = 4;
+  if (c.use_tc) k += launch_window_lists(c);
+  return k;
 }
 
 // ------------------------------------------------------------------ windows (a6)
@@ -411,9 +413,17 @@ template <typename T>
 static int recon_gemm_t(Ctx& c, T* out) {
   const int n = c.n, rmax = c.rmax;
   const T* Zb = Bulk<T>::Z(c);
-  // P[i1][(i2,i3)] = sum_a V1[i1][a] T2[a][(i2,i3)]
-  gemm_batched<T>(c.stream, false, false, n, n * n, rmax, T(1), Zb, rmax, 0, (const T*)c.T2,
-                  n * n, 0, T(0), out, n * n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 0);
+  if (c.t2_ld == n) {
+    // P[i1][(i2,i3)] = sum_a V1[i1][a] T2[a][(i2,i3)]
+    gemm_batched<T>(c.stream, false, false, n, n * n, rmax, T(1), Zb, rmax, 0, (const T*)c.T2,
+                    n * n, 0, T(0), out, n * n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 0);
+  } else {
+    // padded T2 rows: one batch per i2, P[i1][i2][i3] = sum_a V1[i1][a] T2[a][i2][i3]
+    const long long ldb = (long long)n * c.t2_ld;
+    gemm_batched<T>(c.stream, false, false, n, n, rmax, T(1), Zb, rmax, 0, (const T*)c.T2,
+                    (int)ldb, c.t2_ld, T(0), out, n * n, n, n, 1, nullptr, nullptr,
+                    c.sc->rank + 0);
+  }
   return 1;
 }
 
@@ -428,17 +438,14 @@ static int windows_t(Ctx& c, T* out) {
 
 int launch_recon_gemm(Ctx& c, void* out) {
   if (c.fp64) return recon_gemm_t<double>(c, (double*)out);
-  // FP32 bulk: tensor cores (tcgen05, 3xTF32) unless RS_RECON_PATH=cuda asks for the CUDA-core
-  // product or the rank bound is above what the tensor-core kernel stages in shared memory
-  const char* e = std::getenv("RS_RECON_PATH");
-  if (!(e && std::strcmp(e, "cuda") == 0)) {
-    int k = launch_recon_tc(c, (float*)out);
-    if (k >= 0) return k;
-  }
+  // FP32 bulk: the tensor-core assembly (Tucker product and windows in one kernel) when the
+  // context planned it, else the CUDA-core product followed by the window kernel
+  if (c.use_tc) return launch_assemble(c, (float*)out);
   return recon_gemm_t<float>(c, (float*)out);
 }
 
 int launch_windows(Ctx& c, void* out) {
+  if (!c.fp64 && c.use_tc) return 0;      // the tensor-core assembly already added the windows
   return c.fp64 ? windows_t<double>(c, (double*)out) : windows_t<float>(c, (float*)out);
 }
 

@@ -39,8 +39,8 @@ def test_version_and_workspace(lib):
     w1 = lib.rs_workspace_bytes(C.byref(c1))
     w2 = lib.rs_workspace_bytes(C.byref(c2))
     assert 0 < w1 < w2
-    # T2 (rank x n x n) dominates at n = 513
-    assert w2 > 4 * 128 * 513 * 513
+    # T2 (rank bound x n x n, FP32) dominates at n = 513
+    assert w2 > 4 * load_config("c2_protein1000_n513")["max_rank"] * 513 * 513
 
 
 def test_invalid_config_is_rejected_on_host(lib):
