@@ -114,8 +114,8 @@ size_t rs_workspace_bytes(const rs_config* cfg);
 /* Run the whole method for N particles (Sec. 3.2-3.3 and Sec. 6):
  *   xyz (N x 3, row-major, float64) and Z (N, float64): device pointers, or host pointers
  *   with RS_INPUT_HOST;
- *   potential_out: with RS_POTENTIAL a device buffer of n^3 elements (double for RS_FP64,
- *   float otherwise), written in C order; ignored otherwise.
+ *   potential_out: with RS_POTENTIAL a 16-byte aligned device buffer of n^3 elements (double
+ *   for RS_FP64, float otherwise), written in C order; ignored otherwise.
  * Enqueues the work on the context stream and returns without waiting (inputs must stay
  * valid until the stream reaches the solve).  Device-side input errors (outside the box,
  * non-finite values) are reported by rs_report / rs_energy.  min_sep is used only with

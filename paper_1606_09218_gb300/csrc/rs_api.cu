@@ -60,7 +60,7 @@ bool derive(const rs_config& cfg, Ctx& c, std::string& err) {
   c.nbin = (cfg.n + BIN - 1) / BIN;
   c.maxN = cfg.max_particles;
   c.t2_ld = cfg.n;
-  c.use_tc = plan_assemble(c);             // may pad t2_ld for the TMA view of T2
+  c.use_tc = plan_assemble(c);
   return true;
 }
 
@@ -103,7 +103,7 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.beta64, 8 * rm * rm * rm);
   add(v, c.beta, ts * rm * rm * rm);
   add(v, c.T1, ts * rm * rm * n);
-  add(v, c.T2, ts * rm * n * (size_t)c.t2_ld);
+  add(v, c.T2, c.use_tc ? t2_tile_bytes(c) : ts * rm * n * (size_t)c.t2_ld);
   add(v, c.bin_count, 4 * (nbins + 1));
   add(v, c.bin_start, 4 * (nbins + 1));
   add(v, c.bin_items, 4 * N);
@@ -112,10 +112,9 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.kdims, 4 * rm);
   add(v, c.sc, sizeof(DevScalars));
   if (c.use_tc) {
-    const size_t nT = (size_t)c.tc_nt2 * c.tc_nt3;
+    const size_t nT = (size_t)c.tc_ntiles;
     add(v, c.wl_count, 4 * (nT + 1));
     add(v, c.wl_start, 4 * (nT + 1));
-    add(v, c.wl_key, 8 * (size_t)c.wl_cap);
     add(v, c.wl_rec, 16 * (size_t)c.wl_cap);
     add(v, c.wl_rng, 8 * nT * c.tc_nch);
   }
@@ -270,12 +269,6 @@ rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
       return RS_ERR_CUDA;
     }
   }
-  if (c.use_tc) {
-    // the tensor-core assembly needs the TMA descriptor of T2; without it the CUDA-core
-    // product and window kernels serve (they accept the padded T2 rows)
-    std::string terr;
-    if (!encode_t2_map(c, terr)) c.use_tc = false;
-  }
   *out = h;
   return RS_OK;
 }
@@ -297,6 +290,8 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   if (N > 0 && (!xyz || !Z)) return fail(c, RS_ERR_INVALID_ARG, "null particle arrays");
   if ((flags & RS_POTENTIAL) && !potential_out)
     return fail(c, RS_ERR_INVALID_ARG, "RS_POTENTIAL needs potential_out");
+  if ((flags & RS_POTENTIAL) && ((uintptr_t)potential_out & 15u))
+    return fail(c, RS_ERR_INVALID_ARG, "potential_out must be 16-byte aligned");
   if ((flags & RS_VALIDATE_SEPARATION) && !(min_sep > 0.0))
     return fail(c, RS_ERR_INVALID_ARG, "RS_VALIDATE_SEPARATION needs min_sep > 0");
   if (flags & RS_INPUT_HOST) {

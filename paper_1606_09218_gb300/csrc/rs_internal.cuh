@@ -51,6 +51,9 @@ struct DevScalars {
   int blk_acc[3];                // columns accepted by the one-CTA fallback of the current block
   int jacobi_sweeps;             // Jacobi sweeps of the last solve (all modes and passes)
   int fallbacks;                 // blocks that took the one-CTA Gram-Schmidt fallback
+  int chunk_w[32];               // windows per i1 chunk (tensor-core assembly schedule)
+  unsigned zmax_bits;            // max |z| over the particles (float bits; window operand scale)
+  double beta_a2[RMAX_LIMIT];    // ||beta[a, :, :]||^2 (scale of the FP16 Tucker operands)
   // grid barrier of the cooperative Gram-Schmidt kernel: arrival counter and generation on
   // separate 128-byte lines, so that the waiters' polling does not slow the arrivals
   alignas(128) unsigned bar_count;
@@ -112,20 +115,19 @@ struct Ctx {
   int*    kdims = nullptr;      // rmax: per-batch inner sizes of the mode-2 product
   // tensor-core assembly of the FP32 output (rs_tc.cu), planned at create
   bool use_tc = false;
-  int t2_ld = 0;                // i3 stride of T2 (n, or n rounded up to 4 for the TMA view)
+  int t2_ld = 0;                // i3 stride of T2 on the CUDA-core path
   int gamma_cap = 0;            // bound on the window half-width (host evaluation + 1)
   int tc_nch = 0, tc_Nc = 0;    // i1 chunks and chunk width (N of the MMAs)
-  int tc_kpad = 0, tc_K8 = 0;   // K of the Tucker MMAs (rmax rounded to 8), of one window
-  int tc_nt2 = 0, tc_nt3 = 0;   // output tiles of 4 (i2) x 32 (i3) points
+  int tc_kpad = 0;              // K of the Tucker MMAs (rmax rounded to 16)
+  int tc_ntiles = 0;            // output tiles of 128 consecutive grid points (i2, i3) of a plane
+  int tc_na = 0, tc_ns = 0;     // stages of the T2 tiles and of the window operand pairs
   int tc_grid = 0;
   size_t tc_smem = 0;           // dynamic shared memory of the assembly kernel
   long long wl_cap = 0;         // capacity of the window lists (entries)
-  int*       wl_count = nullptr;   // nt2*nt3 + 1
-  int*       wl_start = nullptr;   // nt2*nt3 + 1
-  long long* wl_key = nullptr;     // wl_cap: (j1 << 32) | particle
+  int*       wl_count = nullptr;   // ntiles + 1
+  int*       wl_start = nullptr;   // ntiles + 1
   int4*      wl_rec = nullptr;     // wl_cap: (j1, j2, j3, float bits of z)
-  int2*      wl_rng = nullptr;     // nt2*nt3*nch: entries of each tile column per i1 chunk
-  alignas(64) CUtensorMap tmap_T2;   // 3-D view (i3, i2, a) of T2 for the TMA loads
+  int2*      wl_rng = nullptr;     // ntiles*nch: entries of each tile column per i1 chunk
   DevScalars* sc = nullptr;
   DevScalars* h_sc = nullptr;   // pinned host copy
 
@@ -173,9 +175,10 @@ int launch_bins(Ctx& c);
 int launch_recon_gemm(Ctx& c, void* out);
 // tensor-core assembly (rs_tc.cu)
 bool plan_assemble(Ctx& c);              // host: fills the tc_* fields, false if unsupported
+size_t t2_tile_bytes(const Ctx& c);      // bytes of the tiled FP16 T2 (tensor-core path)
+int launch_t2_tiles(Ctx& c);             // mode-2 product into tiled FP16 hi/lo operands
 int launch_window_lists(Ctx& c);         // per-tile-column window lists
 int launch_assemble(Ctx& c, float* out); // Tucker product + windows in one kernel
-bool encode_t2_map(Ctx& c, std::string& err);
 int launch_windows(Ctx& c, void* out);
 int launch_energy(Ctx& c, int N);
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out);

@@ -6,29 +6,41 @@
 //                 + sum_{nu in L(i)} sum_{k short} (z_nu p_k[i2-j2] p_k[i3-j3]) p_k[i1-j1]
 //                                                                         windows (Defs. 3.4, 3.6)
 //
-// M = 128 grid points (i2, i3) of a 4 x 32 tile, N = a chunk of i1 rows, K = the Tucker rank r1
-// followed by ceil8(R_s) per window that reaches the tile (each window is a rank-R_s outer
-// product, so it is one more K slice of the same accumulator).  The accumulator lives in tensor
-// memory, the sum is stored once, and the output is never read back: the Tucker product and
-// the short-range windows cost one pass over the grid.
+// M = 128 consecutive grid points p = i2 n + i3 of a plane, N = a chunk of i1 rows, K = the
+// Tucker rank r1, then ceil8(R_s) per window that reaches the tile (a window is a rank-R_s outer
+// product: one more K slice).  The sums live in tensor memory, the output is stored once and
+// never read back: the Tucker product and the short-range windows cost one pass over the grid.
 //
-// Precision: every FP32 operand is split into a TF32 high part and a TF32 low part
-// (x = hi + lo, |lo| <= 2^-11 |x|) and D += A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in FP32
-// (three tcgen05.mma kind::tf32 per K slice), an error of order 2^-21 |A||B| per product.
+// Operands and precision (every operand x is split as x = hi + lo in FP16, |x - hi - lo| <=
+// 2^-22 |x| in the normal range, and hi*hi + hi*lo + lo*hi accumulate in FP32):
+//  * Tucker part (kind::f16, its own accumulator): T2 is written by the mode-2 product directly
+//    as FP16 hi / lo tiles in the canonical K-major layout (one contiguous block per tile,
+//    fetched with one bulk copy); V1 (|V1| <= 1) is scaled by 2^8 and T2 by 2^(S-8) with
+//    2^(S-8) max_a ||beta[a]|| < 2^14, a bound of every T2 entry (|T2[a][i2][i3]| <=
+//    ||beta[a,:,:]|| for orthonormal V2, V3): nothing overflows, and values below the FP16
+//    normal range carry absolute errors far below the FP32 rounding of the result;
+//  * windows (kind::f16, a second accumulator, scale 2^(sA+sB)): two windows share one K = 16
+//    MMA (one 8-wide K chunk each); A_w[m][k] = 2^sA z p_k[i2-j2] p_k[i3-j3] is built per window,
+//    while B = 2^sB p_k[i1-j1] is a slice of one factor table stored with a 16-byte row pitch,
+//    so every row offset is a valid operand start and the two windows' slices are one leading
+//    byte offset apart: no per-window B is built.
+// The epilogue scales both accumulators back (exact powers of two) and adds them.
 //
 // CTA (persistent, one per SM, 14 warps):
-//   warp 0     tensor-memory owner; lane 0 issues the MMAs
-//   warp 1     scheduler: TMA load of the T2 slab of the next tile, window list pages
-//   warps 2-5  producers: split T2 slab -> A (K-major, hi/lo); window operands -> slot ring
-//   warps 6-13 epilogue: tensor memory -> registers -> coalesced streaming stores
+//   warp 0     tensor-memory owner; lane 0 issues the MMAs (straight-line, descriptors precomputed)
+//   warp 1     scheduler: bulk copy of the T2 tiles of the next jobs, window list pages
+//   warps 2-5  producers: window operand pairs -> ring of slots (+ ready-made descriptors)
+//   warps 6-13 epilogue: tensor memory -> registers -> shared staging -> bulk stores of the
+//              16-byte aligned middle of each plane row, scalar stores at its two ends
 // A CTA keeps one i1 chunk (its V1 rows, split, as the B operand of the Tucker part) and walks
-// over the tiles; the accumulator is double-buffered so that the stores of one tile overlap the
+// over the tiles; the CTAs are spread over the chunks in proportion to their work (tiles plus
+// windows).  Both accumulators are double-buffered so that the stores of one tile overlap the
 // MMAs of the next.  Every wait is bounded: on expiry the CTA sets FLAG_TIMEOUT, the other roles
-// see an abort flag, the MMA issuer and the TMA issuer wait (bounded) for their work in flight,
-// and the tensor memory is released before return.
+// see an abort flag, the MMA issuer and the copy issuers wait (bounded) for their work in
+// flight, and the tensor memory is released before return.
 #include "rs_internal.cuh"
 
-#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <climits>
 #include <cmath>
@@ -40,16 +52,21 @@ namespace rs {
 namespace {
 
 constexpr int AS_M = 128;                  // grid points per tile (tensor-memory lanes)
-constexpr int AS_T2 = 4, AS_T3 = 32;       // tile = 4 (i2) x 32 (i3)
+constexpr int AS_T3 = 32;                  // i3 columns per CTA of the T2 tile kernel
 constexpr int AS_THREADS = 448;            // 14 warps
 constexpr int WARP_SCHED = 1, WARP_PROD = 2, WARP_EPI = 6;
-constexpr int NPROD = 128;                 // producer threads
+constexpr int NPW = 4;                     // producer warps
 constexpr int NEPI = 8;                    // epilogue warps
+constexpr int NA_MAX = 3, NS_MAX = 8;      // T2 tile stages, window pair slots
+constexpr int STG_ROW = 132;               // floats per staging row (128 + alignment shift)
 constexpr int LIST_CAP = 256;              // window records per list page
 constexpr int WL_SORT_CAP = 4096;          // longest window list of one tile column
 constexpr long long WAIT_LIMIT = 4000000;
 constexpr int SMEM_LIMIT = 232448;         // opt-in shared memory per CTA on this GPU family
 constexpr int SMEM_RESERVE = 1024;         // static shared memory of the kernel
+constexpr double COST_TILE = 2500.0;       // relative cost of one tile job (output bound)
+constexpr double COST_WINDOW = 120.0;      // relative cost of one window of a job
+constexpr int TT_ROWS = 32;                // i2 rows per CTA of the T2 tile kernel
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -97,6 +114,14 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
   return false;
 }
 
+// the same for a whole warp: lane 0 waits, the result is broadcast (warp-uniform control flow)
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          DevScalars* sc) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = wait_bar(bar, parity, abort_flag, sc) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 // Bounded wait that ignores the abort flag (draining work in flight before exit).
 __device__ __forceinline__ void drain_bar(uint64_t* bar, uint32_t parity, DevScalars* sc) {
   for (long long i = 0; i < WAIT_LIMIT; ++i)
@@ -104,69 +129,72 @@ __device__ __forceinline__ void drain_bar(uint64_t* bar, uint32_t parity, DevSca
   atomicOr(&sc->flags, (unsigned)FLAG_TIMEOUT);
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                            uint64_t* bar) {
+// contiguous global -> shared copy completed on an mbarrier (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"((uint64_t)src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+// shared -> global bulk copy (16-byte aligned, size % 16 == 0), tracked by bulk groups
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"((uint64_t)dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// split a pair of FP32 values into FP16 hi / lo pairs (first value in the low half)
+__device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+  const __half l0 = __float2half_rn(x0 - __half2float(h0)), l1 = __float2half_rn(x1 - __half2float(h1));
+  hi = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+  lo = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+}
+
+// eight FP32 values -> 16 bytes of FP16 hi and 16 bytes of FP16 lo
+__device__ __forceinline__ void split8_f16(const float* x, uint4& hi, uint4& lo) {
+  split_h2(x[0], x[1], hi.x, lo.x);
+  split_h2(x[2], x[3], hi.y, lo.y);
+  split_h2(x[4], x[5], hi.z, lo.z);
+  split_h2(x[6], x[7], hi.w, lo.w);
 }
 
 // canonical K-major layout without swizzle: 8-row x 16-byte core matrices, the K chunks of a
-// row group contiguous (LBO = 128 B), row groups SBO = (kw/4)*128 B apart (kw = K width).
-__device__ __forceinline__ uint32_t kmajor_offset(int row, int k4, int kw) {
-  return ((uint32_t)(row >> 3) * (uint32_t)(kw >> 2) + (uint32_t)k4) * 128u + (uint32_t)(row & 7) * 16u;
-}
-
-// split four FP32 values into TF32 hi / lo and store both 16-byte chunks
-__device__ __forceinline__ void store_split4(unsigned char* hi, unsigned char* lo, uint32_t off,
-                                             float x0, float x1, float x2, float x3) {
-  uint32_t h0 = to_tf32(x0), h1 = to_tf32(x1), h2 = to_tf32(x2), h3 = to_tf32(x3);
-  uint32_t l0 = to_tf32(x0 - __uint_as_float(h0)), l1 = to_tf32(x1 - __uint_as_float(h1));
-  uint32_t l2 = to_tf32(x2 - __uint_as_float(h2)), l3 = to_tf32(x3 - __uint_as_float(h3));
-  *(uint4*)(hi + off) = make_uint4(h0, h1, h2, h3);
-  *(uint4*)(lo + off) = make_uint4(l0, l1, l2, l3);
+// row group contiguous (LBO = 128 B), row groups (chunks per row) * 128 B apart.
+__device__ __forceinline__ uint32_t kmajor_offset(int row, int chunk, int chunks_per_row) {
+  return ((uint32_t)(row >> 3) * (uint32_t)chunks_per_row + (uint32_t)chunk) * 128u + (uint32_t)(row & 7) * 16u;
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);          // start address
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;      // leading dimension byte offset
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;      // stride dimension byte offset
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;      // leading dimension (K) byte offset
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;      // stride dimension (M/N) byte offset
   d |= (uint64_t)1 << 46;                            // fixed 0b001
   return d;                                           // base offset 0, no swizzle
 }
 
-// instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = nn
-__device__ __forceinline__ uint32_t idesc_tf32(int nn) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nn >> 3) << 17) | ((uint32_t)(AS_M >> 4) << 24);
+// instruction descriptor (kind::f16): D FP32, A and B FP16, both K-major, M = 128, N = nn
+__device__ __forceinline__ uint32_t idesc_f16(int nn) {
+  return (1u << 4) | ((uint32_t)(nn >> 3) << 17) | ((uint32_t)(AS_M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.u32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
-}
-
-// D (+)= A_hi B_hi + A_hi B_lo + A_lo B_hi for one K slice of 8
-__device__ __forceinline__ void mma3(uint32_t d, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
-                                     uint32_t sbo_a, uint32_t sbo_b, uint32_t idesc, uint32_t acc) {
-  const uint64_t dah = smem_desc(ah, 128, sbo_a), dal = smem_desc(al, 128, sbo_a);
-  const uint64_t dbh = smem_desc(bh, 128, sbo_b), dbl = smem_desc(bl, 128, sbo_b);
-  mma_tf32(d, dah, dbh, idesc, acc);
-  mma_tf32(d, dah, dbl, idesc, 1u);
-  mma_tf32(d, dal, dbh, idesc, 1u);
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -197,29 +225,155 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Power-of-two exponent e with x < 2^e (0 for x <= 0 or non-finite).
+__device__ __forceinline__ int exp2_above(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return 0;
+  int e = 0;
+  frexp(x, &e);
+  return e;
+}
+
+// Scale exponent S of the Tucker operands: 2^(S-8) max_a ||beta[a]|| < 2^14.
+__device__ __forceinline__ int operand_shift(const DevScalars* sc, int r1) {
+  double m = 0.0;
+  for (int a = 0; a < r1; ++a) m = fmax(m, sc->beta_a2[a]);
+  if (!(m > 0.0)) return 0;
+  return max(-100, min(100, 22 - exp2_above(sqrt(m))));
+}
+
 struct AsmArgs {
-  const float* V1;           // mode-1 Tucker basis, n x ldv
+  const unsigned char* T2t;   // FP16 hi / lo tiles of T2, tile_bytes each
+  unsigned long long tile_bytes;
+  const float* V1;            // mode-1 Tucker basis, n x ldv
   int ldv;
-  const float* pk;           // factor table, R x L (FP32)
-  const int4* rec;           // window records (j1, j2, j3, float bits of z), per tile column
-  const int2* rng;           // [tile][chunk] ranges into rec (nullptr: no short-range terms)
-  float* P;                  // output n^3
+  const float* pk;            // factor table, R x L (FP32)
+  const int4* rec;            // window records (j1, j2, j3, float bits of z), per tile
+  const int2* rng;            // [tile][chunk] ranges into rec (nullptr: no short-range terms)
+  float* P;                   // output n^3
   DevScalars* sc;
   int n, L, R_l, R_s;
-  int nch, Nc, kpad, K8, gcap, nt3, ntiles, dstride, tmem_cols;
-  uint32_t off_bh, off_bl, off_raw, off_ah, off_al, off_slot, slot_bytes, off_tab, off_list;
+  int nch, Nc, kp, gcap, TR, D0, ntiles, dstride, tmem_cols, na, ns;
+  uint32_t off_bv, off_a, off_slot, off_tbl, off_tab, off_list, off_stage;
+  uint32_t bv_half, a_half, tbl_half;   // bytes of each hi part (the lo part follows)
 };
+
+constexpr uint32_t SLOT_HALF = AS_M * 16 * 2;    // one pair slot: 128 rows x K 16 FP16, hi or lo
 
 }  // namespace
 
+// ------------------------------------------------------------------ T2 tiles
+// T2[a][i2][i3] = sum_b V2[i2][b] T1[a][b][i3]  (mode-2 product, Eq. (2.3)) written as the A
+// operand of the assembly: per output tile (128 consecutive points p = i2 n + i3, K = kp ranks)
+// an FP16 hi block and an FP16 lo block in the canonical K-major layout, scaled by 2^(S-8);
+// ranks a >= r1 and points beyond the grid are zero.  One CTA: 32 i3 x 32 i2, ranks in groups
+// of 8 (one 16-byte chunk of a row).
+__global__ void __launch_bounds__(256)
+t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int n, int rmax, int kp,
+                int ntiles, const DevScalars* sc, unsigned char* __restrict__ out,
+                unsigned long long tile_bytes) {
+  extern __shared__ __align__(16) float tsm[];
+  float* T1s = tsm;                          // [8][rmax][32]
+  float* V2s = tsm + 8 * rmax * 32;          // [32][rmax]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int t3 = blockIdx.x, i2b = blockIdx.y * TT_ROWS, i3 = t3 * AS_T3 + lane;
+  const int r1 = sc->rank[0], r2 = sc->rank[1];
+  const float scale = ldexpf(1.0f, operand_shift(sc, r1) - 8);
+  const unsigned long long half_bytes = tile_bytes / 2;
+  const long long np = (long long)n * n;
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    // rows of the last tile beyond the grid
+    const long long p_last = (long long)(ntiles - 1) * AS_M;
+    unsigned char* tile = out + (unsigned long long)(ntiles - 1) * tile_bytes;
+    for (int e = tid; e < AS_M * (kp >> 3); e += 256) {
+      const int m = e / (kp >> 3), k8 = e % (kp >> 3);
+      if (p_last + m >= np) {
+        const uint32_t off = kmajor_offset(m, k8, kp >> 3);
+        *(uint4*)(tile + off) = make_uint4(0, 0, 0, 0);
+        *(uint4*)(tile + half_bytes + off) = make_uint4(0, 0, 0, 0);
+      }
+    }
+  }
+  for (int e = tid; e < TT_ROWS * rmax; e += 256) {
+    const int r = e / rmax, b = e % rmax, i2 = i2b + r;
+    V2s[e] = (i2 < n && b < r2) ? V2[(long long)i2 * rmax + b] : 0.f;
+  }
+  for (int a0 = 0; a0 < kp; a0 += 8) {
+    if (a0 >= r1) {
+      // rank slices beyond r1: zero chunks, nothing to compute
+      if (i3 < n)
+        for (int q = 0; q < 4; ++q) {
+          const int i2 = i2b + warp + 8 * q;
+          if (i2 >= n) continue;
+          const long long p = (long long)i2 * n + i3;
+          unsigned char* tile = out + (unsigned long long)(p >> 7) * tile_bytes;
+          const uint32_t off = kmajor_offset((int)(p & 127), a0 >> 3, kp >> 3);
+          *(uint4*)(tile + off) = make_uint4(0, 0, 0, 0);
+          *(uint4*)(tile + half_bytes + off) = make_uint4(0, 0, 0, 0);
+        }
+      continue;
+    }
+    __syncthreads();
+    // asynchronous 4-byte copies (all in flight at once); zero fill outside the ranks / grid
+    for (int e = tid; e < 8 * r2 * AS_T3; e += 256) {
+      const int x = e / (r2 * AS_T3), rem = e % (r2 * AS_T3), b = rem / AS_T3, i3o = rem % AS_T3;
+      const int a = a0 + x, ii = t3 * AS_T3 + i3o;
+      const bool in = a < r1 && ii < n;
+      const float* src = in ? T1 + ((long long)a * rmax + b) * n + ii : T1;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                       smem_addr(&T1s[(x * rmax + b) * AS_T3 + i3o])),
+                   "l"(src), "r"(in ? 4 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    float acc[4][8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int x = 0; x < 8; ++x) acc[q][x] = 0.f;
+    for (int b = 0; b < r2; ++b) {
+      float tv[8], vv[4];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) tv[x] = T1s[(x * rmax + b) * AS_T3 + lane];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) vv[q] = V2s[(warp + 8 * q) * rmax + b];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int x = 0; x < 8; ++x) acc[q][x] = fmaf(vv[q], tv[x], acc[q][x]);
+    }
+    if (i3 < n) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i2 = i2b + warp + 8 * q;
+        if (i2 >= n) continue;
+        float xs[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) xs[x] = acc[q][x] * scale;
+        uint4 hi, lo;
+        split8_f16(xs, hi, lo);
+        const long long p = (long long)i2 * n + i3;
+        unsigned char* tile = out + (unsigned long long)(p >> 7) * tile_bytes;
+        const uint32_t off = kmajor_offset((int)(p & 127), a0 >> 3, kp >> 3);
+        *(uint4*)(tile + off) = hi;
+        *(uint4*)(tile + half_bytes + off) = lo;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ assembly kernel
 __global__ void __launch_bounds__(AS_THREADS, 1)
-assemble_kernel(const __grid_constant__ CUtensorMap tmap, const AsmArgs g) {
+assemble_kernel(const AsmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_raw_full, bar_raw_empty, bar_a_full, bar_a_free, bar_drain;
+  __shared__ __align__(8) uint64_t bar_a_full[NA_MAX], bar_a_empty[NA_MAX];
   __shared__ __align__(8) uint64_t bar_list_full[2], bar_list_empty[2];
-  __shared__ __align__(8) uint64_t bar_slot_full[2], bar_slot_free[2];
-  __shared__ __align__(8) uint64_t bar_d_full[2], bar_d_empty[2];
-  __shared__ int page_n[2], page_total[2], job_nw[2], slot_hdr[2][2];
+  __shared__ __align__(8) uint64_t bar_slot_full[NS_MAX], bar_slot_free[NS_MAX];
+  __shared__ __align__(8) uint64_t bar_d_full[2], bar_d_empty[2], bar_drain;
+  __shared__ __align__(8) uint64_t hdr_db[NS_MAX][2];     // B descriptors (hi, lo) of a pair
+  __shared__ uint32_t hdr_id[NS_MAX][2];                   // instruction descriptor, column offset
+  __shared__ int page_n[2], page_total[2], job_nw[NA_MAX];
+  __shared__ int s_chunk, s_j0, s_stride, s_shiftT, s_shiftA, s_shiftB;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_s;
   volatile int* abort_flag = &abort_s;
@@ -227,66 +381,120 @@ assemble_kernel(const __grid_constant__ CUtensorMap tmap, const AsmArgs g) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   DevScalars* sc = g.sc;
   const int n = g.n;
-  const int chunk = (int)(blockIdx.x % (unsigned)g.nch);
-  const int j0 = (int)(blockIdx.x / (unsigned)g.nch);
-  const int jstride = (int)(gridDim.x / (unsigned)g.nch);
-  const int c0 = chunk * g.Nc;
-  const int cl = min(n, c0 + g.Nc) - 1;                 // last i1 row of this chunk
+  const long long np = (long long)n * n;
   const int r1 = sc->rank[0];
   const int gam = sc->gamma;
-  const bool ok_gamma = gam <= g.gcap;
-  const int njobs = (ok_gamma && j0 < g.ntiles && c0 < n) ? (g.ntiles - 1 - j0) / jstride + 1 : 0;
-  const int tw = 2 * g.gcap + 1;                        // row length of the factor table
-  const int kq = g.kpad >> 2;
-  unsigned char* Bh = smem + g.off_bh;
-  unsigned char* Bl = smem + g.off_bl;
-  const float* raw = (const float*)(smem + g.off_raw);
-  unsigned char* Ah = smem + g.off_ah;
-  unsigned char* Al = smem + g.off_al;
-  float* tab = (float*)(smem + g.off_tab);
-  int4* lists = (int4*)(smem + g.off_list);
 
   if (tid == 0) {
-    mbar_init(&bar_raw_full, 1);
-    mbar_init(&bar_raw_empty, NPROD);
-    mbar_init(&bar_a_full, NPROD);
-    mbar_init(&bar_a_free, 1);
-    mbar_init(&bar_drain, 1);
+    for (int s = 0; s < NA_MAX; ++s) {
+      mbar_init(&bar_a_full[s], 1);
+      mbar_init(&bar_a_empty[s], 1);
+    }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&bar_list_full[b], 1);
-      mbar_init(&bar_list_empty[b], NPROD);
-      mbar_init(&bar_slot_full[b], NPROD);
-      mbar_init(&bar_slot_free[b], 1);
+      mbar_init(&bar_list_empty[b], NPW);
       mbar_init(&bar_d_full[b], 1);
       mbar_init(&bar_d_empty[b], NEPI);
     }
+    for (int s = 0; s < NS_MAX; ++s) {
+      mbar_init(&bar_slot_full[s], NPW);
+      mbar_init(&bar_slot_free[s], 1);
+    }
+    mbar_init(&bar_drain, 1);
     abort_s = 0;
-    if (!ok_gamma) atomicOr(&sc->flags, (unsigned)FLAG_WINDOWS);
+    // spread the CTAs over the i1 chunks in proportion to their work (same result in every CTA)
+    double cost[32], tot = 0.0;
+    for (int c = 0; c < g.nch; ++c) {
+      cost[c] = COST_TILE * g.ntiles + COST_WINDOW * (double)sc->chunk_w[c];
+      tot += cost[c];
+    }
+    int cnt[32], used = 0;
+    const int G = (int)gridDim.x;
+    for (int c = 0; c < g.nch; ++c) {
+      cnt[c] = 1 + (int)floor((double)(G - g.nch) * cost[c] / tot);
+      used += cnt[c];
+    }
+    while (used < G) {
+      int best = 0;
+      for (int c = 1; c < g.nch; ++c)
+        if (cost[c] * cnt[best] > cost[best] * cnt[c]) best = c;
+      ++cnt[best];
+      ++used;
+    }
+    int pre = 0, ch = g.nch - 1;
+    for (int c = 0; c < g.nch; ++c) {
+      if ((int)blockIdx.x < pre + cnt[c]) { ch = c; break; }
+      pre += cnt[c];
+    }
+    s_chunk = ch;
+    s_j0 = (int)blockIdx.x - pre;
+    s_stride = cnt[ch];
+    s_shiftT = operand_shift(sc, r1);
+    // window operand scales: the table 2^sB p_k and A = 2^sA z p_k p_k stay below 2^14
+    double fmax = 0.0;
+    for (int k = 0; k < g.R_s; ++k) fmax = fmax > g.pk[(long long)(g.R_l + k) * g.L + (n - 1)] ? fmax : (double)g.pk[(long long)(g.R_l + k) * g.L + (n - 1)];
+    const double zmax = (double)__uint_as_float(sc->zmax_bits);
+    s_shiftB = (fmax > 0.0) ? 14 - exp2_above(fmax) : 0;
+    s_shiftA = (fmax > 0.0 && zmax > 0.0) ? 14 - exp2_above(zmax * fmax * fmax) : 0;
+    if (gam > g.gcap) atomicOr(&sc->flags, (unsigned)FLAG_WINDOWS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
+    __syncwarp();
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&tmem_slot)),
                  "r"(g.tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // one-time staging by the whole CTA: the short-range factor rows p_k[d], |d| <= gamma, and
-  // the V1 rows of this chunk as the B operand of the Tucker part (K-major, hi / lo)
+  __syncthreads();
+  const int chunk = s_chunk, j0 = s_j0, jstride = s_stride;
+  const int c0 = chunk * g.Nc;
+  const int cl = min(n, c0 + g.Nc) - 1;                 // last i1 row of this chunk
+  const int njobs = (gam <= g.gcap && j0 < g.ntiles && c0 < n) ? (g.ntiles - 1 - j0) / jstride + 1 : 0;
+  const int tw = 2 * g.gcap + 1;                        // row length of the FP32 factor rows
+  unsigned char* Bh = smem + g.off_bv;
+  unsigned char* Bl = Bh + g.bv_half;
+  unsigned char* Th = smem + g.off_tbl;
+  unsigned char* Tl = Th + g.tbl_half;
+  float* tab = (float*)(smem + g.off_tab);
+  int4* lists = (int4*)(smem + g.off_list);
+
+  // one-time staging by the whole CTA: the V1 rows of this chunk (B of the Tucker part, FP16
+  // hi / lo, scaled by 2^8), the short-range factor rows p_k[d] (FP32, for the A operands of the
+  // windows) and the factor table (B of the windows, FP16 hi / lo scaled by 2^sB, one 16-byte
+  // row of 8 ranks per d = rho - D0)
   if (njobs > 0) {
+    const int kc = g.kp >> 3;
+    for (int e = tid; e < g.Nc * kc; e += AS_THREADS) {
+      const int r = e / kc, k8 = e % kc, i1 = c0 + r;
+      float x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int a = 8 * k8 + q;
+        x[q] = (i1 < n && a < r1) ? 256.0f * g.V1[(long long)i1 * g.ldv + a] : 0.f;
+      }
+      uint4 hi, lo;
+      split8_f16(x, hi, lo);
+      const uint32_t off = kmajor_offset(r, k8, kc);
+      *(uint4*)(Bh + off) = hi;
+      *(uint4*)(Bl + off) = lo;
+    }
     for (int e = tid; e < g.R_s * tw; e += AS_THREADS) {
       const int k = e / tw, d = e % tw - g.gcap;
       tab[e] = (d >= -gam && d <= gam) ? g.pk[(long long)(g.R_l + k) * g.L + (n - 1) + d] : 0.f;
     }
-    for (int e = tid; e < g.Nc * kq; e += AS_THREADS) {
-      const int r = e / kq, k4 = e % kq, i1 = c0 + r;
-      float x[4];
+    const float sBf = ldexpf(1.0f, s_shiftB);
+    for (int rho = tid; rho < g.TR; rho += AS_THREADS) {
+      const int d = rho - g.D0;
+      float x[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int a = 4 * k4 + q;
-        x[q] = (i1 < n && a < r1) ? g.V1[(long long)i1 * g.ldv + a] : 0.f;
-      }
-      store_split4(Bh, Bl, kmajor_offset(r, k4, g.kpad), x[0], x[1], x[2], x[3]);
+      for (int k = 0; k < 8; ++k)
+        x[k] = (k < g.R_s && d >= -gam && d <= gam) ? sBf * g.pk[(long long)(g.R_l + k) * g.L + (n - 1) + d] : 0.f;
+      uint4 hi, lo;
+      split8_f16(x, hi, lo);
+      *(uint4*)(Th + (uint32_t)rho * 16u) = hi;
+      *(uint4*)(Tl + (uint32_t)rho * 16u) = lo;
     }
     fence_proxy_async();
   }
@@ -298,40 +506,46 @@ assemble_kernel(const __grid_constant__ CUtensorMap tmap, const AsmArgs g) {
   if (warp == 0) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0 && njobs > 0) {
-      const uint32_t sbo_t = (uint32_t)kq * 128u, sbo_w = (uint32_t)(g.K8 >> 2) * 128u;
-      const uint32_t bh = smem_addr(Bh), bl = smem_addr(Bl), ah = smem_addr(Ah), al = smem_addr(Al);
-      const uint32_t slot0 = smem_addr(smem + g.off_slot);
-      const uint32_t a_w = (uint32_t)AS_M * g.K8 * 4, b_w = (uint32_t)g.Nc * g.K8 * 4;
-      const int ksteps = max(1, min(g.kpad, (r1 + 7) & ~7) >> 3);
-      const uint32_t id_main = idesc_tf32(g.Nc);
-      int gw = 0;
-      for (int t = 0; t < njobs; ++t) {
-        if (!wait_bar(&bar_a_full, t & 1, abort_flag, sc)) break;
-        const int nw = job_nw[t & 1];
+      const uint32_t sbo_t = (uint32_t)(g.kp >> 3) * 128u;    // T2 tiles and V1 (FP16)
+      const uint64_t dBh = smem_desc(smem_addr(Bh), 128, sbo_t);
+      const uint64_t dBl = smem_desc(smem_addr(Bl), 128, sbo_t);
+      const uint64_t dA0 = smem_desc(smem_addr(smem + g.off_a), 128, sbo_t);
+      const uint64_t dS0 = smem_desc(smem_addr(smem + g.off_slot), 128, 256);
+      const uint64_t a_stage = (uint64_t)(2u * g.a_half) >> 4, a_lo = (uint64_t)g.a_half >> 4;
+      const uint64_t s_step = (uint64_t)(2u * SLOT_HALF) >> 4, s_lo = (uint64_t)SLOT_HALF >> 4;
+      const int ksteps = max(1, min(g.kp, (r1 + 15) & ~15) >> 4);
+      const uint32_t id_main = idesc_f16(g.Nc);
+      int st = 0, sl = 0;
+      uint32_t stph = 0, slph = 0;
+      bool ok = true;
+      for (int t = 0; ok && t < njobs; ++t) {
+        if (!wait_bar(&bar_a_full[st], stph, abort_flag, sc)) break;
+        const int nw = job_nw[st];
         if (t >= 2 && !wait_bar(&bar_d_empty[t & 1], ((t - 2) >> 1) & 1, abort_flag, sc)) break;
         fence_after_sync();
-        const uint32_t d = tmem + (uint32_t)((t & 1) * g.dstride);
+        const uint32_t dT = tmem + (uint32_t)((t & 1) * g.dstride);
+        const uint32_t dW = tmem + (uint32_t)((2 + (t & 1)) * g.dstride);
+        const uint64_t ah = dA0 + (uint64_t)st * a_stage, al = ah + a_lo;
         for (int s = 0; s < ksteps; ++s) {
-          const uint32_t ko = (uint32_t)s * 256u;   // two 16-byte K chunks per slice of 8
-          mma3(d, ah + ko, al + ko, bh + ko, bl + ko, sbo_t, sbo_t, id_main, s > 0 ? 1u : 0u);
+          const uint64_t ko = (uint64_t)s * 16u;           // 16 FP16 = 32 bytes per row
+          mma_f16(dT, ah + ko, dBh + ko, id_main, s > 0 ? 1u : 0u);
+          mma_f16(dT, ah + ko, dBl + ko, id_main, 1u);
+          mma_f16(dT, al + ko, dBh + ko, id_main, 1u);
         }
-        mma_commit(&bar_a_free);
-        bool ok = true;
-        for (int w = 0; w < nw; ++w, ++gw) {
-          const int s = gw & 1;
-          if (!wait_bar(&bar_slot_full[s], (gw >> 1) & 1, abort_flag, sc)) { ok = false; break; }
+        mma_commit(&bar_a_empty[st]);
+        if (++st == g.na) { st = 0; stph ^= 1u; }
+        const int npair = (nw + 1) >> 1;
+        for (int q = 0; q < npair; ++q) {
+          if (!wait_bar(&bar_slot_full[sl], slph, abort_flag, sc)) { ok = false; break; }
           fence_after_sync();
-          const int s0 = slot_hdr[s][0], s1 = slot_hdr[s][1];
-          const uint32_t base = slot0 + (uint32_t)s * g.slot_bytes;
-          const uint32_t wah = base, wal = base + a_w, wbh = base + 2 * a_w, wbl = base + 2 * a_w + b_w;
-          const uint32_t boff = (uint32_t)s0 * 2u * sbo_w;          // 16 rows = 2 row groups
-          const uint32_t id_w = idesc_tf32(16 * (s1 - s0 + 1));
-          const uint32_t dw = d + (uint32_t)(16 * s0);
-          for (int ks = 0; ks < (g.K8 >> 3); ++ks) {
-            const uint32_t ko = (uint32_t)ks * 256u;
-            mma3(dw, wah + ko, wal + ko, wbh + boff + ko, wbl + boff + ko, sbo_w, sbo_w, id_w, 1u);
-          }
-          mma_commit(&bar_slot_free[s]);
+          const uint64_t bh = hdr_db[sl][0], bl = hdr_db[sl][1];
+          const uint32_t idw = hdr_id[sl][0], dcol = hdr_id[sl][1];
+          const uint64_t sh = dS0 + (uint64_t)sl * s_step, slo = sh + s_lo;
+          mma_f16(dW + dcol, sh, bh, idw, q > 0 ? 1u : 0u);
+          mma_f16(dW + dcol, sh, bl, idw, 1u);
+          mma_f16(dW + dcol, slo, bh, idw, 1u);
+          mma_commit(&bar_slot_free[sl]);
+          if (++sl == g.ns) { sl = 0; slph ^= 1u; }
         }
         if (!ok) break;
         mma_commit(&bar_d_full[t & 1]);
@@ -343,28 +557,29 @@ assemble_kernel(const __grid_constant__ CUtensorMap tmap, const AsmArgs g) {
     __syncwarp();
   } else if (warp == WARP_SCHED) {
     // ------------------------------------------------------------ scheduler
-    int pg = 0, issued = 0;
+    int pg = 0, issued = 0, st = 0;
+    uint32_t stph = 0;
     for (int t = 0; t < njobs; ++t) {
-      const int T = j0 + t * jstride, t2 = T / g.nt3, t3 = T % g.nt3;
-      int ok = 1;
-      if (lane == 0) {
-        if (t > 0) ok = wait_bar(&bar_raw_empty, (t - 1) & 1, abort_flag, sc);
-        if (ok) {
-          mbar_expect_tx(&bar_raw_full, (uint32_t)(AS_M * g.kpad * 4));
-          tma_load_3d(smem + g.off_raw, &tmap, t3 * AS_T3, t2 * AS_T2, 0, &bar_raw_full);
-          ++issued;
-        }
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
+      const int T = j0 + t * jstride;
       int2 rg = make_int2(0, 0);
       if (g.rng) rg = g.rng[(long long)T * g.nch + chunk];
       const int total = rg.y - rg.x;
+      int ok = 1;
+      if (lane == 0) {
+        if (t >= g.na) ok = wait_bar(&bar_a_empty[st], stph ^ 1u, abort_flag, sc);
+        if (ok) {
+          job_nw[st] = total;
+          mbar_expect_tx(&bar_a_full[st], (uint32_t)g.tile_bytes);
+          bulk_load(smem + g.off_a + (size_t)st * 2 * g.a_half, g.T2t + (unsigned long long)T * g.tile_bytes,
+                    (uint32_t)g.tile_bytes, &bar_a_full[st]);
+          ++issued;
+        }
+      }
+      if (++st == g.na) { st = 0; stph ^= 1u; }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       for (int off = 0;; off += LIST_CAP) {
         const int b = pg & 1;
-        if (lane == 0 && pg >= 2) ok = wait_bar(&bar_list_empty[b], ((pg - 2) >> 1) & 1, abort_flag, sc);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
+        if (pg >= 2 && !warp_wait(&bar_list_empty[b], ((pg - 2) >> 1) & 1, abort_flag, sc)) { ok = 0; break; }
         const int cnt = min(LIST_CAP, total - off);
         for (int i = lane; i < cnt; i += 32) lists[b * LIST_CAP + i] = g.rec[rg.x + off + i];
         if (lane == 0) { page_n[b] = cnt; page_total[b] = total; }
@@ -375,95 +590,101 @@ assemble_kernel(const __grid_constant__ CUtensorMap tmap, const AsmArgs g) {
       }
       if (!ok) break;
     }
-    // the last TMA load has landed before the CTA exits
-    if (lane == 0 && issued > 0) drain_bar(&bar_raw_full, (issued - 1) & 1, sc);
+    // the copies issued last have landed before the CTA exits
+    if (lane == 0)
+      for (int t = max(0, issued - g.na); t < issued; ++t)
+        drain_bar(&bar_a_full[t % g.na], (uint32_t)(t / g.na) & 1u, sc);
     __syncwarp();
   } else if (warp < WARP_EPI) {
     // ------------------------------------------------------------ producers
-    const int pt = tid - WARP_PROD * 32;
-    const int kw = g.K8;
+    const int pt = tid - WARP_PROD * 32;       // operand row m
     unsigned char* slot_base = smem + g.off_slot;
-    const uint32_t a_w = (uint32_t)AS_M * kw * 4, b_w = (uint32_t)g.Nc * kw * 4;
-    int pg = 0, gw = 0;
+    const float sA = ldexpf(1.0f, s_shiftA);
+    const uint32_t tbl_h = smem_addr(Th), tbl_l = smem_addr(Tl);
+    int pg = 0, sl = 0;
+    uint32_t slph = 0;
+    int used = 0;                              // pair slots filled so far (first ns need no wait)
     for (int t = 0; t < njobs; ++t) {
-      const int T = j0 + t * jstride, t2 = T / g.nt3, t3 = T % g.nt3;
+      const int T = j0 + t * jstride;
       int b = pg & 1;
-      if (!wait_bar(&bar_raw_full, t & 1, abort_flag, sc)) break;
-      if (!wait_bar(&bar_list_full[b], (pg >> 1) & 1, abort_flag, sc)) break;
-      if (t > 0 && !wait_bar(&bar_a_free, (t - 1) & 1, abort_flag, sc)) break;
-      // T2 slab (a, m) -> A rows m, K-major, hi / lo; ranks beyond r1 are zero
-      for (int k4 = 0; k4 < kq; ++k4) {
-        float x[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int a = 4 * k4 + q;
-          x[q] = (a < r1) ? raw[a * AS_M + pt] : 0.f;
-        }
-        store_split4(Ah, Al, kmajor_offset(pt, k4, g.kpad), x[0], x[1], x[2], x[3]);
-      }
+      if (!warp_wait(&bar_list_full[b], (pg >> 1) & 1, abort_flag, sc)) break;
       const int nw = page_total[b];
-      if (pt == 0) job_nw[t & 1] = nw;
-      fence_proxy_async();
-      mbar_arrive(&bar_a_full);
-      mbar_arrive(&bar_raw_empty);
-      // windows: A_w[m][k] = z p_k[i2-j2] p_k[i3-j3],  B_w[i1][k] = p_k[i1-j1]
-      const int i2 = t2 * AS_T2 + (pt >> 5), i3 = t3 * AS_T3 + (pt & 31);
-      const int i1 = c0 + pt;
+      const long long p = (long long)T * AS_M + pt;
+      const bool valid = p < np;
+      const int i2 = valid ? (int)(p / n) : 0, i3 = valid ? (int)(p - (long long)i2 * n) : 0;
       bool ok = true;
       int pos = 0, pn = page_n[b];
-      for (int w = 0; w < nw; ++w, ++gw) {
-        if (pos == pn) {
-          mbar_arrive(&bar_list_empty[b]);
+      for (int q = 0; 2 * q < nw; ++q) {
+        if (pos == pn) {                       // pages hold an even number of records
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_list_empty[b]);
           ++pg;
           b = pg & 1;
-          if (!wait_bar(&bar_list_full[b], (pg >> 1) & 1, abort_flag, sc)) { ok = false; break; }
+          if (!warp_wait(&bar_list_full[b], (pg >> 1) & 1, abort_flag, sc)) { ok = false; break; }
           pos = 0;
           pn = page_n[b];
         }
-        const int4 rc = lists[b * LIST_CAP + pos];
-        ++pos;
-        const int s = gw & 1;
-        if (gw >= 2 && !wait_bar(&bar_slot_free[s], ((gw - 2) >> 1) & 1, abort_flag, sc)) { ok = false; break; }
-        unsigned char* sb = slot_base + (size_t)s * g.slot_bytes;
-        const float z = __int_as_float(rc.w);
-        const int d2 = i2 - rc.y, d3 = i3 - rc.z, d1 = i1 - rc.x;
-        const bool in23 = i2 < n && i3 < n && d2 >= -gam && d2 <= gam && d3 >= -gam && d3 <= gam;
-        const float* t2row = tab + (d2 + g.gcap);
-        const float* t3row = tab + (d3 + g.gcap);
-        for (int k4 = 0; k4 < (kw >> 2); ++k4) {
-          float x[4];
+        int4 wa = lists[b * LIST_CAP + pos];
+        const bool has_b = pos + 1 < pn;
+        int4 wb = has_b ? lists[b * LIST_CAP + pos + 1] : wa;
+        pos += 2;
+        if (has_b && wb.x > wa.x) { const int4 tmp = wa; wa = wb; wb = tmp; }   // chunk 0: larger j1
+        if (used >= g.ns && !warp_wait(&bar_slot_free[sl], slph ^ 1u, abort_flag, sc)) { ok = false; break; }
+        unsigned char* sbh = slot_base + (size_t)sl * 2 * SLOT_HALF;
+        unsigned char* sbl = sbh + SLOT_HALF;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int k = 4 * k4 + q;
-            x[q] = (in23 && k < g.R_s) ? z * t2row[k * tw] * t3row[k * tw] : 0.f;
-          }
-          store_split4(sb, sb + a_w, kmajor_offset(pt, k4, kw), x[0], x[1], x[2], x[3]);
-        }
-        if (pt < g.Nc) {
-          const bool in1 = i1 < n && d1 >= -gam && d1 <= gam;
-          const float* t1row = tab + (d1 + g.gcap);
-          for (int k4 = 0; k4 < (kw >> 2); ++k4) {
-            float x[4];
+        for (int w = 0; w < 2; ++w) {
+          const int4 rc = w == 0 ? wa : wb;
+          const bool live = (w == 0 || has_b) && valid;
+          const float z = __int_as_float(rc.w) * sA;
+          const int d2 = i2 - rc.y, d3 = i3 - rc.z;
+          const bool in23 = live && d2 >= -gam && d2 <= gam && d3 >= -gam && d3 <= gam;
+          const float* t2row = tab + (d2 + g.gcap);
+          const float* t3row = tab + (d3 + g.gcap);
+          float x[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int k = 4 * k4 + q;
-              x[q] = (in1 && k < g.R_s) ? t1row[k * tw] : 0.f;
-            }
-            store_split4(sb + 2 * a_w, sb + 2 * a_w + b_w, kmajor_offset(pt, k4, kw), x[0], x[1],
-                         x[2], x[3]);
-          }
+          for (int k = 0; k < 8; ++k)
+            x[k] = (in23 && k < g.R_s) ? z * t2row[k * tw] * t3row[k * tw] : 0.f;
+          uint4 hi, lo;
+          split8_f16(x, hi, lo);
+          const uint32_t off = kmajor_offset(pt, w, 2);
+          *(uint4*)(sbh + off) = hi;
+          *(uint4*)(sbl + off) = lo;
         }
         if (pt == 0) {
-          // 16-column groups of the chunk that this window reaches
-          const int lo1 = max(c0, rc.x - gam) - c0, hi1 = min(cl, rc.x + gam) - c0;
-          slot_hdr[s][0] = lo1 >> 4;
-          slot_hdr[s][1] = hi1 >> 4;
+          // 16-column groups of the chunk that the pair reaches (all of them for the first
+          // pair of a job, which overwrites the window accumulator), the table rows of the
+          // first row for each window, and the descriptors
+          int s0, s1;
+          if (q == 0) {
+            s0 = 0;
+            s1 = (g.Nc >> 4) - 1;
+          } else {
+            int lo1 = max(c0, wa.x - gam) - c0, hi1 = min(cl, wa.x + gam) - c0;
+            if (has_b) {
+              lo1 = min(lo1, max(c0, wb.x - gam) - c0);
+              hi1 = max(hi1, min(cl, wb.x + gam) - c0);
+            }
+            s0 = lo1 >> 4;
+            s1 = hi1 >> 4;
+          }
+          const int rho_a = c0 + 16 * s0 - wa.x + g.D0;
+          const int rho_b = c0 + 16 * s0 - wb.x + g.D0;        // >= rho_a
+          const uint32_t lbo = (uint32_t)(rho_b - rho_a) * 16u;
+          hdr_db[sl][0] = smem_desc(tbl_h + (uint32_t)rho_a * 16u, lbo, 128);
+          hdr_db[sl][1] = smem_desc(tbl_l + (uint32_t)rho_a * 16u, lbo, 128);
+          hdr_id[sl][0] = idesc_f16(16 * (s1 - s0 + 1));
+          hdr_id[sl][1] = (uint32_t)(16 * s0);
         }
         fence_proxy_async();
-        mbar_arrive(&bar_slot_full[s]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_slot_full[sl]);
+        if (++sl == g.ns) { sl = 0; slph ^= 1u; }
+        ++used;
       }
       if (!ok) break;
-      mbar_arrive(&bar_list_empty[b]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_list_empty[b]);
       ++pg;
     }
   } else {
@@ -471,37 +692,64 @@ assemble_kernel(const __grid_constant__ CUtensorMap tmap, const AsmArgs g) {
     const int ew = warp - WARP_EPI;
     const int q = warp & 3;                        // tensor-memory lanes 32q .. 32q+31
     const int half = ew >> 2;
-    const int cb = half * (g.Nc >> 1), ce = cb + (g.Nc >> 1);
-    const long long plane = (long long)n * n;
+    const int hw = g.Nc >> 1;
+    const int cb = half * hw, ce = cb + hw;
+    const float uT = ldexpf(1.0f, -s_shiftT), uW = ldexpf(1.0f, -(s_shiftA + s_shiftB));
+    float* stage = (float*)(smem + g.off_stage) + half * 32 * STG_ROW;
+    const int m = 32 * q + lane;
     for (int t = 0; t < njobs; ++t) {
-      const int T = j0 + t * jstride, t2 = T / g.nt3, t3 = T % g.nt3;
-      int ok = 1;
-      if (lane == 0) ok = wait_bar(&bar_d_full[t & 1], (t >> 1) & 1, abort_flag, sc);
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
+      const int T = j0 + t * jstride;
+      bool has_w = false;
+      if (g.rng) { const int2 rg = g.rng[(long long)T * g.nch + chunk]; has_w = rg.y > rg.x; }
+      if (!warp_wait(&bar_d_full[t & 1], (t >> 1) & 1, abort_flag, sc)) break;
       fence_after_sync();
-      const int i2 = t2 * AS_T2 + q, i3 = t3 * AS_T3 + lane;
-      const bool valid = i2 < n && i3 < n;
-      float* out = g.P + (long long)i2 * n + i3;
-      const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((t & 1) * g.dstride);
+      const long long p0 = (long long)T * AS_M;
+      const int cnt = (int)min((long long)AS_M, np - p0);
+      const uint32_t baseT = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((t & 1) * g.dstride);
+      const uint32_t baseW = baseT + (uint32_t)(2 * g.dstride);
       for (int c = cb; c < ce; c += 32) {
-        uint32_t v[32];
+        const int ncol = min(32, ce - c);
+        uint32_t vt[32], vw[32];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (c + 8 * u < ce) tmem_ld8(base + (uint32_t)(c + 8 * u), v + 8 * u);
-        tmem_wait_ld();
-        if (valid) {
+          if (8 * u < ncol) tmem_ld8(baseT + (uint32_t)(c + 8 * u), vt + 8 * u);
+        if (has_w) {
 #pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            const int i1 = c0 + c + u;
-            if (c + u < ce && i1 < n) __stcs(out + (long long)i1 * plane, __uint_as_float(v[u]));
+          for (int u = 0; u < 4; ++u)
+            if (8 * u < ncol) tmem_ld8(baseW + (uint32_t)(c + 8 * u), vw + 8 * u);
+        }
+        tmem_wait_ld();
+        // the bulk stores of the previous group have read the staging rows
+        if (lane < 8) bulk_wait_read();
+        named_sync(1 + half, 128);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (j < ncol) {
+            const long long a = (long long)(c0 + c + j) * np + p0;
+            float v = __uint_as_float(vt[j]) * uT;
+            if (has_w) v += __uint_as_float(vw[j]) * uW;
+            stage[j * STG_ROW + (int)(a & 3) + m] = v;
           }
+        }
+        fence_proxy_async();
+        named_sync(1 + half, 128);
+        const int j = 8 * q + lane;                // staging row written out by this lane
+        if (lane < 8 && j < ncol && c0 + c + j < n) {
+          const long long a = (long long)(c0 + c + j) * np + p0;
+          const int o = (int)(a & 3);
+          const long long as = a + ((4 - o) & 3), ae = (a + cnt) & ~3ll;
+          const float* row = stage + j * STG_ROW + o;
+          for (long long x = a; x < min(as, a + cnt); ++x) g.P[x] = row[x - a];
+          if (ae > as) bulk_store(g.P + as, row + (as - a), (uint32_t)((ae - as) * 4));
+          for (long long x = max(ae, as); x < a + cnt; ++x) g.P[x] = row[x - a];
+          bulk_commit();
         }
       }
       fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_d_empty[t & 1]);
     }
+    if (lane < 8) bulk_wait_all();
   }
   fence_before_sync();
   __syncthreads();
@@ -513,62 +761,80 @@ assemble_kernel(const __grid_constant__ CUtensorMap tmap, const AsmArgs g) {
 }
 
 // ------------------------------------------------------------------ window lists
-// For every output tile column (4 i2 x 32 i3 points, all i1) the particles whose window
+// For every output tile (128 consecutive points p = i2 n + i3, all i1) the particles whose window
 // (|i_l - j_l| <= gamma) reaches it, sorted by (j1, particle) so that the windows of one i1
-// chunk are a contiguous range and the summation order does not depend on scheduling.
-__global__ void wl_count_kernel(const int* __restrict__ jidx, const int* __restrict__ nz_idx,
-                                const DevScalars* sc, int n, int nt3, int* count) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= sc->n_nz) return;
-  const int p = nz_idx[m], g = sc->gamma;
-  const int j2 = jidx[3 * p + 1], j3 = jidx[3 * p + 2];
-  const int a2 = max(0, j2 - g) / AS_T2, b2 = min(n - 1, j2 + g) / AS_T2;
-  const int a3 = max(0, j3 - g) / AS_T3, b3 = min(n - 1, j3 + g) / AS_T3;
-  for (int t2 = a2; t2 <= b2; ++t2)
-    for (int t3 = a3; t3 <= b3; ++t3) atomicAdd(&count[t2 * nt3 + t3], 1);
+// chunk are a contiguous range and the summation order does not depend on scheduling.  One CTA
+// per tile scans the particles with nonzero charge (no global atomics).
+__device__ __forceinline__ bool reaches_tile(int j2, int j3, long long p0, long long p1, int n, int g) {
+  const int r0 = (int)(p0 / n), r1 = (int)(p1 / n);
+  for (int r = r0; r <= r1; ++r) {
+    const int lo3 = (r == r0) ? (int)(p0 - (long long)r * n) : 0;
+    const int hi3 = (r == r1) ? (int)(p1 - (long long)r * n) : n - 1;
+    if (j2 >= r - g && j2 <= r + g && j3 >= lo3 - g && j3 <= hi3 + g) return true;
+  }
+  return false;
 }
 
-__global__ void wl_fill_kernel(const int* __restrict__ jidx, const int* __restrict__ nz_idx,
-                               DevScalars* sc, int n, int nt3, const int* start, int* cursor,
-                               long long cap, long long* key) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= sc->n_nz) return;
-  const int p = nz_idx[m], g = sc->gamma;
-  const int j1 = jidx[3 * p], j2 = jidx[3 * p + 1], j3 = jidx[3 * p + 2];
-  const int a2 = max(0, j2 - g) / AS_T2, b2 = min(n - 1, j2 + g) / AS_T2;
-  const int a3 = max(0, j3 - g) / AS_T3, b3 = min(n - 1, j3 + g) / AS_T3;
-  const long long k = ((long long)j1 << 32) | (unsigned)p;
-  for (int t2 = a2; t2 <= b2; ++t2)
-    for (int t3 = a3; t3 <= b3; ++t3) {
-      const int T = t2 * nt3 + t3;
-      const long long pos = (long long)start[T] + atomicAdd(&cursor[T], 1);
-      if (pos < cap) key[pos] = k;
-      else atomicOr(&sc->flags, (unsigned)FLAG_WINDOWS);
-    }
-}
-
-// one CTA per tile column: bitonic sort of its keys, records, and the range of each i1 chunk
 __global__ void __launch_bounds__(256)
-wl_sort_kernel(const int* __restrict__ start, long long cap, const long long* __restrict__ key,
-               const int* __restrict__ jidx, const double* __restrict__ Z, DevScalars* sc, int n,
+wl_count_kernel(const int* __restrict__ jidx, const int* __restrict__ nz_idx, const double* __restrict__ Z,
+                DevScalars* sc, int n, int* count) {
+  __shared__ int wsum[8];
+  const int T = blockIdx.x, tid = threadIdx.x;
+  const long long np = (long long)n * n;
+  const long long p0 = (long long)T * AS_M, p1 = min(np, p0 + AS_M) - 1;
+  const int g = sc->gamma, nnz = sc->n_nz;
+  int cnt = 0;
+  for (int m = tid; m < nnz; m += 256) {
+    const int p = nz_idx[m];
+    cnt += reaches_tile(jidx[3 * p + 1], jidx[3 * p + 2], p0, p1, n, g) ? 1 : 0;
+    if (T == 0) atomicMax(&sc->zmax_bits, __float_as_uint(fabsf((float)Z[p])));
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((tid & 31) == 0) wsum[tid >> 5] = cnt;
+  __syncthreads();
+  if (tid == 0) {
+    int s = 0;
+    for (int w = 0; w < 8; ++w) s += wsum[w];
+    count[T] = s;
+  }
+}
+
+// one CTA per tile: collect its keys (j1 << 32 | particle), bitonic sort, write the records and
+// the range of each i1 chunk
+__global__ void __launch_bounds__(256)
+wl_fill_kernel(const int* __restrict__ start, long long cap, const int* __restrict__ jidx,
+               const int* __restrict__ nz_idx, const double* __restrict__ Z, DevScalars* sc, int n,
                int nch, int Nc, int4* rec, int2* rng) {
   __shared__ long long ks[WL_SORT_CAP];
+  __shared__ int fill;
   const int T = blockIdx.x, tid = threadIdx.x;
-  const long long s = min((long long)start[T], cap), e = min((long long)start[T + 1], cap);
-  int len = (int)(e - s);
-  const int g = sc->gamma;
-  if (len > WL_SORT_CAP) {
+  const long long np = (long long)n * n;
+  const long long p0 = (long long)T * AS_M, p1 = min(np, p0 + AS_M) - 1;
+  const int g = sc->gamma, nnz = sc->n_nz;
+  const long long s = start[T], e = start[T + 1];
+  const int len = (int)(e - s);
+  if (len > WL_SORT_CAP || e > cap) {
     if (tid == 0) atomicOr(&sc->flags, (unsigned)FLAG_WINDOWS);
-    for (int c = tid; c < nch; c += blockDim.x) rng[(long long)T * nch + c] = make_int2((int)s, (int)s);
+    for (int c = tid; c < nch; c += blockDim.x) rng[(long long)T * nch + c] = make_int2(0, 0);
     return;
   }
-  int m = 1;
-  while (m < len) m <<= 1;
-  for (int i = tid; i < m; i += blockDim.x) ks[i] = (i < len) ? key[s + i] : LLONG_MAX;
+  if (tid == 0) fill = 0;
   __syncthreads();
-  for (int k = 2; k <= m; k <<= 1)
+  for (int m = tid; m < nnz; m += 256) {
+    const int p = nz_idx[m];
+    const int j1 = jidx[3 * p];
+    if (reaches_tile(jidx[3 * p + 1], jidx[3 * p + 2], p0, p1, n, g)) {
+      const int pos = atomicAdd(&fill, 1);       // order is restored by the sort below
+      if (pos < len) ks[pos] = ((long long)j1 << 32) | (unsigned)p;
+    }
+  }
+  int m2 = 1;
+  while (m2 < len) m2 <<= 1;
+  for (int i = len + tid; i < m2; i += blockDim.x) ks[i] = LLONG_MAX;
+  __syncthreads();
+  for (int k = 2; k <= m2; k <<= 1)
     for (int jx = k >> 1; jx > 0; jx >>= 1) {
-      for (int i = tid; i < m; i += blockDim.x) {
+      for (int i = tid; i < m2; i += blockDim.x) {
         const int ixj = i ^ jx;
         if (ixj > i) {
           const long long a = ks[i], b = ks[ixj];
@@ -587,9 +853,10 @@ wl_sort_kernel(const int* __restrict__ start, long long cap, const long long* __
     const int lo_j = c * Nc - g, hi_j = min(n - 1, c * Nc + Nc - 1) + g;
     int lo = 0, hi = len;                       // first key with j1 >= lo_j
     while (lo < hi) { const int mid = (lo + hi) >> 1; if ((int)(ks[mid] >> 32) < lo_j) lo = mid + 1; else hi = mid; }
-    int lo2 = lo, hi2 = len;                    // first key with j1 > hi_j
-    while (lo2 < hi2) { const int mid = (lo2 + hi2) >> 1; if ((int)(ks[mid] >> 32) <= hi_j) lo2 = mid + 1; else hi2 = mid; }
-    rng[(long long)T * nch + c] = make_int2((int)(s + lo), (int)(s + lo2));
+    int lo2b = lo, hi2b = len;                  // first key with j1 > hi_j
+    while (lo2b < hi2b) { const int mid = (lo2b + hi2b) >> 1; if ((int)(ks[mid] >> 32) <= hi_j) lo2b = mid + 1; else hi2b = mid; }
+    rng[(long long)T * nch + c] = make_int2((int)(s + lo), (int)(s + lo2b));
+    if (lo2b > lo) atomicAdd(&sc->chunk_w[c], lo2b - lo);
   }
 }
 
@@ -616,18 +883,12 @@ __global__ void wl_scan_kernel(const int* count, int nt, int* start) {
 
 int launch_window_lists(Ctx& c) {
   if (c.R_s == 0) return 0;
-  const int nT = c.tc_nt2 * c.tc_nt3;
-  int grid = (c.maxN + 255) / 256;
-  if (grid < 1) grid = 1;
-  cudaMemsetAsync(c.wl_count, 0, sizeof(int) * (nT + 1), c.stream);
-  wl_count_kernel<<<grid, 256, 0, c.stream>>>(c.j, c.nz_idx, c.sc, c.n, c.tc_nt3, c.wl_count);
+  const int nT = c.tc_ntiles;
+  wl_count_kernel<<<nT, 256, 0, c.stream>>>(c.j, c.nz_idx, c.Z, c.sc, c.n, c.wl_count);
   wl_scan_kernel<<<1, 1024, 0, c.stream>>>(c.wl_count, nT, c.wl_start);
-  cudaMemsetAsync(c.wl_count, 0, sizeof(int) * (nT + 1), c.stream);
-  wl_fill_kernel<<<grid, 256, 0, c.stream>>>(c.j, c.nz_idx, c.sc, c.n, c.tc_nt3, c.wl_start,
-                                             c.wl_count, c.wl_cap, c.wl_key);
-  wl_sort_kernel<<<nT, 256, 0, c.stream>>>(c.wl_start, c.wl_cap, c.wl_key, c.j, c.Z, c.sc, c.n,
+  wl_fill_kernel<<<nT, 256, 0, c.stream>>>(c.wl_start, c.wl_cap, c.j, c.nz_idx, c.Z, c.sc, c.n,
                                            c.tc_nch, c.tc_Nc, c.wl_rec, c.wl_rng);
-  return 4;
+  return 3;
 }
 
 // ------------------------------------------------------------------ host planning
@@ -660,67 +921,88 @@ int host_gamma(const Ctx& c) {
 
 inline size_t al128(size_t x) { return (x + 127) & ~(size_t)127; }
 
+struct Layout {
+  size_t bv_half, a_half, tbl_half, tab, list, stage;
+  int TR, D0;
+};
+
+Layout layout_of(const Ctx& c) {
+  Layout L;
+  L.bv_half = al128((size_t)c.tc_Nc * c.tc_kpad * 2);
+  L.a_half = (size_t)AS_M * c.tc_kpad * 2;
+  L.D0 = c.tc_Nc + c.gamma_cap;
+  L.TR = L.D0 + c.tc_Nc + c.gamma_cap + 16;
+  L.tbl_half = al128((size_t)L.TR * 16);
+  L.tab = al128((size_t)c.R_s * (2 * c.gamma_cap + 1) * 4);
+  L.list = (size_t)2 * LIST_CAP * 16;
+  L.stage = (size_t)2 * 32 * STG_ROW * 4;
+  return L;
+}
+
+size_t smem_total(const Layout& L, int na, int ns) {
+  return 2 * L.bv_half + (size_t)na * 2 * L.a_half + (size_t)ns * 2 * SLOT_HALF + 2 * L.tbl_half + L.tab +
+         L.list + L.stage;
+}
+
 }  // namespace
 
 bool plan_assemble(Ctx& c) {
   if (c.fp64) return false;
   const char* env = std::getenv("RS_RECON_PATH");
   if (env && std::strcmp(env, "cuda") == 0) return false;
+  if (c.R_s > 8) return false;                            // one 8-wide K chunk per window
   const int n = c.n;
   const int gh = host_gamma(c);
   c.gamma_cap = gh + 1 < n - 1 ? gh + 1 : n - 1;
-  c.tc_kpad = (c.rmax + 7) & ~7;
-  c.tc_K8 = c.R_s > 8 ? 16 : 8;
+  c.tc_kpad = (c.rmax + 15) & ~15;
   c.tc_nch = (n + 127) / 128;
   const int per = (n + c.tc_nch - 1) / c.tc_nch;
   c.tc_Nc = (per + 15) & ~15;
-  c.tc_nt2 = (n + AS_T2 - 1) / AS_T2;
-  c.tc_nt3 = (n + AS_T3 - 1) / AS_T3;
-  if (c.tc_kpad > 256) return false;                       // TMA box extent
-  const size_t sz_b = al128((size_t)c.tc_Nc * c.tc_kpad * 4);
-  const size_t sz_a = al128((size_t)AS_M * c.tc_kpad * 4);
-  const size_t slot = al128((size_t)2 * (AS_M + c.tc_Nc) * c.tc_K8 * 4);
-  const size_t sz_tab = al128((size_t)c.R_s * (2 * c.gamma_cap + 1) * 4);
-  const size_t total = 2 * sz_b + 3 * sz_a + 2 * slot + sz_tab + (size_t)2 * LIST_CAP * 16;
-  if (total > (size_t)(SMEM_LIMIT - SMEM_RESERVE)) return false;
-  c.tc_smem = total;
-  const long long touch2 = std::min<long long>(c.tc_nt2, (2 * c.gamma_cap) / AS_T2 + 2);
-  const long long touch3 = std::min<long long>(c.tc_nt3, (2 * c.gamma_cap) / AS_T3 + 2);
-  long long cap = (long long)c.maxN * touch2 * touch3;
+  c.tc_ntiles = (int)(((long long)n * n + AS_M - 1) / AS_M);
+  if (c.tc_nch > 32) return false;
+  const Layout L = layout_of(c);
+  const size_t limit = (size_t)(SMEM_LIMIT - SMEM_RESERVE);
+  const int choices[6][2] = {{2, 8}, {2, 6}, {2, 4}, {1, 4}, {1, 2}, {1, 1}};
+  c.tc_na = 0;
+  for (auto& ch : choices)
+    if (smem_total(L, ch[0], ch[1]) <= limit) { c.tc_na = ch[0]; c.tc_ns = ch[1]; break; }
+  if (c.tc_na == 0) return false;
+  c.tc_smem = smem_total(L, c.tc_na, c.tc_ns);
+  // the T2 tile kernel stages 8 rank slices of T1 for 32 i3 plus 32 rows of V2
+  if ((size_t)1152 * c.rmax > limit) return false;
+  // window list entries: every particle reaches at most the tiles of 2 gamma + 1 rows of
+  // n points plus one tile
+  const long long per_particle = ((long long)(2 * c.gamma_cap + 1) * n + AS_M - 1) / AS_M + 2;
+  long long cap = (long long)c.maxN * std::min<long long>(c.tc_ntiles, per_particle);
   if (cap < 1) cap = 1;
   if (cap > INT_MAX / 2) return false;
   c.wl_cap = cap;
-  c.t2_ld = (n + 3) & ~3;
   return true;
 }
 
-bool encode_t2_map(Ctx& c, std::string& err) {
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-          cudaSuccess ||
-      q != cudaDriverEntryPointSuccess || !fn) {
-    cudaGetLastError();
-    err = "cuTensorMapEncodeTiled not available";
-    return false;
+size_t t2_tile_bytes(const Ctx& c) {
+  return (size_t)c.tc_ntiles * 2 * layout_of(c).a_half;
+}
+
+int launch_t2_tiles(Ctx& c) {
+  static bool attr = false;
+  const size_t shm = (size_t)1152 * c.rmax;
+  if (!attr) {
+    cudaFuncSetAttribute(t2_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMEM_LIMIT - SMEM_RESERVE));
+    attr = true;
   }
-  auto enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  const cuuint64_t dims[3] = {(cuuint64_t)c.n, (cuuint64_t)c.n, (cuuint64_t)c.rmax};
-  const cuuint64_t strides[2] = {(cuuint64_t)c.t2_ld * 4, (cuuint64_t)c.n * c.t2_ld * 4};
-  const cuuint32_t box[3] = {AS_T3, AS_T2, (cuuint32_t)c.tc_kpad};
-  const cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(&c.tmap_T2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c.T2, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    err = "cuTensorMapEncodeTiled rejected the T2 view";
-    return false;
-  }
-  return true;
+  const dim3 grid((c.n + AS_T3 - 1) / AS_T3, (c.n + TT_ROWS - 1) / TT_ROWS);
+  t2_tiles_kernel<<<grid, 256, shm, c.stream>>>((const float*)c.T1, c.Z32 + (size_t)c.n * c.rmax, c.n,
+                                                c.rmax, c.tc_kpad, c.tc_ntiles, c.sc,
+                                                (unsigned char*)c.T2, 2 * layout_of(c).a_half);
+  return 1;
 }
 
 int launch_assemble(Ctx& c, float* out) {
+  const Layout L = layout_of(c);
   AsmArgs g;
+  g.T2t = (const unsigned char*)c.T2;
+  g.tile_bytes = 2 * L.a_half;
   g.V1 = c.Z32;
   g.ldv = c.rmax;
   g.pk = c.pk32;
@@ -734,38 +1016,35 @@ int launch_assemble(Ctx& c, float* out) {
   g.R_s = c.R_s;
   g.nch = c.tc_nch;
   g.Nc = c.tc_Nc;
-  g.kpad = c.tc_kpad;
-  g.K8 = c.tc_K8;
+  g.kp = c.tc_kpad;
   g.gcap = c.gamma_cap;
-  g.nt3 = c.tc_nt3;
-  g.ntiles = c.tc_nt2 * c.tc_nt3;
+  g.TR = L.TR;
+  g.D0 = L.D0;
+  g.ntiles = c.tc_ntiles;
   int ds = 16;
   while (ds < c.tc_Nc) ds <<= 1;
   g.dstride = ds;
-  g.tmem_cols = 2 * ds < 32 ? 32 : 2 * ds;
-  const size_t sz_b = al128((size_t)c.tc_Nc * c.tc_kpad * 4);
-  const size_t sz_a = al128((size_t)AS_M * c.tc_kpad * 4);
-  const size_t slot = al128((size_t)2 * (AS_M + c.tc_Nc) * c.tc_K8 * 4);
-  const size_t sz_tab = al128((size_t)c.R_s * (2 * c.gamma_cap + 1) * 4);
-  g.off_bh = 0;
-  g.off_bl = (uint32_t)sz_b;
-  g.off_raw = (uint32_t)(2 * sz_b);
-  g.off_ah = (uint32_t)(2 * sz_b + sz_a);
-  g.off_al = (uint32_t)(2 * sz_b + 2 * sz_a);
-  g.off_slot = (uint32_t)(2 * sz_b + 3 * sz_a);
-  g.slot_bytes = (uint32_t)slot;
-  g.off_tab = (uint32_t)(2 * sz_b + 3 * sz_a + 2 * slot);
-  g.off_list = (uint32_t)(2 * sz_b + 3 * sz_a + 2 * slot + sz_tab);
+  g.tmem_cols = 4 * ds < 32 ? 32 : 4 * ds;
+  g.na = c.tc_na;
+  g.ns = c.tc_ns;
+  g.off_bv = 0;
+  g.off_a = (uint32_t)(2 * L.bv_half);
+  g.off_slot = (uint32_t)(g.off_a + (size_t)c.tc_na * 2 * L.a_half);
+  g.off_tbl = (uint32_t)(g.off_slot + (size_t)c.tc_ns * 2 * SLOT_HALF);
+  g.off_tab = (uint32_t)(g.off_tbl + 2 * L.tbl_half);
+  g.off_list = (uint32_t)(g.off_tab + L.tab);
+  g.off_stage = (uint32_t)(g.off_list + L.list);
+  g.bv_half = (uint32_t)L.bv_half;
+  g.a_half = (uint32_t)L.a_half;
+  g.tbl_half = (uint32_t)L.tbl_half;
   if (c.tc_grid == 0) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms < 1) sms = 1;
-    const int per_chunk = sms / c.tc_nch > 0 ? sms / c.tc_nch : 1;
-    c.tc_grid = c.tc_nch * per_chunk;
+    c.tc_grid = sms > c.tc_nch ? sms : c.tc_nch;
     cudaFuncSetAttribute(assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.tc_smem);
   }
-  assemble_kernel<<<c.tc_grid, AS_THREADS, c.tc_smem, c.stream>>>(c.tmap_T2, g);
+  assemble_kernel<<<c.tc_grid, AS_THREADS, c.tc_smem, c.stream>>>(g);
   return 1;
 }
 

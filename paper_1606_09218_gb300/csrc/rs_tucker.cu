@@ -149,10 +149,23 @@ core_kernel(const T* __restrict__ Qp, const int* __restrict__ jidx, const int* _
   }
 }
 
+// beta in the bulk type, and ||beta[a, :, :]||^2 per slice a (block partial sums in shared
+// memory, one global atomic per slice and block)
 template <typename T>
-__global__ void convert_beta_kernel(const double* beta64, T* beta, long long tot) {
+__global__ void convert_beta_kernel(const double* beta64, T* beta, long long tot, int rmax,
+                                    DevScalars* sc) {
+  __shared__ double acc[RMAX_LIMIT];
+  for (int a = threadIdx.x; a < rmax; a += blockDim.x) acc[a] = 0.0;
+  __syncthreads();
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < tot) beta[e] = (T)beta64[e];
+  if (e < tot) {
+    const double v = beta64[e];
+    beta[e] = (T)v;
+    if (v != 0.0) atomicAdd(&acc[e / ((long long)rmax * rmax)], v * v);
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < rmax; a += blockDim.x)
+    if (acc[a] != 0.0) atomicAdd(&sc->beta_a2[a], acc[a]);
 }
 
 // adims[a] = n for a < r_1 (batches of the mode-2 product that carry data), else 0;
@@ -178,13 +191,15 @@ static int projection_core_t(Ctx& c) {
   int ksplit = 16;
   dim3 g2(ta * tb * tb, ksplit);
   core_kernel<T><<<g2, 256, 0, c.stream>>>(Qp, c.j, c.nz_idx, c.Z, n, rmax, c.R_l, c.sc, c.beta64);
-  convert_beta_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(c.beta64, (T*)c.beta, tot);
+  convert_beta_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(c.beta64, (T*)c.beta, tot,
+                                                                                rmax, c.sc);
   // T1[a][b][i3] = sum_c beta[a][b][c] V3[i3][c]      (rows (a,b), K = r3)
   const T* Zb = Bulk<T>::Z(c);
   const long long sZ = (long long)n * rmax;
   gemm_batched<T>(c.stream, false, true, rmax * rmax, n, rmax, T(1), (const T*)c.beta, rmax, 0,
                   Zb + 2 * sZ, rmax, 0, T(0), (T*)c.T1, n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 2);
   // T2[a][i2][i3] = sum_b V2[i2][b] T1[a][b][i3]        (batch a < r1, K = r2)
+  if (c.use_tc && !c.fp64) return 4 + launch_t2_tiles(c);   // tiled FP16 operands
   batch_dims_kernel<<<(rmax + 127) / 128, 128, 0, c.stream>>>(c.adims, c.kdims, rmax, n, c.sc);
   gemm_batched<T>(c.stream, false, false, n, n, rmax, T(1), Zb + sZ, rmax, 0, (const T*)c.T1, n,
                   (long long)rmax * n, T(0), (T*)c.T2, c.t2_ld, (long long)n * c.t2_ld, rmax, 1,
