@@ -65,7 +65,7 @@ constexpr long long WAIT_LIMIT = 4000000;
 constexpr int SMEM_LIMIT = 232448;         // opt-in shared memory per CTA on this GPU family
 constexpr int SMEM_RESERVE = 1024;         // static shared memory of the kernel
 constexpr double COST_TILE = 2500.0;       // relative cost of one tile job (output bound)
-constexpr double COST_WINDOW = 120.0;      // relative cost of one window of a job
+constexpr double COST_WINDOW = 60.0;       // relative cost of one window of a job
 constexpr int TT_ROWS = 32;                // i2 rows per CTA of the T2 tile kernel
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -153,10 +153,11 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 
 // split a pair of FP32 values into FP16 hi / lo pairs (first value in the low half)
 __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-  const __half l0 = __float2half_rn(x0 - __half2float(h0)), l1 = __float2half_rn(x1 - __half2float(h1));
-  hi = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-  lo = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // eight FP32 values -> 16 bytes of FP16 hi and 16 bytes of FP16 lo
@@ -452,7 +453,7 @@ assemble_kernel(const AsmArgs g) {
   const int c0 = chunk * g.Nc;
   const int cl = min(n, c0 + g.Nc) - 1;                 // last i1 row of this chunk
   const int njobs = (gam <= g.gcap && j0 < g.ntiles && c0 < n) ? (g.ntiles - 1 - j0) / jstride + 1 : 0;
-  const int tw = 2 * g.gcap + 1;                        // row length of the FP32 factor rows
+  const int tw = 2 * g.gcap + 1;                        // rows d = -gcap .. gcap of the FP32 factors
   unsigned char* Bh = smem + g.off_bv;
   unsigned char* Bl = Bh + g.bv_half;
   unsigned char* Th = smem + g.off_tbl;
@@ -461,8 +462,8 @@ assemble_kernel(const AsmArgs g) {
   int4* lists = (int4*)(smem + g.off_list);
 
   // one-time staging by the whole CTA: the V1 rows of this chunk (B of the Tucker part, FP16
-  // hi / lo, scaled by 2^8), the short-range factor rows p_k[d] (FP32, for the A operands of the
-  // windows) and the factor table (B of the windows, FP16 hi / lo scaled by 2^sB, one 16-byte
+  // hi / lo, scaled by 2^8), the short-range factors p_k[d] (FP32, 8 ranks per row d, for the A
+  // operands of the windows) and the factor table (B of the windows, FP16 hi / lo scaled by 2^sB, one 16-byte
   // row of 8 ranks per d = rho - D0)
   if (njobs > 0) {
     const int kc = g.kp >> 3;
@@ -480,9 +481,9 @@ assemble_kernel(const AsmArgs g) {
       *(uint4*)(Bh + off) = hi;
       *(uint4*)(Bl + off) = lo;
     }
-    for (int e = tid; e < g.R_s * tw; e += AS_THREADS) {
-      const int k = e / tw, d = e % tw - g.gcap;
-      tab[e] = (d >= -gam && d <= gam) ? g.pk[(long long)(g.R_l + k) * g.L + (n - 1) + d] : 0.f;
+    for (int e = tid; e < 8 * tw; e += AS_THREADS) {
+      const int k = e & 7, d = (e >> 3) - g.gcap;
+      tab[e] = (k < g.R_s && d >= -gam && d <= gam) ? g.pk[(long long)(g.R_l + k) * g.L + (n - 1) + d] : 0.f;
     }
     const float sBf = ldexpf(1.0f, s_shiftB);
     for (int rho = tid; rho < g.TR; rho += AS_THREADS) {
@@ -639,14 +640,15 @@ assemble_kernel(const AsmArgs g) {
           const float z = __int_as_float(rc.w) * sA;
           const int d2 = i2 - rc.y, d3 = i3 - rc.z;
           const bool in23 = live && d2 >= -gam && d2 <= gam && d3 >= -gam && d3 <= gam;
-          const float* t2row = tab + (d2 + g.gcap);
-          const float* t3row = tab + (d3 + g.gcap);
-          float x[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            x[k] = (in23 && k < g.R_s) ? z * t2row[k * tw] * t3row[k * tw] : 0.f;
+          const float4* r2 = (const float4*)tab + 2 * (in23 ? d2 + g.gcap : 0);
+          const float4* r3 = (const float4*)tab + 2 * (in23 ? d3 + g.gcap : 0);
+          const float4 a0 = r2[0], a1 = r2[1], b0 = r3[0], b1 = r3[1];
+          const float zz = in23 ? z : 0.f;
           uint4 hi, lo;
-          split8_f16(x, hi, lo);
+          split_h2(zz * a0.x * b0.x, zz * a0.y * b0.y, hi.x, lo.x);
+          split_h2(zz * a0.z * b0.z, zz * a0.w * b0.w, hi.y, lo.y);
+          split_h2(zz * a1.x * b1.x, zz * a1.y * b1.y, hi.z, lo.z);
+          split_h2(zz * a1.z * b1.z, zz * a1.w * b1.w, hi.w, lo.w);
           const uint32_t off = kmajor_offset(pt, w, 2);
           *(uint4*)(sbh + off) = hi;
           *(uint4*)(sbl + off) = lo;
@@ -722,13 +724,13 @@ assemble_kernel(const AsmArgs g) {
         // the bulk stores of the previous group have read the staging rows
         if (lane < 8) bulk_wait_read();
         named_sync(1 + half, 128);
+        const int o0 = (int)((((long long)(c0 + c)) * np + p0) & 3), ostep = (int)(np & 3);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           if (j < ncol) {
-            const long long a = (long long)(c0 + c + j) * np + p0;
             float v = __uint_as_float(vt[j]) * uT;
-            if (has_w) v += __uint_as_float(vw[j]) * uW;
-            stage[j * STG_ROW + (int)(a & 3) + m] = v;
+            if (has_w) v = fmaf(__uint_as_float(vw[j]), uW, v);
+            stage[j * STG_ROW + ((o0 + j * ostep) & 3) + m] = v;
           }
         }
         fence_proxy_async();
@@ -933,7 +935,7 @@ Layout layout_of(const Ctx& c) {
   L.D0 = c.tc_Nc + c.gamma_cap;
   L.TR = L.D0 + c.tc_Nc + c.gamma_cap + 16;
   L.tbl_half = al128((size_t)L.TR * 16);
-  L.tab = al128((size_t)c.R_s * (2 * c.gamma_cap + 1) * 4);
+  L.tab = al128((size_t)8 * (2 * c.gamma_cap + 1) * 4);
   L.list = (size_t)2 * LIST_CAP * 16;
   L.stage = (size_t)2 * 32 * STG_ROW * 4;
   return L;
