@@ -15,61 +15,68 @@ template <> struct Bulk<double> { static const double* pk(const Ctx& c) { return
 
 // ------------------------------------------------------------------ projection
 // Qp[l][j][k][a] = sum_i Z_l[i][a] p_k[i - j]   (Z0^(l)^T applied to the shifted reference
-// factors; the projected side matrix is U~^(l)[a, (nu,k)] = w_nu Qp[l][j_l^(nu)][k][a]).
+// factors; the projected side matrix is U~^(l)[a, (nu,k)] = w_nu Qp[l][j_l^(nu)][k][a]).  Only the
+// coordinates j that carry charge (the compacted list nzj) are computed; a >= r_l is zero.
+// CTA: 64 rows j x 64 columns a for one (l, k); thread: 4 j x 4 a; K = i in chunks of 32 with
+// the full factor row p_k in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256)
-proj_kernel(const T* __restrict__ Zb, const T* __restrict__ pk, int n, int rmax, int R_l,
-            const DevScalars* sc, T* Qp) {
-  const int l = blockIdx.z, k = blockIdx.y, j0 = blockIdx.x * 32;
-  const int r = sc->rank[l];
-  if (r == 0) return;
+proj_kernel(const T* __restrict__ Zb, const T* __restrict__ pk, const int* __restrict__ nzj, int n,
+            int rmax, int R_l, const DevScalars* sc, T* Qp) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  T* sp = (T*)psm;                                   // p_k[d], d = -(n-1) .. n-1
+  T* sV = sp + ((2 * n - 1 + 3) & ~3);               // [32][64] slice of Z_l
+  const int l = blockIdx.z, k = blockIdx.y;
+  const int nat = (rmax + 63) / 64;
+  const int j0 = (blockIdx.x / nat) * 64, a0 = (blockIdx.x % nat) * 64;
+  const int cnt = sc->nzj_count[l], r = sc->rank[l];
+  if (j0 >= cnt) return;
   const int L = 2 * n - 1;
-  const int al = threadIdx.x % 32, jl = threadIdx.x / 32;
-  const int na = (r + 31) / 32;     // a-groups in use (<= rmax/32)
-  __shared__ T sZ[32][161];
-  __shared__ T sp[64];
-  T acc[4][5];
+  const int tid = threadIdx.x, tj = tid >> 4, ta = tid & 15;
+  int jj[4];
 #pragma unroll
-  for (int s = 0; s < 4; ++s)
+  for (int x = 0; x < 4; ++x) {
+    const int idx = j0 + 4 * tj + x;
+    jj[x] = idx < cnt ? nzj[l * n + idx] : -1;
+  }
+  T acc[4][4];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) acc[s][q] = T(0);
-  const T* Zl = Zb + (long long)l * n * rmax;
-  const T* pkk = pk + (long long)k * L;
-  for (int i0 = 0; i0 < n; i0 += 32) {
-    for (int e = threadIdx.x; e < 32 * na * 32; e += 256) {
-      int ii = e / (na * 32), a = e % (na * 32);
-      int i = i0 + ii;
-      sZ[ii][a] = (i < n && a < rmax) ? Zl[(long long)i * rmax + a] : T(0);
-    }
-    // p_k[i - j] for i in [i0, i0+32), j in [j0, j0+32): offsets i - j in [i0-j0-31, i0-j0+31]
-    if (threadIdx.x < 63) {
-      int d = i0 - j0 - 31 + threadIdx.x;
-      int idx = d + n - 1;
-      sp[threadIdx.x] = (idx >= 0 && idx < L) ? pkk[idx] : T(0);
-    }
-    __syncthreads();
-    const int ilim = min(32, n - i0);
-    for (int ii = 0; ii < ilim; ++ii) {
+  for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        int jj = jl + 8 * s;                      // j = j0 + jj
-        T f = sp[ii - jj + 31];
+    for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+  if (a0 < r) {
+    const T* pkk = pk + (long long)k * L;
+    for (int e = tid; e < L; e += 256) sp[e] = pkk[e];
+    const T* Zl = Zb + (long long)l * n * rmax;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      __syncthreads();
+      for (int e = tid; e < 32 * 64; e += 256) {
+        const int ii = e >> 6, aa = e & 63, i = i0 + ii, a = a0 + aa;
+        sV[e] = (i < n && a < r) ? Zl[(long long)i * rmax + a] : T(0);
+      }
+      __syncthreads();
+      const int ilim = min(32, n - i0);
+      for (int ii = 0; ii < ilim; ++ii) {
+        const int i = i0 + ii;
+        T v[4], pj[4];
 #pragma unroll
-        for (int q = 0; q < 5; ++q)
-          if (q < na) acc[s][q] = fma(sZ[ii][al + 32 * q], f, acc[s][q]);
+        for (int y = 0; y < 4; ++y) v[y] = sV[ii * 64 + 4 * ta + y];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) pj[x] = jj[x] >= 0 ? sp[i - jj[x] + n - 1] : T(0);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fma(pj[x], v[y], acc[x][y]);
       }
     }
-    __syncthreads();
   }
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    int j = j0 + jl + 8 * s;
-    if (j >= n) continue;
+  for (int x = 0; x < 4; ++x) {
+    if (jj[x] < 0) continue;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      int a = al + 32 * q;
-      if (a < rmax && q < (rmax + 31) / 32)
-        Qp[(((long long)l * n + j) * R_l + k) * rmax + a] = (a < r) ? acc[s][q] : T(0);
+    for (int y = 0; y < 4; ++y) {
+      const int a = a0 + 4 * ta + y;
+      if (a < rmax) Qp[(((long long)l * n + jj[x]) * R_l + k) * rmax + a] = (a < r) ? acc[x][y] : T(0);
     }
   }
 }
@@ -77,95 +84,170 @@ proj_kernel(const T* __restrict__ Zb, const T* __restrict__ pk, int n, int rmax,
 // ------------------------------------------------------------------ core
 // beta[a][b][c] = sum_{p nonzero} z_p sum_{k long} Qp1[j1][k][a] Qp2[j2][k][b] Qp3[j3][k][c]
 // (Eq. (6.2): beta = xi x_1 U~1 x_2 U~2 x_3 U~3 with xi = sign z and w^3 = |z|).
-// CTA tile: 32 a x (8 b x 8 c); K = (particle, k) split over gridDim.y; FP32 products are
-// summed in chunks of 64 K-elements and the chunks accumulated in FP64.
+// CTA tile: 64 a x 4 b x 32 c over a slice of K = (particle, k); thread: 4 a x 1 b x 8 c.
+// FP32 path: products in FP32, each 32-term chunk added to a (hi, lo) FP32 pair with an
+// error-free two-sum, so the K sum carries about twice the FP32 precision; the CTA's partial
+// sums are added to beta64 in FP64.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+
+constexpr int CORE_KMAX = 1024;           // K elements of one CTA (row offsets kept in shared memory)
+
 template <typename T>
-__global__ void __launch_bounds__(256)
+constexpr size_t core_smem_bytes() {
+  return sizeof(T) * (2 * 32 * 100 + CORE_KMAX) + sizeof(int) * 3 * CORE_KMAX;
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool in) {
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(in ? 4 : 0) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(in ? 8 : 0) : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2)
 core_kernel(const T* __restrict__ Qp, const int* __restrict__ jidx, const int* __restrict__ nz_idx,
             const double* __restrict__ Z, int n, int rmax, int R_l, const DevScalars* sc,
             double* beta64) {
   const int r1 = sc->rank[0], r2 = sc->rank[1], r3 = sc->rank[2];
-  const int ta = (rmax + 31) / 32, tb = (rmax + 7) / 8;
+  const int nbt = (rmax + 3) / 4, nct = (rmax + 31) / 32;
   int bt = blockIdx.x;
-  const int tcI = bt % tb; bt /= tb;
-  const int tbI = bt % tb; bt /= tb;
-  const int taI = bt;
-  if (taI >= ta) return;
-  const int a0 = taI * 32, b0 = tbI * 8, c0 = tcI * 8;
+  const int cI = bt % nct; bt /= nct;
+  const int bI = bt % nbt; bt /= nbt;
+  const int a0 = bt * 64, b0 = bI * 4, c0 = cI * 32;
   if (a0 >= r1 || b0 >= r2 || c0 >= r3) return;
   const int nnz = sc->n_nz;
   const long long Ktot = (long long)nnz * R_l;
   const long long per = (Ktot + gridDim.y - 1) / gridDim.y;
   const long long kb = blockIdx.y * per, ke = min(Ktot, kb + per);
   if (kb >= ke) return;
-  __shared__ T sA[32][33];
-  __shared__ T sB[32][8];
-  __shared__ T sC[32][8];
-  const int a = threadIdx.x % 32, bl = threadIdx.x / 32;     // b = b0 + bl; c loops
-  T acc[8];
-  double acc64[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) { acc[q] = T(0); acc64[q] = 0.0; }
+  extern __shared__ __align__(16) unsigned char csm[];
+  T (*s1)[32][64] = (T(*)[32][64])csm;                          // [2][32][64]
+  T (*s2)[32][4] = (T(*)[32][4])(csm + sizeof(T) * 2 * 32 * 64);  // [2][32][4]
+  T (*s3)[32][32] = (T(*)[32][32])(csm + sizeof(T) * 2 * 32 * 68);  // [2][32][32]
+  T* zK = (T*)(csm + sizeof(T) * 2 * 32 * 100);                 // [CORE_KMAX]
+  int* off1 = (int*)(csm + sizeof(T) * (2 * 32 * 100 + CORE_KMAX));
+  int* off2 = off1 + CORE_KMAX;
+  int* off3 = off2 + CORE_KMAX;
+  const int tid = threadIdx.x;
+  const int nK = (int)(ke - kb);                  // <= CORE_KMAX (host sizes the split)
   const long long sL = (long long)n * R_l * rmax;
-  int chunk_count = 0;
-  for (long long K0 = kb; K0 < ke; K0 += 32) {
-    // stage 32 K-elements
-    {
-      int kk = threadIdx.x / 8, part = threadIdx.x % 8;   // 32 x 8 loaders
-      long long K = K0 + kk;
-      bool ok = K < ke;
-      int p = ok ? nz_idx[K / R_l] : 0;
-      int k = ok ? (int)(K % R_l) : 0;
-      T z = ok ? (T)Z[p] : T(0);
-      int j1 = jidx[3 * p], j2 = jidx[3 * p + 1], j3 = jidx[3 * p + 2];
-      const T* q1 = Qp + (((long long)0 * n + j1) * R_l + k) * rmax + a0;
-      const T* q2 = Qp + sL + ((long long)j2 * R_l + k) * rmax + b0;
-      const T* q3 = Qp + 2 * sL + ((long long)j3 * R_l + k) * rmax + c0;
-      for (int q = part; q < 32; q += 8) sA[kk][q] = (ok && a0 + q < rmax) ? q1[q] : T(0);
-      sB[kk][part] = (ok && b0 + part < rmax) ? z * q2[part] : T(0);
-      sC[kk][part] = (ok && c0 + part < rmax) ? q3[part] : T(0);
+  // row offsets of the three projected factors and the charge, for every K of this CTA
+  for (int e = tid; e < nK; e += 256) {
+    const long long K = kb + e;
+    const int p = nz_idx[K / R_l], k = (int)(K % R_l);
+    off1[e] = (int)(((long long)jidx[3 * p] * R_l + k) * rmax);
+    off2[e] = (int)(sL + ((long long)jidx[3 * p + 1] * R_l + k) * rmax);
+    off3[e] = (int)(2 * sL + ((long long)jidx[3 * p + 2] * R_l + k) * rmax);
+    zK[e] = (T)Z[p];
+  }
+  __syncthreads();
+  // gathers of one chunk of 32 K into buffer bf (zero outside K range / ranks)
+  auto stage = [&](int ch, int bf) {
+    for (int e = tid; e < 32 * 100; e += 256) {
+      const int kk = e / 100, part = e - kk * 100;
+      const int kl = ch * 32 + kk;
+      const bool ok = kl < nK;
+      if (part < 64) {
+        const int a = a0 + part;
+        cp_async_elem(&s1[bf][kk][part], Qp + (ok ? off1[kl] + a : 0), ok && a < rmax);
+      } else if (part < 68) {
+        const int b = b0 + part - 64;
+        cp_async_elem(&s2[bf][kk][part - 64], Qp + (ok ? off2[kl] + b : 0), ok && b < rmax);
+      } else {
+        const int c = c0 + part - 68;
+        cp_async_elem(&s3[bf][kk][part - 68], Qp + (ok ? off3[kl] + c : 0), ok && c < rmax);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const int ta = tid & 15, tb = (tid >> 4) & 3, tc = tid >> 6;    // 4 a x 1 b x 8 c per thread
+  T acc[4][8];
+  T hi[4][8], lo[4][8];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 8; ++y) { acc[x][y] = T(0); hi[x][y] = T(0); lo[x][y] = T(0); }
+  const int nch = (nK + 31) / 32;
+  stage(0, 0);
+  for (int ch = 0; ch < nch; ++ch) {
+    const int bf = ch & 1;
+    if (ch + 1 < nch) {
+      stage(ch + 1, bf ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < 32; ++kk) {
-      T ab = sA[kk][a] * sB[kk][bl];
+      const int kl = ch * 32 + kk;
+      const T zb = (kl < nK ? zK[kl] : T(0)) * s2[bf][kk][tb];
+      T t[4], q3[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q] = fma(ab, sC[kk][q], acc[q]);
-    }
-    __syncthreads();
-    if (++chunk_count == 2) {
+      for (int x = 0; x < 4; ++x) t[x] = s1[bf][kk][4 * ta + x] * zb;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) { acc64[q] += (double)acc[q]; acc[q] = T(0); }
-      chunk_count = 0;
+      for (int y = 0; y < 8; ++y) q3[y] = s3[bf][kk][8 * tc + y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = fma(t[x], q3[y], acc[x][y]);
     }
+    // fold the chunk sum into the (hi, lo) pair
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        if (sizeof(T) == 4) two_sum_add(*(float*)&hi[x][y], *(float*)&lo[x][y], (float)acc[x][y]);
+        else hi[x][y] += acc[x][y];
+        acc[x][y] = T(0);
+      }
+    __syncthreads();                              // buffer bf is refilled two chunks later
   }
-  const int aa = a0 + a, bb = b0 + bl;
-  if (aa < r1 && bb < r2) {
+  const int bb = b0 + tb;
+  if (bb >= r2) return;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int cc = c0 + q;
-      if (cc < r3) atomicAdd(&beta64[((long long)aa * rmax + bb) * rmax + cc], acc64[q] + (double)acc[q]);
+  for (int x = 0; x < 4; ++x) {
+    const int aa = a0 + 4 * ta + x;
+    if (aa >= r1) continue;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      const int cc = c0 + 8 * tc + y;
+      if (cc < r3) atomicAdd(&beta64[((long long)aa * rmax + bb) * rmax + cc], (double)hi[x][y] + (double)lo[x][y]);
     }
   }
 }
 
-// beta in the bulk type, and ||beta[a, :, :]||^2 per slice a (block partial sums in shared
-// memory, one global atomic per slice and block)
+// beta in the bulk type, and ||beta[a, :, :]||^2 per slice a (one CTA per slice)
 template <typename T>
-__global__ void convert_beta_kernel(const double* beta64, T* beta, long long tot, int rmax,
-                                    DevScalars* sc) {
-  __shared__ double acc[RMAX_LIMIT];
-  for (int a = threadIdx.x; a < rmax; a += blockDim.x) acc[a] = 0.0;
-  __syncthreads();
-  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < tot) {
-    const double v = beta64[e];
-    beta[e] = (T)v;
-    if (v != 0.0) atomicAdd(&acc[e / ((long long)rmax * rmax)], v * v);
+__global__ void __launch_bounds__(256)
+convert_beta_kernel(const double* beta64, T* beta, int rmax, DevScalars* sc) {
+  __shared__ double red[8];
+  const int a = blockIdx.x;
+  const long long base = (long long)a * rmax * rmax;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < rmax * rmax; e += blockDim.x) {
+    const double v = beta64[base + e];
+    beta[base + e] = (T)v;
+    s += v * v;
   }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  for (int a = threadIdx.x; a < rmax; a += blockDim.x)
-    if (acc[a] != 0.0) atomicAdd(&sc->beta_a2[a], acc[a]);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    sc->beta_a2[a] = t;
+  }
 }
 
 // adims[a] = n for a < r_1 (batches of the mode-2 product that carry data), else 0;
@@ -182,17 +264,33 @@ template <typename T>
 static int projection_core_t(Ctx& c) {
   const int n = c.n, rmax = c.rmax;
   T* Qp = (T*)c.Qp;
-  dim3 g1((n + 31) / 32, c.R_l, 3);
-  proj_kernel<T><<<g1, 256, 0, c.stream>>>(Bulk<T>::Z(c), Bulk<T>::pk(c), n, rmax, c.R_l, c.sc, Qp);
+  const size_t psmem = sizeof(T) * ((size_t)((2 * n - 1 + 3) & ~3) + 32 * 64);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(proj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
+  dim3 g1(((n + 63) / 64) * ((rmax + 63) / 64), c.R_l, 3);
+  proj_kernel<T><<<g1, 256, psmem, c.stream>>>(Bulk<T>::Z(c), Bulk<T>::pk(c), c.nzj, n, rmax, c.R_l, c.sc, Qp);
   long long tot = (long long)rmax * rmax * rmax;
   cudaMemsetAsync(c.beta64, 0, sizeof(double) * tot, c.stream);
-  const int ta = (rmax + 31) / 32, tb = (rmax + 7) / 8;
   // split K so that the whole GPU is busy even for small ranks
-  int ksplit = 16;
-  dim3 g2(ta * tb * tb, ksplit);
-  core_kernel<T><<<g2, 256, 0, c.stream>>>(Qp, c.j, c.nz_idx, c.Z, n, rmax, c.R_l, c.sc, c.beta64);
-  convert_beta_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(c.beta64, (T*)c.beta, tot,
-                                                                                rmax, c.sc);
+  const int ntile = ((rmax + 63) / 64) * ((rmax + 3) / 4) * ((rmax + 31) / 32);
+  int ksplit = (8 * 152 + ntile - 1) / ntile;
+  if (ksplit < 1) ksplit = 1;
+  // every CTA keeps the row offsets of its K range in shared memory
+  const long long kmax = (long long)c.maxN * c.R_l;
+  const int kmin_split = (int)((kmax + CORE_KMAX - 1) / CORE_KMAX);
+  if (ksplit < kmin_split) ksplit = kmin_split;
+  dim3 g2(ntile, ksplit);
+  static bool core_attr = false;
+  if (!core_attr) {
+    cudaFuncSetAttribute(core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)core_smem_bytes<T>());
+    core_attr = true;
+  }
+  core_kernel<T><<<g2, 256, core_smem_bytes<T>(), c.stream>>>(Qp, c.j, c.nz_idx, c.Z, n, rmax, c.R_l, c.sc,
+                                                               c.beta64);
+  convert_beta_kernel<T><<<rmax, 256, 0, c.stream>>>(c.beta64, (T*)c.beta, rmax, c.sc);
   // T1[a][b][i3] = sum_c beta[a][b][c] V3[i3][c]      (rows (a,b), K = r3)
   const T* Zb = Bulk<T>::Z(c);
   const long long sZ = (long long)n * rmax;
