@@ -437,6 +437,154 @@ def gaussian_pair_forces(xyz, z, t, a, kset):
 
 
 # ----------------------------------------------------------------------------
+# Galerkin kernel off the grid and the adjoint forces  (Sec. 4.3)
+# ----------------------------------------------------------------------------
+def cell_average_gaussian_derivative(t: float, h: float, centre_offset):
+    """d/dc of ``cell_average_gaussian``: the cell average (1/h) int_{c-h/2}^{c+h/2} exp(-t^2 x^2) dx
+    differentiated in its centre c is, by the fundamental theorem of calculus,
+    (exp(-t^2 (c + h/2)^2) - exp(-t^2 (c - h/2)^2)) / h."""
+    c = np.asarray(centre_offset, dtype=np.float64)
+    return (np.exp(-(t * (c + 0.5 * h)) ** 2) - np.exp(-(t * (c - 0.5 * h)) ** 2)) / h
+
+
+def galerkin_factors_at(t, a, h: float, y, derivative: bool = False):
+    """p_k(y) = a_k^{1/3} * (cell average of exp(-t_k^2 x^2) over the cell centred at y) for any
+    offsets y (leading axis over k), or its derivative in y.  On grid offsets y = d*h these are
+    the entries of ``reference_factors`` (Eq. (2.10)); off the grid they extend the grid tensor
+    P_R continuously in the centre position (reading used for the adjoint forces of Sec. 4.3)."""
+    y = np.asarray(y, dtype=np.float64)
+    f = cell_average_gaussian_derivative if derivative else cell_average_gaussian
+    out = np.empty((len(t),) + y.shape)
+    for k in range(len(t)):
+        out[k] = a[k] ** (1.0 / 3.0) * f(t[k], h, y)
+    return out
+
+
+def galerkin_pair_energy(xyz, z, t, a, kset, h: float):
+    """1/2 sum_{j != nu} z_j z_nu K_h(x_j - x_nu) with the Galerkin RS kernel
+    K_h(r) = sum_{k in kset} p_k(r_1) p_k(r_2) p_k(r_3)  (the continuous form of P_R, Eq. (2.10),
+    from ``galerkin_factors_at``); pair-sum form of Eq. (4.6), the self term cancels (Lemma 4.1)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    tk, ak = t[kset], a[kset]
+    E = 0.0
+    for s in range(0, len(z), 256):
+        d = xyz[s:s + 256, None, :] - xyz[None, :, :]
+        f = [galerkin_factors_at(tk, ak, h, d[:, :, l]) for l in range(3)]
+        K = (f[0] * f[1] * f[2]).sum(0)
+        rows = np.arange(s, min(s + 256, len(z)))
+        K[np.arange(len(rows)), rows] = 0.0
+        E += float(z[rows] @ K @ z)
+    return 0.5 * E
+
+
+def galerkin_pair_forces(xyz, z, t, a, kset, h: float):
+    """-d/dx_j of ``galerkin_pair_energy``: F_j = -z_j sum_{nu != j} z_nu grad K_h(x_j - x_nu)
+    (each pair appears twice in the energy; Sec. 4.3 with the spurious 1/2 of the printed force
+    formula removed)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    tk, ak = t[kset], a[kset]
+    F = np.zeros_like(xyz)
+    for s in range(0, len(z), 256):
+        d = xyz[s:s + 256, None, :] - xyz[None, :, :]
+        f = [galerkin_factors_at(tk, ak, h, d[:, :, l]) for l in range(3)]
+        g = [galerkin_factors_at(tk, ak, h, d[:, :, l], derivative=True) for l in range(3)]
+        rows = np.arange(s, min(s + 256, len(z)))
+        for l in range(3):
+            prod = g[l] * f[(l + 1) % 3] * f[(l + 2) % 3]
+            dK = prod.sum(0)
+            dK[np.arange(len(rows)), rows] = 0.0
+            F[rows, l] = -z[rows] * (dK @ z)
+    return F
+
+
+def rs_tucker_forces(j, z, pk, dpk, klong, kshort, gamma: int, Us, Z0s, beta, n: int):
+    """Adjoint forces of the RS-Tucker energy at snapped centres (Sec. 4.3 applied to
+    Def. 3.9 / Lemma 3.10):  F_j = -z_j [grad P_l^T(x_j) + sum_{nu != j, window} z_nu grad P_s,nu(x_j)].
+
+    The long-range part P_l^T = beta x_l V^(l) is differentiated through the continuous form of
+    its Tucker vectors: with U^(l) = Z D W^T (SVD), Z0^(l) = U^(l) W D^{-1}, so each basis vector
+    is a combination of the side-matrix columns, v_a(y) = sum_K u_K(y) (U^T Z0)[K, a] / sigma_a^2,
+    and v_a'(y) uses the derivative factors ``dpk`` (rows of ``galerkin_factors_at`` with
+    derivative=True on the doubled grid).  (Projecting the derivative factor vectors onto the
+    Tucker subspaces instead does not converge with eps: the subspaces are built for the
+    factors, not for their derivatives.)  The short-range part is the window sum of Def. 3.4
+    differentiated term by term.  ``Us`` are the side matrices of ``side_matrices``."""
+    c = n - 1
+    z = np.asarray(z, dtype=np.float64)
+    w = np.abs(z) ** (1.0 / 3.0)
+    N = len(z)
+    V, Vd = [], []
+    for l in range(3):
+        Y = Us[l].T @ Z0s[l]                                   # (N*R_l, r): (U^T Z0)
+        s2 = np.einsum("Ka,Ka->a", Y, Y)                       # ||U^T z_a||^2 = sigma_a^2
+        i = j[:, l]
+        # derivative columns u_K'(x_i) for K = (nu, k): w_nu * dp_k[i - j_nu]
+        idx = i[:, None] - j[None, :, l] + c                   # (N, N)
+        dU = dpk[klong][:, idx] * w[None, None, :]             # (R_l, N, N): [k][point][nu]
+        dU = dU.transpose(1, 2, 0).reshape(N, -1)              # (point, (nu, k))
+        Vd.append(dU @ Y / s2[None, :])
+        V.append(Z0s[l][i])
+    F = np.zeros((N, 3))
+    grads = [np.einsum("abc,ma,mb,mc->m", beta, Vd[0], V[1], V[2], optimize=True),
+             np.einsum("abc,ma,mb,mc->m", beta, V[0], Vd[1], V[2], optimize=True),
+             np.einsum("abc,ma,mb,mc->m", beta, V[0], V[1], Vd[2], optimize=True)]
+    for l in range(3):
+        F[:, l] = -z * grads[l]
+    # short-range windows of the other particles
+    for m in range(N):
+        dj = j[m][None, :] - j                                 # (N, 3)
+        near = np.all(np.abs(dj) <= gamma, axis=1)
+        near[m] = False
+        if not near.any():
+            continue
+        d = dj[near] + c
+        f = [pk[kshort][:, d[:, l]] for l in range(3)]
+        g = [dpk[kshort][:, d[:, l]] for l in range(3)]
+        for l in range(3):
+            dP = (g[l] * f[(l + 1) % 3] * f[(l + 2) % 3]).sum(0)
+            F[m, l] -= z[m] * float(dP @ z[near])
+    return F
+
+
+def rs_direct_long_forces(j, z, pk, dpk, klong, kshort, gamma: int, n: int):
+    """Forces of the untruncated long-range canonical sum plus the windows at snapped centres:
+    F_j = -z_j [grad P_l(x_j) + window terms], grad P_l(x_j) = sum_{nu != j} z_nu sum_{k long}
+    grad (p_k (x) p_k (x) p_k)(x_j - x_nu) with the Galerkin factors and their derivatives on the
+    grid offsets (the survey's F = -z grad P_l, exact for P_l by symmetry)."""
+    c = n - 1
+    z = np.asarray(z, dtype=np.float64)
+    N = len(z)
+    F = np.zeros((N, 3))
+    for m in range(N):
+        d = j[m][None, :] - j + c                              # (N, 3)
+        f = [pk[klong][:, d[:, l]] for l in range(3)]
+        g = [dpk[klong][:, d[:, l]] for l in range(3)]
+        zz = z.copy()
+        zz[m] = 0.0
+        for l in range(3):
+            F[m, l] = -z[m] * float((g[l] * f[(l + 1) % 3] * f[(l + 2) % 3]).sum(0) @ zz)
+        dj = j[m][None, :] - j
+        near = np.all(np.abs(dj) <= gamma, axis=1)
+        near[m] = False
+        if near.any():
+            ds = dj[near] + c
+            fs = [pk[kshort][:, ds[:, l]] for l in range(3)]
+            gs = [dpk[kshort][:, ds[:, l]] for l in range(3)]
+            for l in range(3):
+                F[m, l] -= z[m] * float((gs[l] * fs[(l + 1) % 3] * fs[(l + 2) % 3]).sum(0) @ z[near])
+    return F
+
+
+def reference_factor_derivatives(t, a, h: float, n: int):
+    """Derivatives in the centre offset of the rows of ``reference_factors`` on the doubled grid
+    (``galerkin_factors_at`` with derivative=True at y = d*h, d = -(n-1)..(n-1))."""
+    d = np.arange(-(n - 1), n, dtype=np.float64) * h
+    return galerkin_factors_at(t, a, h, d, derivative=True)
+
+
+# ----------------------------------------------------------------------------
 # Whole-problem driver used by the tests
 # ----------------------------------------------------------------------------
 class Problem:
@@ -500,3 +648,22 @@ class Problem:
 
     def energy_P0(self):
         return energy_from_potential(self.P0_points(self.j), self.z, self.PR0)
+
+    # forces (Sec. 4.3)
+    def forces_galerkin(self, kset=None):
+        """Adjoint forces of the untruncated Galerkin RS kernel at the snapped centres."""
+        ks = self.kall if kset is None else kset
+        return galerkin_pair_forces(self.xyz_snapped, self.z, self.t, self.a, ks, self.h)
+
+    def forces_rs_tucker(self, ranks=None, eps=None):
+        """Adjoint forces of the RS-Tucker tensor (long part at the given ranks + windows)."""
+        Z0s, beta, rk, _, Us, _ = self.tucker(eps=eps, cap=0 if ranks is not None else None, ranks=ranks)
+        dpk = reference_factor_derivatives(self.t, self.a, self.h, self.n)
+        return rs_tucker_forces(self.j, self.z, self.pk, dpk, self.klong, self.kshort, self.gamma, Us,
+                                Z0s, beta, self.n), rk
+
+    def forces_direct_long(self):
+        """Untruncated long-range forces plus windows at the snapped centres."""
+        dpk = reference_factor_derivatives(self.t, self.a, self.h, self.n)
+        return rs_direct_long_forces(self.j, self.z, self.pk, dpk, self.klong, self.kshort, self.gamma,
+                                     self.n)

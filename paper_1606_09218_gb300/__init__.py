@@ -10,7 +10,7 @@ from __future__ import annotations
 import ctypes as C
 
 from . import _lib
-from ._lib import (RS_ENERGY, RS_FP32, RS_FP32_SPLIT, RS_FP64, RS_INPUT_HOST,  # noqa: F401
+from ._lib import (RS_ENERGY, RS_FORCES, RS_FP32, RS_FP32_SPLIT, RS_FP64, RS_INPUT_HOST,  # noqa: F401
                    RS_POTENTIAL, RS_VALIDATE_SEPARATION, RSError)
 
 PRECISIONS = {"fp64": RS_FP64, "fp32_split": RS_FP32_SPLIT, "fp32": RS_FP32}
@@ -89,7 +89,7 @@ class RSContext:
         return self._torch.empty((n, n, n), dtype=self.dtype, device="cuda")
 
     def solve(self, xyz, Z, potential=None, energy: bool = True, want_potential: bool = True,
-              min_sep: float = 0.0) -> int:
+              min_sep: float = 0.0, forces: bool = False) -> int:
         """Enqueue one solve.  ``xyz`` (N,3) and ``Z`` (N,) float64: CUDA tensors, or host
         (CPU tensors / numpy) which the library copies in.  Returns the launch status."""
         torch = self._torch
@@ -118,6 +118,9 @@ class RSContext:
             flags |= RS_POTENTIAL
         if energy:
             flags |= RS_ENERGY
+        if forces:
+            flags |= RS_FORCES
+        self.last_N = N
         if min_sep > 0:
             flags |= RS_VALIDATE_SEPARATION
         st = self.lib.rs_solve(self.h, N, C.c_void_p(pxyz), C.c_void_p(pZ), flags, float(min_sep),
@@ -130,6 +133,14 @@ class RSContext:
         E = C.c_double()
         _lib.check(self.lib.rs_energy(self.h, C.byref(E)), self.h)
         return float(E.value)
+
+    def forces(self):
+        """Adjoint forces of the last solve (it must have asked for ``forces=True``) as an
+        (N, 3) float64 CUDA tensor."""
+        torch = self._torch
+        F = torch.empty((self.last_N, 3), dtype=torch.float64, device="cuda")
+        _lib.check(self.lib.rs_forces(self.h, C.c_void_p(F.data_ptr()), 0), self.h)
+        return F
 
     def report(self) -> dict:
         s = _lib.RSStatsC()
@@ -192,3 +203,31 @@ class RSContext:
 
 def version() -> str:
     return _lib.load().rs_version().decode()
+
+
+def _energy_function():
+    import torch
+
+    class RSEnergy(torch.autograd.Function):
+        """E(xyz) of the RS tensor with its adjoint forces as the gradient: dE/dxyz = -F."""
+
+        @staticmethod
+        def forward(fctx, xyz, Z, rs):
+            rs.solve(xyz.detach(), Z.detach(), energy=True, want_potential=False, forces=True)
+            E = rs.energy()
+            F = rs.forces()
+            fctx.save_for_backward(F)
+            return torch.tensor(E, dtype=torch.float64, device=xyz.device)
+
+        @staticmethod
+        def backward(fctx, gE):
+            (F,) = fctx.saved_tensors
+            return -gE * F, None, None
+
+    return RSEnergy
+
+
+def rs_energy(xyz, Z, ctx: RSContext):
+    """Differentiable interaction energy: ``rs_energy(xyz, Z, ctx).backward()`` puts -F into
+    ``xyz.grad`` (Sec. 4.3 forces through the C ABI)."""
+    return _energy_function().apply(xyz, Z, ctx)

@@ -30,10 +30,10 @@ STATUS_NAMES = {0: "RS_OK", 1: "RS_RANK_CAPPED", -1: "RS_ERR_INVALID_ARG", -2: "
 # precisions
 RS_FP64, RS_FP32_SPLIT, RS_FP32 = 0, 1, 2
 # solve flags
-RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_VALIDATE_SEPARATION = 1, 2, 4, 16
+RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_FORCES, RS_VALIDATE_SEPARATION = 1, 2, 4, 8, 16
 
 #: every symbol ``include/rs.h`` declares
-EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_energy", "rs_report",
+EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_energy", "rs_forces", "rs_report",
             "rs_get_tucker", "rs_eval_points", "rs_profile_enable", "rs_profile_read", "rs_stage_name",
             "rs_debug_buffer", "rs_gram_noalloc",
             "rs_last_error", "rs_version"]
@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.rs_solve.restype = C.c_int
     lib.rs_energy.argtypes = [vp, C.POINTER(C.c_double)]
     lib.rs_energy.restype = C.c_int
+    lib.rs_forces.argtypes = [vp, vp, C.c_int]
+    lib.rs_forces.restype = C.c_int
     lib.rs_report.argtypes = [vp, C.POINTER(RSStatsC)]
     lib.rs_report.restype = C.c_int
     lib.rs_get_tucker.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),

@@ -76,6 +76,8 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   const size_t nbins = (size_t)c.nbin * c.nbin * c.nbin;
   add(v, c.pk64, 8 * R * L);
   add(v, c.pk32, 4 * R * L);
+  add(v, c.dpk64, 8 * R * L);
+  add(v, c.dpk32, 4 * R * L);
   add(v, c.xyz, 8 * 3 * N);
   add(v, c.Z, 8 * N);
   add(v, c.j, 4 * 3 * N);
@@ -110,6 +112,8 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.Epart, 8 * ((N + 7) / 8 + 1));
   add(v, c.adims, 4 * rm);
   add(v, c.kdims, 4 * rm);
+  add(v, c.Vd, ts * 3 * n * rm);
+  add(v, c.Fout, 8 * 3 * N);
   add(v, c.sc, sizeof(DevScalars));
   if (c.use_tc) {
     const size_t nT = (size_t)c.tc_ntiles;
@@ -333,6 +337,7 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   if (flags & RS_POTENTIAL) k += launch_windows(c, potential_out);      // a6
   mark(8);
   if (flags & RS_ENERGY) k += launch_energy(c, N);                      // a8
+  if (flags & RS_FORCES) k += launch_forces(c);                          // a9
   mark(9);
   st = check_launch(c, "solve");
   if (st != RS_OK) return st;
@@ -356,6 +361,25 @@ rs_status rs_energy(rs_ctx* h, double* E) {
     return RS_ERR_CUDA;
   }
   *E = c.h_sc->energy;
+  rs_status s2 = status_of(*c.h_sc);
+  return s2 < 0 ? s2 : RS_OK;
+}
+
+rs_status rs_forces(rs_ctx* h, double* F, int to_host) {
+  if (!h || !F) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.solved || !(c.last_flags & RS_FORCES)) return fail(c, RS_ERR_NOT_READY, "no forces computed");
+  if (c.last_N > 0) {
+    cudaError_t e = cudaMemcpyAsync(F, c.Fout, sizeof(double) * 3 * (size_t)c.last_N,
+                                    to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c.stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c.err = std::string("forces copy: ") + cudaGetErrorString(e);
+      return RS_ERR_CUDA;
+    }
+  }
+  rs_status st = sync_scalars(c);
+  if (st != RS_OK) return st;
   rs_status s2 = status_of(*c.h_sc);
   return s2 < 0 ? s2 : RS_OK;
 }

@@ -79,6 +79,8 @@ struct Ctx {
   // device buffers
   double* pk64 = nullptr;   // R x L
   float*  pk32 = nullptr;   // R x L
+  double* dpk64 = nullptr;  // R x L: derivatives of the factors in the centre offset
+  float*  dpk32 = nullptr;  // R x L
   double* xyz = nullptr;    // maxN x 3 (copy of host input)
   double* Z = nullptr;      // maxN
   int*    j = nullptr;      // maxN x 3 grid indices
@@ -113,6 +115,8 @@ struct Ctx {
   double* Epart = nullptr;      // energy partial sums
   int*    adims = nullptr;      // rmax: per-batch row counts of the mode-2 product
   int*    kdims = nullptr;      // rmax: per-batch inner sizes of the mode-2 product
+  void*   Vd = nullptr;         // 3 x n x rmax (T): derivatives of the Tucker basis functions
+  double* Fout = nullptr;       // maxN x 3 forces of the last solve
   // tensor-core assembly of the FP32 output (rs_tc.cu), planned at create
   bool use_tc = false;
   int t2_ld = 0;                // i3 stride of T2 on the CUDA-core path
@@ -181,6 +185,7 @@ int launch_window_lists(Ctx& c);         // per-tile-column window lists
 int launch_assemble(Ctx& c, float* out); // Tucker product + windows in one kernel
 int launch_windows(Ctx& c, void* out);
 int launch_energy(Ctx& c, int N);
+int launch_forces(Ctx& c);
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out);
 
 // generic batched GEMM on row-major matrices:

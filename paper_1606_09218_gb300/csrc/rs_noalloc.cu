@@ -16,8 +16,8 @@
 
 namespace rs {
 // kernels of the setup stage (rs_setup.cu), launched here on scratch inside the static array
-__global__ void factors_kernel(double* pk64, float* pk32, int R, int n, double h, double hq,
-                               double u0);
+__global__ void factors_kernel(double* pk64, float* pk32, double* dpk64, float* dpk32, int R, int n,
+                               double h, double hq, double u0);
 __global__ void scalars_kernel(const double* pk64, int R, int R_l, int n, double delta_rel,
                                DevScalars* sc);
 __global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n, double b,
@@ -59,18 +59,20 @@ extern "C" rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* 
     return RS_ERR_INVALID_ARG;
   }
   const int L = 2 * n - 1, R_l = R - R_s;
-  // scratch layout: scalars | pk64 | pk32 | j | C | nzj | F
+  // scratch layout: scalars | pk64 | pk32 | dpk64 | dpk32 | j | C | nzj | F
   size_t off = 0;
   const size_t o_sc = off;   off = align256(off + sizeof(DevScalars));
   const size_t o_pk64 = off; off = align256(off + sizeof(double) * (size_t)R * L);
   const size_t o_pk32 = off; off = align256(off + sizeof(float) * (size_t)R * L);
+  const size_t o_dpk64 = off; off = align256(off + sizeof(double) * (size_t)R * L);
+  const size_t o_dpk32 = off; off = align256(off + sizeof(float) * (size_t)R * L);
   const size_t o_j = off;    off = align256(off + sizeof(int) * 3 * (size_t)(N > 0 ? N : 1));
   const size_t o_C = off;    off = align256(off + sizeof(double) * 3 * (size_t)n);
   const size_t o_nzj = off;  off = align256(off + sizeof(int) * 3 * (size_t)n);
   const size_t o_F = off;    off = align256(off + sizeof(double) * (size_t)L * L);
   if (off > kNoAllocBytes) {
     set_host_error("rs_gram_noalloc: problem needs " + std::to_string(off) +
-                   " bytes of scratch, above the fixed 16 MiB (n up to 513 with N up to ~130000)");
+                   " bytes of scratch, above the fixed 16 MiB (n up to 513 with N up to ~100000)");
     return RS_ERR_CAPACITY;
   }
   int dev = 0;
@@ -99,6 +101,8 @@ extern "C" rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* 
   DevScalars* sc = (DevScalars*)(base + o_sc);
   double* pk64 = (double*)(base + o_pk64);
   float* pk32 = (float*)(base + o_pk32);
+  double* dpk64 = (double*)(base + o_dpk64);
+  float* dpk32 = (float*)(base + o_dpk32);
   int* j = (int*)(base + o_j);
   double* C = (double*)(base + o_C);
   int* nzj = (int*)(base + o_nzj);
@@ -108,7 +112,7 @@ extern "C" rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* 
   cudaMemsetAsync(sc, 0, sizeof(DevScalars), s);
   cudaMemsetAsync(C, 0, sizeof(double) * 3 * (size_t)n, s);
   const int tot = R * L;
-  factors_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pk64, pk32, R, n, h, cfg->h_q, cfg->u0);
+  factors_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pk64, pk32, dpk64, dpk32, R, n, h, cfg->h_q, cfg->u0);
   scalars_kernel<<<1, 256, 0, s>>>(pk64, R, R_l, n, cfg->delta_rel, sc);
   if (N > 0) prepare_kernel<<<(N + 255) / 256, 256, 0, s>>>(xyz, Z, N, n, cfg->b, h, j, C, sc);
   compact_nzj_kernel<<<3, 1024, 0, s>>>(C, n, nzj, sc);

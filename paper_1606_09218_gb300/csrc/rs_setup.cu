@@ -9,20 +9,28 @@ namespace rs {
 // p_k[d] = a_k^{1/3} * (1/h) int_{dh-h/2}^{dh+h/2} exp(-t_k^2 x^2) dx,  d = -(n-1)..(n-1)
 // with t_k = exp(u0 + k h_q), a_k = (2/sqrt(pi)) h_q t_k (exponential sinc rule of the
 // Laplace-Gauss transform of 1/z, Eqs. (2.6)-(2.8); Galerkin cell averages, Eq. (2.5)).
-__global__ void factors_kernel(double* pk64, float* pk32, int R, int n, double h, double hq,
-                               double u0) {
+// dp_k[d] = d/dc of p_k at the centre offset c = d*h: a_k^{1/3} (exp(-t_k^2 (c+h/2)^2) -
+// exp(-t_k^2 (c-h/2)^2)) / h (the cell average differentiated in its centre; adjoint forces).
+__global__ void factors_kernel(double* pk64, float* pk32, double* dpk64, float* dpk32, int R, int n,
+                               double h, double hq, double u0) {
   const int L = 2 * n - 1;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= R * L) return;
   int k = e / L, di = e % L;
   double t = exp(u0 + k * hq);
   double a = 1.1283791670955126 * hq * t;          // 2/sqrt(pi)
-  double c = fabs((double)(di - (n - 1))) * h;
+  double cs = (double)(di - (n - 1)) * h;
+  double c = fabs(cs);
   double lo = t * (c - 0.5 * h), hi = t * (c + 0.5 * h);
   double diff = (lo > 0.5) ? (erfc(lo) - erfc(hi)) : (erf(hi) - erf(lo));
-  double v = cbrt(a) * (0.88622692545275801 / (t * h)) * diff;   // sqrt(pi)/2
+  double ca = cbrt(a);
+  double v = ca * (0.88622692545275801 / (t * h)) * diff;   // sqrt(pi)/2
   pk64[e] = v;
   pk32[e] = (float)v;
+  const double up = t * (cs + 0.5 * h), dn = t * (cs - 0.5 * h);
+  const double dv = ca * (exp(-up * up) - exp(-dn * dn)) / h;
+  dpk64[e] = dv;
+  dpk32[e] = (float)dv;
 }
 
 // P_R(0), P_{R_l}(0), delta and the window half-width gamma (one CTA).
@@ -66,8 +74,8 @@ __global__ void scalars_kernel(const double* pk64, int R, int R_l, int n, double
 
 int launch_factors(Ctx& c) {
   int tot = c.R * c.L;
-  factors_kernel<<<(tot + 255) / 256, 256, 0, c.stream>>>(c.pk64, c.pk32, c.R, c.n, c.h,
-                                                          c.cfg.h_q, c.cfg.u0);
+  factors_kernel<<<(tot + 255) / 256, 256, 0, c.stream>>>(c.pk64, c.pk32, c.dpk64, c.dpk32, c.R, c.n,
+                                                          c.h, c.cfg.h_q, c.cfg.u0);
   scalars_kernel<<<1, 256, 0, c.stream>>>(c.pk64, c.R, c.R_l, c.n, c.cfg.delta_rel, c.sc);
   return 2;
 }

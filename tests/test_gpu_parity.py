@@ -274,3 +274,80 @@ def test_tensor_core_reconstruction_matches_cuda_core_path(name, monkeypatch):
         a, b = float(P[i]), float(ref[i])
         assert abs(a - b) <= 1e-5 * max(1.0, abs(b)), (i, a, b)
     ctx.close()
+
+
+# ---------------------------------------------------------------- adjoint forces (Sec. 4.3)
+def _forces_tol(cfg, rounding):
+    """Both the GPU and the oracle RS-Tucker forces are within O(eps) of the untruncated forces
+    (oracle pin: relative error <= 1e-5 at eps = 1e-6); 20*eps covers both, plus the rounding of
+    the bulk precision."""
+    return 20 * cfg["eps"] + rounding
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
+def test_forces_match_oracle(prec):
+    """Forces through the C ABI.  FP64 path: the adjoint of the RS-Tucker energy (continued Tucker
+    basis) against the oracle's RS-Tucker forces at the same ranks; FP32 bulk path: the untruncated
+    long-range pair kernel plus windows against the oracle's direct form.  Both against the forces
+    of the untruncated Galerkin kernel (O(eps)); zero-charge particles get zero force and the
+    total force is (nearly) zero."""
+    rng = np.random.default_rng(12)
+    cfg = dict(b=4.0, n=45, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8,
+               precision=prec, snap=True)
+    N = 16
+    xyz = rng.uniform(-3.2, 3.2, (N, 3))
+    Z = rng.uniform(-1, 1, N)
+    Z[3] = 0.0
+    pr = O.Problem(cfg, xyz, Z)
+    ctx = _ctx(cfg, N)
+    ctx.solve(torch.tensor(xyz, device="cuda"), torch.tensor(Z, device="cuda"), forces=True)
+    F = ctx.forces().cpu().numpy()
+    rep = ctx.report()
+    assert rep["status"] == 0
+    Fo = pr.forces_rs_tucker(ranks=rep["ranks"])[0] if prec == "fp64" else pr.forces_direct_long()
+    Fg = pr.forces_galerkin()
+    tol = _forces_tol(cfg, 1e-10 if prec == "fp64" else 2e-6)
+    assert np.linalg.norm(F - Fo) / np.linalg.norm(Fo) < tol
+    assert np.linalg.norm(F - Fg) / np.linalg.norm(Fg) < tol
+    assert np.all(F[3] == 0.0)
+    assert np.abs(F.sum(0)).max() <= tol * np.abs(F).max() * N
+    ctx.close()
+
+
+def test_forces_c2_full_size_sampled():
+    """Config 2 at full size (FP32 bulk): adjoint forces against the untruncated Galerkin
+    forces of the oracle on a sample of particles."""
+    cfg = load_config("c2_protein1000_n513")
+    p = make_particles(cfg)
+    pr = O.Problem(cfg, p.xyz, p.Z)
+    ctx = _ctx(cfg, len(p.Z))
+    ctx.solve(torch.tensor(p.xyz, device="cuda"), torch.tensor(p.Z, device="cuda"), forces=True,
+              want_potential=False)
+    F = ctx.forces().cpu().numpy()
+    assert ctx.report()["status"] == 0
+    Fg = pr.forces_galerkin()
+    sel = np.nonzero(pr.z != 0)[0][::7]
+    err = np.linalg.norm(F[sel] - Fg[sel]) / np.linalg.norm(Fg[sel])
+    assert err < _forces_tol(cfg, 2e-6), err
+    ctx.close()
+
+
+def test_forces_autograd_and_not_ready():
+    """rs_energy(...).backward() puts -F into xyz.grad; asking for forces of a solve that did
+    not compute them is an error."""
+    from paper_1606_09218_gb300 import RSError, rs_energy
+    rng = np.random.default_rng(8)
+    cfg = dict(b=4.0, n=33, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8,
+               precision="fp64", snap=True)
+    xyz = torch.tensor(rng.uniform(-2.5, 2.5, (5, 3)), device="cuda", requires_grad=True)
+    Z = torch.tensor(rng.uniform(-1, 1, 5), device="cuda")
+    ctx = _ctx(cfg, 5)
+    E = rs_energy(xyz, Z, ctx)
+    E.backward()
+    F = ctx.forces()
+    assert torch.allclose(xyz.grad, -F)
+    assert abs(float(E) - ctx.energy()) == 0.0
+    ctx.solve(xyz.detach(), Z, forces=False)
+    with pytest.raises(RSError):
+        ctx.forces()
+    ctx.close()

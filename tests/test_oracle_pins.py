@@ -437,3 +437,75 @@ def test_gaussian_pair_forces_finite_difference_and_coulomb_limit():
     assert np.max(np.abs(Fall - Fc)) <= 0.05 * np.max(np.abs(Fc))
     Eall = O.gaussian_pair_energy(xyz, z, t, a, np.arange(cfg["R"]))
     assert abs(Eall - O.energy_direct(xyz, z)) <= 1.05 * cfg["fit"]["max_rel_err"] * O.energy_scale(xyz, z)
+
+
+# ---------------------------------------------------------------- Sec. 4.3 adjoint forces
+def test_galerkin_factors_on_grid_and_derivative():
+    """The continuous Galerkin factors reproduce the grid factors at grid offsets (Eq. (2.10)),
+    and their closed-form derivative matches central differences of the factors themselves."""
+    cfg = small_cfg()
+    pr = O.Problem(cfg, np.zeros((1, 3)), np.ones(1))
+    d = np.arange(-(pr.n - 1), pr.n) * pr.h
+    assert np.allclose(O.galerkin_factors_at(pr.t, pr.a, pr.h, d), pr.pk, rtol=1e-13, atol=1e-15)
+    y = np.linspace(-2.0, 2.0, 41) + 0.0123
+    hf = 1e-5
+    fd = (O.galerkin_factors_at(pr.t, pr.a, pr.h, y + hf) - O.galerkin_factors_at(pr.t, pr.a, pr.h, y - hf)) / (2 * hf)
+    g = O.galerkin_factors_at(pr.t, pr.a, pr.h, y, derivative=True)
+    assert np.max(np.abs(g - fd)) <= 1e-7 * np.max(np.abs(g))
+    # odd in the offset: zero derivative at the cell centre
+    assert np.all(O.reference_factor_derivatives(pr.t, pr.a, pr.h, pr.n)[:, pr.n - 1] == 0.0)
+
+
+def test_galerkin_pair_forces_finite_difference_momentum_and_limit():
+    """F = -grad E for the Galerkin pair energy (central differences), total force zero
+    (each pair contributes equal and opposite forces), and as h -> 0 the cell averages tend to
+    point values so the forces tend to the collocated Gaussian-sum pair forces."""
+    cfg = small_cfg()
+    rng = np.random.default_rng(31)
+    xyz, z = random_particles(rng, 6, 2.5, 1.0)
+    pr = O.Problem(cfg, xyz, z)
+    F = O.galerkin_pair_forces(xyz, z, pr.t, pr.a, pr.kall, pr.h)
+    hfd = 1e-5
+    for jj in range(3):
+        for l in range(3):
+            xp, xm = xyz.copy(), xyz.copy()
+            xp[jj, l] += hfd
+            xm[jj, l] -= hfd
+            fd = -(O.galerkin_pair_energy(xp, z, pr.t, pr.a, pr.kall, pr.h)
+                   - O.galerkin_pair_energy(xm, z, pr.t, pr.a, pr.kall, pr.h)) / (2 * hfd)
+            assert abs(F[jj, l] - fd) <= 1e-7 * np.abs(F).max()
+    assert np.abs(F.sum(0)).max() <= 1e-12 * np.abs(F).max()
+    Fh = O.galerkin_pair_forces(xyz, z, pr.t, pr.a, pr.kall, 1e-3)
+    Fg = O.gaussian_pair_forces(xyz, z, pr.t, pr.a, pr.kall)
+    assert np.max(np.abs(Fh - Fg)) <= 1e-4 * np.max(np.abs(Fg))
+
+
+def test_rs_tucker_forces_converge_with_eps():
+    """The adjoint forces of the RS-Tucker tensor (Tucker long part through the continuous basis
+    functions, windows for the short part) tend to the forces of the untruncated Galerkin kernel
+    as eps decreases: the error is of order eps down to 1e-8."""
+    cfg = small_cfg()
+    rng = np.random.default_rng(3)
+    xyz = rng.uniform(-2.5, 2.5, (6, 3))
+    z = rng.uniform(-1, 1, 6)
+    pr = O.Problem(cfg, xyz, z)
+    F = pr.forces_galerkin()
+    errs = []
+    for e in (1e-4, 1e-6, 1e-8):
+        Ft, _ = pr.forces_rs_tucker(eps=e)
+        errs.append(np.linalg.norm(Ft - F) / np.linalg.norm(F))
+    assert errs[0] <= 3e-3 and errs[1] <= 1e-5 and errs[2] <= 1e-6, errs
+    assert errs[2] < errs[1] < errs[0]
+
+
+def test_direct_long_forces_equal_galerkin_up_to_window_cut():
+    """Untruncated long-range pair forces plus the windows equal the Galerkin pair forces of the
+    whole kernel except for the window cut-off (each cut term is below delta)."""
+    cfg = small_cfg()
+    rng = np.random.default_rng(3)
+    xyz = rng.uniform(-2.5, 2.5, (6, 3))
+    z = rng.uniform(-1, 1, 6)
+    pr = O.Problem(cfg, xyz, z)
+    F = pr.forces_galerkin()
+    Fd = pr.forces_direct_long()
+    assert np.linalg.norm(Fd - F) / np.linalg.norm(F) <= 1e-7
