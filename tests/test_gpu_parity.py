@@ -346,7 +346,7 @@ def test_forces_autograd_and_not_ready():
     E.backward()
     F = ctx.forces()
     assert torch.allclose(xyz.grad, -F)
-    assert abs(float(E) - ctx.energy()) == 0.0
+    assert abs(float(E.detach()) - ctx.energy()) == 0.0
     ctx.solve(xyz.detach(), Z, forces=False)
     with pytest.raises(RSError):
         ctx.forces()
