@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -200,6 +201,37 @@ size_t rs_workspace_bytes(const rs_config* cfg) {
   return tot;
 }
 
+namespace {
+
+// raise the dynamic shared memory limit of the large-tile kernels once per device
+bool ensure_kernel_attributes(std::string& err) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return true;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = set_attributes_eigen(optin);
+  if (e == cudaSuccess) e = set_attributes_tucker(optin);
+  if (e == cudaSuccess) e = set_attributes_tc(optin);
+  if (e != cudaSuccess) {
+    err = std::string("kernel attributes: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return false;
+  }
+  done[dev] = true;
+  return true;
+}
+
+}  // namespace
+
 rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
   if (!cfg || !out) { g_create_err = "null argument"; return RS_ERR_INVALID_ARG; }
   *out = nullptr;
@@ -213,6 +245,11 @@ rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
     return RS_ERR_INVALID_ARG;
   }
   c.stream = (cudaStream_t)stream;
+  if (!ensure_kernel_attributes(err)) {
+    g_create_err = err;
+    delete h;
+    return RS_ERR_CUDA;
+  }
   // RS_DEBUG_POISON=1 fills every workspace buffer with 0xFF bytes (NaN / -1) so that a
   // read of memory the current solve did not write shows up in the results.
   const char* poison = std::getenv("RS_DEBUG_POISON");

@@ -828,7 +828,6 @@ static int refine(Ctx& c, double*& Qa, double*& Qb) {
   const long long sQ = (long long)n * ks, sK = (long long)ks * ks;
   const int* ke = c.sc->k_eff;
   size_t shm = 2ull * ks * (ks + 1) * sizeof(float);
-  cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   // pass 1: T -> W1^T T W1
   jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, 12, 1e-4f);
   congruence(c, c.T, c.W);
@@ -865,7 +864,6 @@ int launch_subspace(Ctx& c) {
   {
     void* args[] = {(void*)&c.X, (void*)&c.Q, (void*)&c.part, (void*)&n, (void*)&ks, (void*)&c.sc};
     const size_t shm = sizeof(double) * (size_t)((n + NBC - 1) / NBC) * ks;
-    cudaFuncSetAttribute(bcgs2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     cudaLaunchCooperativeKernel((void*)bcgs2_kernel, dim3(3 * NBC), dim3(256), args, shm, c.stream);
   }
   const int* ke = c.sc->k_eff;
@@ -895,6 +893,12 @@ int launch_subspace(Ctx& c) {
   gather_Z_kernel<<<(unsigned)((totZ + 255) / 256), 256, 0, c.stream>>>(Qa, c.order, n, ks, c.rmax,
                                                                         c.sc, c.Z64, c.Z32);
   return k + 2;
+}
+
+cudaError_t set_attributes_eigen(int optin) {
+  cudaError_t e = allow_max_dynamic_smem((const void*)jacobi32_kernel, optin);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)bcgs2_kernel, optin);
+  return e;
 }
 
 }  // namespace rs

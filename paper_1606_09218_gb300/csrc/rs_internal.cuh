@@ -186,6 +186,20 @@ int launch_assemble(Ctx& c, float* out); // Tucker product + windows in one kern
 int launch_windows(Ctx& c, void* out);
 int launch_energy(Ctx& c, int N);
 int launch_forces(Ctx& c);
+
+// Kernels launched with more than 48 KB of dynamic shared memory.  The limit is an attribute of
+// the kernel (process-wide per device), so it is raised once per device to the opt-in maximum
+// rather than to the size one context needs: contexts of different sizes then never lower it
+// under one another, and no launch sets it concurrently with another thread's launch.
+inline cudaError_t allow_max_dynamic_smem(const void* f, int optin) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, f);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+}
+cudaError_t set_attributes_eigen(int optin);
+cudaError_t set_attributes_tucker(int optin);
+cudaError_t set_attributes_tc(int optin);
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out);
 
 // generic batched GEMM on row-major matrices:

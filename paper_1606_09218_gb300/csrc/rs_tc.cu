@@ -987,12 +987,7 @@ size_t t2_tile_bytes(const Ctx& c) {
 }
 
 int launch_t2_tiles(Ctx& c) {
-  static bool attr = false;
   const size_t shm = (size_t)1152 * c.rmax;
-  if (!attr) {
-    cudaFuncSetAttribute(t2_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMEM_LIMIT - SMEM_RESERVE));
-    attr = true;
-  }
   const dim3 grid((c.n + AS_T3 - 1) / AS_T3, (c.n + TT_ROWS - 1) / TT_ROWS);
   t2_tiles_kernel<<<grid, 256, shm, c.stream>>>((const float*)c.T1, c.Z32 + (size_t)c.n * c.rmax, c.n,
                                                 c.rmax, c.tc_kpad, c.tc_ntiles, c.sc,
@@ -1044,10 +1039,15 @@ int launch_assemble(Ctx& c, float* out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     c.tc_grid = sms > c.tc_nch ? sms : c.tc_nch;
-    cudaFuncSetAttribute(assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.tc_smem);
   }
   assemble_kernel<<<c.tc_grid, AS_THREADS, c.tc_smem, c.stream>>>(g);
   return 1;
+}
+
+cudaError_t set_attributes_tc(int optin) {
+  cudaError_t e = allow_max_dynamic_smem((const void*)t2_tiles_kernel, optin);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)assemble_kernel, optin);
+  return e;
 }
 
 }  // namespace rs

@@ -265,11 +265,6 @@ static int projection_core_t(Ctx& c) {
   const int n = c.n, rmax = c.rmax;
   T* Qp = (T*)c.Qp;
   const size_t psmem = sizeof(T) * ((size_t)((2 * n - 1 + 3) & ~3) + 32 * 64);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(proj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
-  }
   dim3 g1(((n + 63) / 64) * ((rmax + 63) / 64), c.R_l, 3);
   proj_kernel<T><<<g1, 256, psmem, c.stream>>>(Bulk<T>::Z(c), Bulk<T>::pk(c), c.nzj, n, rmax, c.R_l, c.sc, Qp);
   long long tot = (long long)rmax * rmax * rmax;
@@ -283,11 +278,6 @@ static int projection_core_t(Ctx& c) {
   const int kmin_split = (int)((kmax + CORE_KMAX - 1) / CORE_KMAX);
   if (ksplit < kmin_split) ksplit = kmin_split;
   dim3 g2(ntile, ksplit);
-  static bool core_attr = false;
-  if (!core_attr) {
-    cudaFuncSetAttribute(core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)core_smem_bytes<T>());
-    core_attr = true;
-  }
   core_kernel<T><<<g2, 256, core_smem_bytes<T>(), c.stream>>>(Qp, c.j, c.nz_idx, c.Z, n, rmax, c.R_l, c.sc,
                                                                c.beta64);
   convert_beta_kernel<T><<<rmax, 256, 0, c.stream>>>(c.beta64, (T*)c.beta, rmax, c.sc);
@@ -896,6 +886,14 @@ int launch_eval_points(Ctx& c, int M, const int* idx, double* out) {
   if (c.fp64) eval_points_kernel<double><<<blocks, 256, 0, c.stream>>>(v, c.Z64, (const double*)c.T1, M, idx, out);
   else eval_points_kernel<float><<<blocks, 256, 0, c.stream>>>(v, c.Z32, (const float*)c.T1, M, idx, out);
   return 1;
+}
+
+cudaError_t set_attributes_tucker(int optin) {
+  cudaError_t e = allow_max_dynamic_smem((const void*)proj_kernel<float>, optin);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)proj_kernel<double>, optin);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)core_kernel<float>, optin);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)core_kernel<double>, optin);
+  return e;
 }
 
 }  // namespace rs
