@@ -10,6 +10,9 @@ The metric is grid points per second (n^3 per solve).  For N > 1 (torchrun) ever
 solves its own seeded replica (independent problems, weak scaling, no data-path
 collective); the reported value is the whole-job rate over the slowest rank's time.
 
+The JSON line also carries a serving sub-report (``serving``): the 256-request workload
+c4 replayed with Poisson arrivals through the library's request loop, p50/p99 latency.
+
 ``--impl reference`` times the FP64 CPU oracle (full-rank canonical sum at sampled grid
 points) on the host cores, on the same workload and metric.
 """
@@ -169,6 +172,59 @@ def run_reference(args, rank, world):
     return 0
 
 
+SERVING_WORKLOAD = "c4_serving256"
+
+
+def serving_report(max_slots: int = 8, hbm_budget: int = 16 << 30):
+    """Replay the serving workload through the library's request loop (``rs_server_*``):
+    requests of varying N and n arrive at their Poisson times with host inputs, each computes
+    the potential into its own device buffer and the energy; latency is submit to result."""
+    import numpy as np
+    import torch
+    from paper_1606_09218_gb300 import RSServer, config_from_workload
+    from workloads import load_config, make_serving_requests
+    scfg = load_config(SERVING_WORKLOAD)
+    sv = scfg["serving"]
+    reqs = make_serving_requests(scfg)
+    cfgs = {n: config_from_workload(scfg, n=n, max_particles=int(sv["N_max"])) for n in sv["n_choices"]}
+    pots = [torch.empty((r.n,) * 3, dtype=torch.float32, device="cuda") for r in reqs]
+    torch.cuda.synchronize()
+    srv = RSServer(hbm_budget=hbm_budget, max_slots=max_slots)
+    # warm-up: one request of each grid size creates a slot of each configuration
+    for n in cfgs:
+        r = next(q for q in reqs if q.n == n)
+        warm = torch.empty((n,) * 3, dtype=torch.float32, device="cuda")
+        srv.wait(srv.submit(cfgs[n], r.particles.xyz, r.particles.Z, potential=warm))
+    t0 = time.perf_counter()
+    tickets = []
+    for r, pot in zip(reqs, pots):
+        dt = t0 + r.arrival_s - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(cfgs[r.n], r.particles.xyz, r.particles.Z, potential=pot))
+    res = [srv.wait(t) for t in tickets]
+    span = time.perf_counter() - t0
+    info = srv.info()
+    srv.close()
+    lat = np.array([x["latency_ms"] for x in res])
+    que = np.array([x["queue_ms"] for x in res])
+    ok = sum(1 for x in res if x["status"] >= 0)
+    errors = {}
+    for x in res:
+        if x["status"] < 0:
+            errors[x["message"]] = errors.get(x["message"], 0) + 1
+    pts = sum(r.n ** 3 for r in reqs)
+    del pots
+    return {"workload": SERVING_WORKLOAD, "requests": len(reqs), "ok": ok, "errors": errors,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "queue_p50_ms": float(np.percentile(que, 50)),
+            "queue_p99_ms": float(np.percentile(que, 99)), "span_s": span,
+            "solves_per_s": len(reqs) / span, "grid_pts_per_s": pts / span,
+            "arrivals": f"Poisson, mean gap {sv['mean_gap_ms']} ms, last at {reqs[-1].arrival_s:.3f} s",
+            "max_slots": max_slots, "hbm_budget_bytes": hbm_budget, "slots_at_end": info["slots"],
+            "latency": "submit (host inputs) to result (energy on host, potential in a device buffer)"}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -293,6 +349,10 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_launch": per_launch_ms, "algorithmic_bytes": bytes_alg,
             "bytes_formula": "4*n^3 (output) + 4*r1*n^2 (T2 slab)"}
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_report()
+
     cpu = None
     if not args.no_cpu:
         r, M, dt = oracle_rate(cfg, parts, float(os.environ.get("RS_CPU_SAMPLE_S", "12")))
@@ -317,6 +377,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "stages_ms_per_step": {k: v / max(nsolves, 1) for k, v in stages.items()},
         "plain_gpu": plain,
+        "serving": serving,
         "energy": E,
     }
     print(json.dumps(line), flush=True)
@@ -335,6 +396,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain-path comparison")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving replay")
     args = ap.parse_args()
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)

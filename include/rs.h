@@ -191,6 +191,50 @@ const char* rs_stage_name(int stage);
 rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* xyz, const double* Z,
                           double* G, void* cuda_stream);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of solves of different N and n (no counterpart in the paper, whose
+ * experiments are single solves).  rs_submit queues a request (its inputs are copied); a worker
+ * thread admits queued requests to slots — a slot is a context with its own CUDA stream, kept for
+ * later requests of the same configuration — when an idle slot of the configuration exists or a
+ * new slot fits hbm_budget (the sum of the slots' rs_workspace_bytes, idle slots of other
+ * configurations are released to make room) and at most max_slots slots exist; admitted requests
+ * run concurrently.  The queue is scanned in arrival order; a request that cannot be admitted
+ * yet does not hold back later ones that can.  Results match a solve of the same request alone
+ * (separate workspaces; only the order of FP64 atomic sums may differ). */
+typedef struct rs_server rs_server;
+
+typedef struct {
+    rs_config cfg;          /* configuration; N <= cfg.max_particles */
+    int    N;
+    const double* xyz;      /* host, N x 3 row-major; copied by rs_submit */
+    const double* Z;        /* host, N; copied by rs_submit */
+    int    flags;           /* RS_ENERGY and/or RS_POTENTIAL */
+    void*  potential_out;   /* with RS_POTENTIAL: caller-owned 16-byte aligned device buffer of
+                               n^3 elements, valid until rs_wait returns */
+} rs_request;
+
+typedef struct {
+    int    status;          /* rs_status of the solve (RS_RANK_CAPPED is a warning) */
+    double energy;          /* with RS_ENERGY */
+    double latency_ms;      /* rs_submit -> completion observed by the worker */
+    double queue_ms;        /* rs_submit -> launch */
+    int    ranks[3];
+    int    slot;            /* slot index that ran the request */
+    char   message[128];    /* with a negative status: the error text, NUL-terminated */
+} rs_result;
+
+/* Start a server on the current device.  Errors: RS_ERR_INVALID_ARG, RS_ERR_OOM, RS_ERR_CUDA. */
+rs_status rs_server_create(size_t hbm_budget, int max_slots, rs_server** out);
+/* Queue one request; *ticket identifies it for rs_wait.  RS_ERR_CAPACITY if N > max_particles. */
+rs_status rs_submit(rs_server* srv, const rs_request* req, unsigned long long* ticket);
+/* Wait up to timeout_ms for a request; fills *out and releases the ticket.  RS_ERR_TIMEOUT if
+ * it is not done in time (the ticket stays valid); RS_ERR_INVALID_ARG for an unknown ticket. */
+rs_status rs_wait(rs_server* srv, unsigned long long ticket, int timeout_ms, rs_result* out);
+/* Slots, workspace bytes held and queued requests (any pointer may be NULL). */
+rs_status rs_server_info(rs_server* srv, int* slots, size_t* bytes_in_use, int* queued);
+/* Finish queued and running requests, free every slot and stop the worker.  Safe on NULL. */
+void rs_server_destroy(rs_server* srv);
+
 /* Text of the last error of this context (or of rs_create when ctx is NULL). */
 const char* rs_last_error(rs_ctx* ctx);
 

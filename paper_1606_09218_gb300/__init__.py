@@ -205,6 +205,56 @@ def version() -> str:
     return _lib.load().rs_version().decode()
 
 
+class RSServer:
+    """Continuous-batching request loop of the library (``rs_server_*``): requests of any
+    configuration are queued by ``submit`` and run concurrently as slots and HBM budget allow."""
+
+    def __init__(self, hbm_budget: int = 32 << 30, max_slots: int = 8):
+        self.lib = _lib.load()
+        h = C.c_void_p()
+        _lib.check(self.lib.rs_server_create(C.c_size_t(int(hbm_budget)), int(max_slots), C.byref(h)), None)
+        self.h = h
+
+    def submit(self, cfg: _lib.RSConfigC, xyz, Z, energy: bool = True, potential=None) -> int:
+        """Queue one solve (host inputs, copied by the library); returns its ticket."""
+        import numpy as np
+        xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64))
+        Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64))
+        req = _lib.RSRequestC()
+        req.cfg = cfg
+        req.N = int(Z.size)
+        req.xyz = xyz.ctypes.data
+        req.Z = Z.ctypes.data
+        req.flags = (RS_ENERGY if energy else 0) | (RS_POTENTIAL if potential is not None else 0)
+        req.potential_out = potential.data_ptr() if potential is not None else None
+        t = C.c_ulonglong()
+        _lib.check(self.lib.rs_submit(self.h, C.byref(req), C.byref(t)), None)
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 120000) -> dict:
+        r = _lib.RSResultC()
+        _lib.check(self.lib.rs_wait(self.h, C.c_ulonglong(ticket), int(timeout_ms), C.byref(r)), None)
+        return dict(status=r.status, energy=r.energy, latency_ms=r.latency_ms, queue_ms=r.queue_ms,
+                    ranks=list(r.ranks), slot=r.slot, message=r.message.decode(errors="replace"))
+
+    def info(self) -> dict:
+        sl, q = C.c_int(), C.c_int()
+        b = C.c_size_t()
+        _lib.check(self.lib.rs_server_info(self.h, C.byref(sl), C.byref(b), C.byref(q)), None)
+        return dict(slots=sl.value, bytes_in_use=b.value, queued=q.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rs_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _energy_function():
     import torch
 

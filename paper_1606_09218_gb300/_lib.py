@@ -36,6 +36,7 @@ RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_FORCES, RS_VALIDATE_SEPARATION = 1, 2
 EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_energy", "rs_forces", "rs_report",
             "rs_get_tucker", "rs_eval_points", "rs_profile_enable", "rs_profile_read", "rs_stage_name",
             "rs_debug_buffer", "rs_gram_noalloc",
+            "rs_server_create", "rs_submit", "rs_wait", "rs_server_info", "rs_server_destroy",
             "rs_last_error", "rs_version"]
 RS_NSTAGE = 9
 
@@ -45,6 +46,17 @@ class RSConfigC(C.Structure):
                 ("h_q", C.c_double), ("u0", C.c_double), ("eps", C.c_double),
                 ("rank_cap", C.c_int), ("max_rank", C.c_int), ("delta_rel", C.c_double),
                 ("precision", C.c_int), ("snap", C.c_int), ("max_particles", C.c_int)]
+
+
+class RSRequestC(C.Structure):
+    _fields_ = [("cfg", RSConfigC), ("N", C.c_int), ("xyz", C.c_void_p), ("Z", C.c_void_p),
+                ("flags", C.c_int), ("potential_out", C.c_void_p)]
+
+
+class RSResultC(C.Structure):
+    _fields_ = [("status", C.c_int), ("energy", C.c_double), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double), ("ranks", C.c_int * 3), ("slot", C.c_int),
+                ("message", C.c_char * 128)]
 
 
 class RSStatsC(C.Structure):
@@ -84,6 +96,16 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.rs_energy.restype = C.c_int
     lib.rs_forces.argtypes = [vp, vp, C.c_int]
     lib.rs_forces.restype = C.c_int
+    lib.rs_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
+    lib.rs_server_create.restype = C.c_int
+    lib.rs_submit.argtypes = [vp, C.POINTER(RSRequestC), C.POINTER(C.c_ulonglong)]
+    lib.rs_submit.restype = C.c_int
+    lib.rs_wait.argtypes = [vp, C.c_ulonglong, C.c_int, C.POINTER(RSResultC)]
+    lib.rs_wait.restype = C.c_int
+    lib.rs_server_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
+    lib.rs_server_info.restype = C.c_int
+    lib.rs_server_destroy.argtypes = [vp]
+    lib.rs_server_destroy.restype = None
     lib.rs_report.argtypes = [vp, C.POINTER(RSStatsC)]
     lib.rs_report.restype = C.c_int
     lib.rs_get_tucker.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),

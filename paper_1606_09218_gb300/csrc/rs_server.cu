@@ -1,0 +1,307 @@
+// Serving loop: continuous batching of RS solves of different N and n.
+//
+// Requests are queued by rs_submit (their inputs copied), and a worker thread admits them to
+// slots.  A slot is a context with its own CUDA stream, pinned staging buffers and a completion
+// event; it is kept for later requests of the same configuration.  A request is admitted when an
+// idle slot of its configuration exists, or when a new slot fits the HBM budget (the sum of the
+// slots' workspace bytes), possibly after releasing idle slots of other configurations.  Admitted
+// requests run concurrently on their streams; the worker polls the events, reads the results and
+// wakes the waiters.  The queue is scanned in arrival order, and a request that cannot be
+// admitted yet does not block later requests that can.
+#include "rs_internal.cuh"
+
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Job {
+  unsigned long long ticket = 0;
+  rs_config cfg{};
+  int N = 0;
+  std::vector<double> xyz, Z;
+  int flags = 0;
+  void* pot = nullptr;
+  Clock::time_point t_sub, t_launch;
+  rs_result res{};
+  bool done = false;
+};
+
+struct Slot {
+  rs_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  rs_config cfg{};
+  size_t bytes = 0;
+  double* hx = nullptr;     // pinned staging, 3 * max_particles
+  double* hz = nullptr;     // pinned staging, max_particles
+  std::shared_ptr<Job> job;
+};
+
+bool same_config(const rs_config& a, const rs_config& b) { return std::memcmp(&a, &b, sizeof(rs_config)) == 0; }
+
+}  // namespace
+
+struct rs_server {
+  size_t budget = 0;
+  int max_slots = 0;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Job>> pending;
+  std::unordered_map<unsigned long long, std::shared_ptr<Job>> jobs;
+  std::vector<std::unique_ptr<Slot>> slots;
+  size_t used = 0;
+  unsigned long long next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+
+  void release_slot(size_t i) {
+    Slot& s = *slots[i];
+    rs_destroy(s.ctx);
+    if (s.ev) cudaEventDestroy(s.ev);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.hx) cudaFreeHost(s.hx);
+    if (s.hz) cudaFreeHost(s.hz);
+    used -= s.bytes;
+    slots.erase(slots.begin() + (long)i);
+  }
+
+  // create a slot for cfg; nullptr if a CUDA or library call fails
+  Slot* make_slot(const rs_config& cfg, size_t bytes) {
+    std::unique_ptr<Slot> s(new Slot());
+    s->cfg = cfg;
+    s->bytes = bytes;
+    const size_t cap = (size_t)(cfg.max_particles > 0 ? cfg.max_particles : 1);
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost((void**)&s->hx, sizeof(double) * 3 * cap) != cudaSuccess ||
+        cudaMallocHost((void**)&s->hz, sizeof(double) * cap) != cudaSuccess ||
+        rs_create(&cfg, s->stream, &s->ctx) != RS_OK) {
+      cudaGetLastError();
+      if (s->ctx) rs_destroy(s->ctx);
+      if (s->ev) cudaEventDestroy(s->ev);
+      if (s->stream) cudaStreamDestroy(s->stream);
+      if (s->hx) cudaFreeHost(s->hx);
+      if (s->hz) cudaFreeHost(s->hz);
+      return nullptr;
+    }
+    used += bytes;
+    slots.push_back(std::move(s));
+    return slots.back().get();
+  }
+
+  void finish(const std::shared_ptr<Job>& job, rs_status st, Slot* s) {
+    job->res.status = st;
+    if (st < 0) {
+      const char* m = rs_last_error(s ? s->ctx : nullptr);
+      std::snprintf(job->res.message, sizeof(job->res.message), "%s", (m && *m) ? m : "error");
+    }
+    job->res.latency_ms = ms_between(job->t_sub, Clock::now());
+    job->res.queue_ms = ms_between(job->t_sub, job->t_launch);
+    job->done = true;
+    cv_done.notify_all();
+  }
+
+  void launch(Slot* s, const std::shared_ptr<Job>& job) {
+    job->t_launch = Clock::now();
+    for (size_t i = 0; i < slots.size(); ++i)
+      if (slots[i].get() == s) job->res.slot = (int)i;
+    if (job->N > 0) {
+      std::memcpy(s->hx, job->xyz.data(), sizeof(double) * 3 * (size_t)job->N);
+      std::memcpy(s->hz, job->Z.data(), sizeof(double) * (size_t)job->N);
+    }
+    const int flags = (job->flags & (RS_ENERGY | RS_POTENTIAL)) | RS_INPUT_HOST;
+    rs_status st = rs_solve(s->ctx, job->N, s->hx, s->hz, flags, 0.0, job->pot);
+    if (st != RS_OK) {
+      finish(job, st, s);
+      return;
+    }
+    cudaEventRecord(s->ev, s->stream);
+    s->job = job;
+  }
+
+  void complete(Slot* s) {
+    std::shared_ptr<Job> job = s->job;
+    s->job.reset();
+    rs_stats stt;
+    std::memset(&stt, 0, sizeof(stt));
+    rs_status st = rs_report(s->ctx, &stt);
+    for (int l = 0; l < 3; ++l) job->res.ranks[l] = stt.ranks[l];
+    if (st >= 0 && (job->flags & RS_ENERGY)) {
+      double E = 0.0;
+      rs_status se = rs_energy(s->ctx, &E);
+      job->res.energy = E;
+      if (se != RS_OK) st = se;
+    }
+    finish(job, st, s);
+  }
+
+  // one pass of admissions in arrival order; returns true if anything was launched
+  bool admit() {
+    bool any = false;
+    for (auto it = pending.begin(); it != pending.end();) {
+      std::shared_ptr<Job> job = *it;
+      Slot* chosen = nullptr;
+      for (auto& s : slots)
+        if (!s->job && same_config(s->cfg, job->cfg)) { chosen = s.get(); break; }
+      if (!chosen) {
+        const size_t need = rs_workspace_bytes(&job->cfg);
+        if (need == 0) {                                   // invalid configuration
+          it = pending.erase(it);
+          job->t_launch = Clock::now();
+          finish(job, RS_ERR_INVALID_ARG, nullptr);
+          continue;
+        }
+        // release idle slots of other configurations while the new one does not fit
+        // (the victim is an idle slot of the configuration with the most idle slots)
+        while ((used + need > budget || (int)slots.size() >= max_slots)) {
+          size_t victim = slots.size();
+          int best = 0;
+          for (size_t i = 0; i < slots.size(); ++i) {
+            if (slots[i]->job) continue;
+            int idle_same = 0;
+            for (auto& t : slots)
+              if (!t->job && same_config(t->cfg, slots[i]->cfg)) ++idle_same;
+            if (idle_same > best) { best = idle_same; victim = i; }
+          }
+          if (victim == slots.size()) break;
+          release_slot(victim);
+        }
+        if (used + need <= budget && (int)slots.size() < max_slots) {
+          chosen = make_slot(job->cfg, need);
+          if (!chosen) {                                   // device memory short: free idle slots, retry once
+            for (size_t i = slots.size(); i-- > 0;)
+              if (!slots[i]->job) release_slot(i);
+            chosen = make_slot(job->cfg, need);
+          }
+        }
+        if (!chosen && slots.empty()) {                    // cannot run even alone
+          it = pending.erase(it);
+          job->t_launch = Clock::now();
+          finish(job, RS_ERR_OOM, nullptr);
+          continue;
+        }
+      }
+      if (!chosen) { ++it; continue; }
+      it = pending.erase(it);
+      launch(chosen, job);
+      any = true;
+    }
+    return any;
+  }
+
+  void run() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (true) {
+      bool busy = false;
+      for (auto& s : slots)
+        if (s->job) {
+          busy = true;
+          if (cudaEventQuery(s->ev) == cudaSuccess) complete(s.get());
+        }
+      cudaGetLastError();                                  // cudaErrorNotReady from the polls
+      const bool launched = admit();
+      bool running = false;
+      for (auto& s : slots) running = running || (s->job != nullptr);
+      if (stop && pending.empty() && !running) break;
+      if (!launched) {
+        if (running || busy)
+          cv_work.wait_for(lk, std::chrono::microseconds(50));
+        else
+          cv_work.wait_for(lk, std::chrono::milliseconds(5));
+      }
+    }
+    while (!slots.empty()) release_slot(slots.size() - 1);
+  }
+};
+
+extern "C" rs_status rs_server_create(size_t hbm_budget, int max_slots, rs_server** out) {
+  if (!out || max_slots < 1 || hbm_budget == 0) return RS_ERR_INVALID_ARG;
+  *out = nullptr;
+  rs_server* s = new (std::nothrow) rs_server();
+  if (!s) return RS_ERR_OOM;
+  s->budget = hbm_budget;
+  s->max_slots = max_slots;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return RS_ERR_CUDA;
+  }
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return RS_OK;
+}
+
+extern "C" rs_status rs_submit(rs_server* s, const rs_request* req, unsigned long long* ticket) {
+  if (!s || !req || !ticket || req->N < 0 || (req->N > 0 && (!req->xyz || !req->Z))) return RS_ERR_INVALID_ARG;
+  if (req->N > req->cfg.max_particles) return RS_ERR_CAPACITY;
+  if ((req->flags & RS_POTENTIAL) && !req->potential_out) return RS_ERR_INVALID_ARG;
+  std::shared_ptr<Job> job(new Job());
+  job->cfg = req->cfg;
+  job->N = req->N;
+  job->xyz.assign(req->xyz, req->xyz + 3 * (size_t)req->N);
+  job->Z.assign(req->Z, req->Z + (size_t)req->N);
+  job->flags = req->flags;
+  job->pot = req->potential_out;
+  job->t_sub = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    job->ticket = s->next_ticket++;
+    s->jobs[job->ticket] = job;
+    s->pending.push_back(job);
+  }
+  s->cv_work.notify_one();
+  *ticket = job->ticket;
+  return RS_OK;
+}
+
+extern "C" rs_status rs_wait(rs_server* s, unsigned long long ticket, int timeout_ms, rs_result* out) {
+  if (!s || !out) return RS_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return RS_ERR_INVALID_ARG;
+  std::shared_ptr<Job> job = it->second;
+  const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+  while (!job->done) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !job->done) return RS_ERR_TIMEOUT;
+  }
+  *out = job->res;
+  s->jobs.erase(ticket);
+  return RS_OK;
+}
+
+extern "C" void rs_server_destroy(rs_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  delete s;
+}
+
+extern "C" rs_status rs_server_info(rs_server* s, int* slots, size_t* bytes_in_use, int* queued) {
+  if (!s) return RS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (slots) *slots = (int)s->slots.size();
+  if (bytes_in_use) *bytes_in_use = s->used;
+  if (queued) *queued = (int)s->pending.size();
+  return RS_OK;
+}

@@ -1,0 +1,115 @@
+"""GPU tests of the continuous-batching request loop (``rs_server_*``) on configuration-4
+shaped requests: each result is the same alone and in the mix, admission respects the HBM
+budget and the slot limit, and a served energy matches the oracle within the FP32 serving
+tolerance.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import rs_oracle as O  # noqa: E402
+from workloads import load_config, make_serving_requests  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+SERVE_TOL = 1e-4      # FP32 serving path, relative to the energy scale sum |z_j z_k| / r_jk
+
+
+def _requests(count, nmax, nmin=0):
+    cfg = load_config("c4_serving256")
+    reqs = [r for r in make_serving_requests(cfg, seed=4242, count=max(48, 4 * count)) if nmin <= r.n <= nmax]
+    reqs = [r for r in reqs if len(r.particles.Z) <= 600][:count]
+    return cfg, reqs
+
+
+def _cfg(cfg, n):
+    from paper_1606_09218_gb300 import config_from_workload
+    return config_from_workload(cfg, n=n, max_particles=600)
+
+
+def test_results_same_alone_and_in_mix():
+    """Every request computes its potential (the tensor-core assembly runs concurrently for
+    grids of different sizes) and its energy; the mix gives the results of the lone runs."""
+    from paper_1606_09218_gb300 import RSServer
+    cfg, reqs = _requests(12, 513)
+    assert len(reqs) >= 8 and len({r.n for r in reqs}) >= 3
+    srv = RSServer(hbm_budget=24 << 30, max_slots=6)
+    alone = []
+    pots_alone = []
+    for r in reqs:
+        pot = torch.empty((r.n,) * 3, dtype=torch.float32, device="cuda")
+        res = srv.wait(srv.submit(_cfg(cfg, r.n), r.particles.xyz, r.particles.Z, potential=pot))
+        assert res["status"] >= 0, res
+        alone.append(res)
+        pots_alone.append(pot)
+    pots_mix = [torch.empty((r.n,) * 3, dtype=torch.float32, device="cuda") for r in reqs]
+    tickets = [srv.submit(_cfg(cfg, r.n), r.particles.xyz, r.particles.Z, potential=pots_mix[i])
+               for i, r in enumerate(reqs)]
+    mix = [srv.wait(t) for t in tickets]
+    info = srv.info()
+    assert info["slots"] <= 6 and info["bytes_in_use"] <= (24 << 30)
+    # more than one slot ran in the mix: the requests overlapped on the device
+    assert len({m["slot"] for m in mix}) > 1
+    for r, a, m in zip(reqs, alone, mix):
+        scale = O.energy_scale(r.particles.xyz, r.particles.Z)
+        assert m["status"] == a["status"] and m["ranks"] == a["ranks"], (a, m)
+        assert abs(m["energy"] - a["energy"]) <= 1e-9 * scale, (a, m)
+    for pa, pm in zip(pots_alone, pots_mix):
+        assert float((pa - pm).abs().max()) <= 1e-6 * float(pa.abs().max())
+    srv.close()
+
+
+def test_contexts_of_different_sizes_interleave():
+    """A context keeps working after a context of another grid size has run: the kernels'
+    launch limits are per process, not per context."""
+    from paper_1606_09218_gb300 import RSContext
+    cfg, reqs = _requests(48, 513)
+    big = next(r for r in reqs if r.n == 513)
+    small = next(r for r in reqs if r.n == 129)
+    a = RSContext(_cfg(cfg, 513))
+    pa = a.new_potential()
+    a.solve(big.particles.xyz, big.particles.Z, potential=pa, energy=True)
+    Ea = a.energy()
+    first = pa.clone()
+    b = RSContext(_cfg(cfg, 129))
+    pb = b.new_potential()
+    b.solve(small.particles.xyz, small.particles.Z, potential=pb, energy=True)
+    b.energy()
+    a.solve(big.particles.xyz, big.particles.Z, potential=pa, energy=True)
+    assert abs(a.energy() - Ea) <= 1e-12 * abs(Ea) + 1e-12
+    assert float((pa - first).abs().max()) <= 1e-6 * float(first.abs().max())
+    assert a.report()["status"] >= 0
+    a.close()
+    b.close()
+
+
+def test_admission_by_footprint_serialises_within_budget():
+    """A budget that holds one n = 257 workspace at a time still serves every request."""
+    import ctypes as C
+    from paper_1606_09218_gb300 import RSServer, _lib
+    cfg, reqs = _requests(6, 257)
+    lib = _lib.load()
+    need = max(lib.rs_workspace_bytes(C.byref(_cfg(cfg, r.n))) for r in reqs)
+    srv = RSServer(hbm_budget=int(need * 1.2), max_slots=4)
+    tickets = [srv.submit(_cfg(cfg, r.n), r.particles.xyz, r.particles.Z) for r in reqs]
+    res = [srv.wait(t) for t in tickets]
+    assert all(r["status"] >= 0 for r in res)
+    assert srv.info()["bytes_in_use"] <= int(need * 1.2)
+    srv.close()
+
+
+def test_served_energy_matches_oracle():
+    from paper_1606_09218_gb300 import RSServer
+    cfg, reqs = _requests(1, 129)
+    assert reqs
+    r = reqs[0]
+    srv = RSServer(hbm_budget=8 << 30, max_slots=2)
+    res = srv.wait(srv.submit(_cfg(cfg, r.n), r.particles.xyz, r.particles.Z))
+    srv.close()
+    c = dict(cfg)
+    c.update(cfg["quad_by_n"][str(r.n)])
+    c["n"] = r.n
+    pr = O.Problem(c, r.particles.xyz, r.particles.Z)
+    scale = O.energy_scale(pr.xyz_snapped, pr.z)
+    assert abs(res["energy"] - pr.energy_P0()) <= SERVE_TOL * scale + 3 * cfg["eps"] * scale
