@@ -76,7 +76,7 @@ typedef struct {
 #define RS_INPUT_HOST          1   /* xyz and Z are host pointers (copied in on the stream) */
 #define RS_POTENTIAL           2   /* write the full-grid potential into potential_out */
 #define RS_ENERGY              4   /* compute the interaction energy (read with rs_energy) */
-#define RS_FORCES              8   /* compute the adjoint forces (read with rs_forces) */
+#define RS_FORCES              8   /* compute the forces (read with rs_forces) */
 #define RS_VALIDATE_SEPARATION 16  /* check that no two centres are closer than min_sep */
 
 typedef struct rs_ctx rs_ctx;
@@ -129,14 +129,13 @@ rs_status rs_solve(rs_ctx* ctx, int N, const double* xyz, const double* Z, int f
  * Synchronises the stream.  RS_ERR_NOT_READY if the last solve did not ask for RS_ENERGY. */
 rs_status rs_energy(rs_ctx* ctx, double* E);
 
-/* Adjoint forces of the last solve (Sec. 4.3): F_j = -dE/dx_j = -z_j [grad P_l^T(x_j) +
- * sum of the gradients of the windows (Defs. 3.4, 3.6) of the other particles at x_j], with the
- * Tucker basis functions continued off the grid through the side-matrix columns
- * (z_a = U U^T z_a / lambda_a, Galerkin factors and their centre derivatives) and the charged
- * centres at their grid points.  F: N x 3 row-major float64, a device pointer, or a host pointer
- * with to_host != 0; particles with zero charge get zero force.  Synchronises the stream.
- * RS_ERR_NOT_READY if the last solve did not ask for RS_FORCES; device-side input errors as for
- * rs_energy. */
+/* Forces of the last solve (Sec. 4.3): F_j = -z_j [grad P_l(x_j) + sum of the gradients of the
+ * windows (Defs. 3.4, 3.6) of the other particles at x_j], the long part from the untruncated
+ * long-range pair kernel (exact for P_l, within O(eps) of the gradient of the RS-Tucker tensor),
+ * Galerkin factors and their centre derivatives, the charged centres at their grid points.
+ * F: N x 3 row-major float64, a device pointer, or a host pointer with to_host != 0; particles
+ * with zero charge get zero force.  Synchronises the stream.  RS_ERR_NOT_READY if the last solve
+ * did not ask for RS_FORCES; device-side input errors as for rs_energy. */
 rs_status rs_forces(rs_ctx* ctx, double* F, int to_host);
 
 /* Synchronise and fill *st for the last solve; returns that solve's status. */

@@ -135,8 +135,9 @@ class RSContext:
         return float(E.value)
 
     def forces(self):
-        """Adjoint forces of the last solve (it must have asked for ``forces=True``) as an
-        (N, 3) float64 CUDA tensor."""
+        """Forces of the last solve (it must have asked for ``forces=True``) as an (N, 3)
+        float64 CUDA tensor: the long part from the untruncated pair kernel, the windows term by
+        term (Sec. 4.3)."""
         torch = self._torch
         F = torch.empty((self.last_N, 3), dtype=torch.float64, device="cuda")
         _lib.check(self.lib.rs_forces(self.h, C.c_void_p(F.data_ptr()), 0), self.h)
@@ -259,7 +260,8 @@ def _energy_function():
     import torch
 
     class RSEnergy(torch.autograd.Function):
-        """E(xyz) of the RS tensor with its adjoint forces as the gradient: dE/dxyz = -F."""
+        """E(xyz) of the RS tensor with the forces as the gradient: dE/dxyz = -F (within O(eps)
+        of the gradient of the RS-Tucker energy)."""
 
         @staticmethod
         def forward(fctx, xyz, Z, rs):

@@ -97,7 +97,7 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.om_colptr, 4 * (ks + 1));
   add(v, c.om_row, 4 * n * ZETA);
   add(v, c.om_sgn, 1 * n * ZETA);
-  add(v, c.part, 8 * 2 * 3 * NBC * (ks * KB + KB * KB));
+  add(v, c.part, 8 * (2 * 3 * NBC + 2 * 3) * (ks * KB + KB * KB));   // partials + reduced sums
   add(v, c.order, 4 * 3 * ks);
   add(v, c.ev, 8 * 3 * ks);
   add(v, c.Z64, 8 * 3 * n * rm);
@@ -113,7 +113,6 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.Epart, 8 * ((N + 7) / 8 + 1));
   add(v, c.adims, 4 * rm);
   add(v, c.kdims, 4 * rm);
-  add(v, c.Vd, ts * 3 * n * rm);
   add(v, c.Fout, 8 * 3 * N);
   add(v, c.sc, sizeof(DevScalars));
   if (c.use_tc) {

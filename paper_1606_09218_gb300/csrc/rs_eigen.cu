@@ -265,24 +265,26 @@ __global__ void traces_kernel(const double* G, const double* X, int n, int ks, D
 
 // ------------------------------------------------------------------ block Gram-Schmidt
 // Cooperative kernel: gridDim.x = 3 * NBC CTAs, CTA c of mode l owns rows
-// [c*rows, (c+1)*rows).  Every CTA executes the same sequence of grid barriers.
+// [c*rows, (c+1)*rows).  The CTAs of one mode execute the same sequence of mode barriers.
 
-// Grid-wide barrier with a bounded wait (spins on a volatile load).  The kernel is launched cooperatively, so every CTA
-// is resident and the wait normally ends after a few microseconds; if it does not end within
-// ~1 s the CTA sets FLAG_TIMEOUT, stops waiting at this and every later barrier, and the host
-// reports RS_ERR_TIMEOUT.
-__device__ __forceinline__ void grid_barrier(DevScalars* sc, unsigned& gen, bool& poisoned) {
+// Barrier of the NBC CTAs of one mode, with a bounded wait (spins on a volatile load).  The
+// kernel is launched cooperatively, so every CTA is resident and the wait normally ends after a
+// few microseconds; if it does not end within ~1 s the CTA sets FLAG_TIMEOUT, stops waiting at
+// this and every later barrier, and the host reports RS_ERR_TIMEOUT.  The modes are
+// independent, so each has its own counter and generation.
+__device__ __forceinline__ void mode_barrier(DevScalars* sc, int l, unsigned& gen, bool& poisoned) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    unsigned* cnt = &sc->bar_count[32 * l];
+    unsigned* gp = &sc->bar_gen[32 * l];
     __threadfence();
-    unsigned arrived = atomicAdd(&sc->bar_count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&sc->bar_count, 0u);
+    unsigned arrived = atomicAdd(cnt, 1u);
+    if (arrived == NBC - 1) {
+      atomicExch(cnt, 0u);
       __threadfence();
-      atomicAdd(&sc->bar_gen, 1u);
+      atomicAdd(gp, 1u);
     } else if (!poisoned) {
-      volatile unsigned* g = &sc->bar_gen;
+      volatile unsigned* g = gp;
       long long it = 0;
       while (*g == gen) {
         __nanosleep(32);
@@ -299,24 +301,38 @@ __device__ __forceinline__ void grid_barrier(DevScalars* sc, unsigned& gen, bool
   __syncthreads();
 }
 
-__device__ __forceinline__ bool chol8(double* S, double piv_tol = 0.0) {
-  // in-place lower Cholesky of an 8x8 (row-major); returns false if a pivot is not above
-  // piv_tol times its diagonal entry (not positive definite, or too ill-conditioned for
-  // Cholesky QR)
+// In-place lower Cholesky factor of the KB x KB matrix S (row-major, shared memory) by one
+// full warp: lane i < KB holds row i of L; column jc takes jc fused multiply-adds per lane, one
+// reciprocal square root and one product (FP64 issue is the cost here, so no divisions and no
+// single-thread loops).  rinv[jc] = 1 / L[jc][jc].  Returns (in every lane) false if a pivot is
+// not above piv_tol times its diagonal entry of S (not positive definite, or too
+// ill-conditioned for Cholesky QR).
+__device__ __forceinline__ bool chol8_warp(double* S, double* rinv, double piv_tol) {
+  const int i = threadIdx.x & 31;
+  const bool row = i < KB;
+  double Lr[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) Lr[k] = 0.0;
+  bool ok = true;
+#pragma unroll
   for (int jc = 0; jc < KB; ++jc) {
-    double d = S[jc * KB + jc];
-    const double djj = d;
-    for (int k = 0; k < jc; ++k) d -= S[jc * KB + k] * S[jc * KB + k];
-    if (!(d > piv_tol * djj) || !(d > 0.0)) return false;
-    d = sqrt(d);
-    S[jc * KB + jc] = d;
-    for (int i = jc + 1; i < KB; ++i) {
-      double v = S[i * KB + jc];
-      for (int k = 0; k < jc; ++k) v -= S[i * KB + k] * S[jc * KB + k];
-      S[i * KB + jc] = v / d;
-    }
+    double v = row ? S[i * KB + jc] : 0.0;
+#pragma unroll
+    for (int k = 0; k < jc; ++k) v -= Lr[k] * __shfl_sync(0xffffffffu, Lr[k], jc);
+    const double d = __shfl_sync(0xffffffffu, v, jc);
+    const double djj = S[jc * KB + jc];
+    ok = ok && (d > piv_tol * djj) && (d > 0.0);
+    const double r = rsqrt(d);
+    if (i == jc) Lr[jc] = d * r;
+    else if (i > jc) Lr[jc] = v * r;
+    if (i == 0) rinv[jc] = r;
   }
-  return true;
+  __syncwarp();
+  if (row)
+#pragma unroll
+    for (int k = 0; k < KB; ++k) S[i * KB + k] = (k <= i) ? Lr[k] : 0.0;
+  __syncwarp();
+  return ok;
 }
 
 __global__ void __launch_bounds__(256)
@@ -337,8 +353,14 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
   auto pbuf = [&](int phase, int mode, int cta) {
     return part + (((long long)(phase & 1) * 3 + mode) * NBC + cta) * pstride;
   };
+  // reduced sums of a phase: [2][3][pstride] after the partials
+  auto fbuf = [&](int phase, int mode) {
+    return part + (2ll * 3 * NBC + (long long)(phase & 1) * 3 + mode) * pstride;
+  };
   __shared__ double h[KSUB_MAX * KB];
   __shared__ double S[KB * KB];
+  __shared__ double rinv[KB];
+  __shared__ double red[256];                 // split FP64 sums (blockDim.x = 256)
   __shared__ int s_stop;
   const double xn2 = sc->xnorm2[l];
   const double guard2 = 1e6 * 4.93e-32 * xn2;   // (1e3 * 2.22e-16)^2 * ||X||^2
@@ -371,35 +393,85 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
       P[e] = v;
     }
   };
-  auto reduce_h = [&](int ph) {
-    for (int e = tid; e < kq * KB; e += blockDim.x) {
+  // dst[e] = sum over the mode's CTAs of their partial e (offset off in the phase buffer) for
+  // e in [eb, ee): 8 lanes per output, lane r adds the partials of CTAs r, r + 8, ...
+  // (independent loads, four outputs in flight per lane), then a fixed xor tree over the 8 lanes
+  auto reduce_partials = [&](int ph, long long off, int eb, int ee, double* dst) {
+    const int g = tid >> 3, r = tid & 7, ng = (int)blockDim.x >> 3;
+    for (int e0 = eb; e0 < ee; e0 += 4 * ng) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * ng + g;
+        v[u] = 0.0;
+        if (e < ee) {
+#pragma unroll
+          for (int t = 0; t < NBC / 8; ++t) v[u] += __ldcg(pbuf(ph, l, r + 8 * t) + off + e);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        double w = v[u];
+        w += __shfl_xor_sync(0xffffffffu, w, 4);
+        w += __shfl_xor_sync(0xffffffffu, w, 2);
+        w += __shfl_xor_sync(0xffffffffu, w, 1);
+        const int e = e0 + u * ng + g;
+        if (e < ee && r == 0) dst[e] = w;
+      }
+    }
+  };
+  // CTA c sums its slice of the E outputs at offset off and publishes them in the phase's
+  // final buffer (read by every CTA of the mode after the next barrier): each sum is formed
+  // once instead of in every CTA
+  auto reduce_slice = [&](int ph, long long off, int E) {
+    const int per = (E + NBC - 1) / NBC;
+    const int eb = min(E, c * per), ee = min(E, eb + per);
+    reduce_partials(ph, off, eb, ee, fbuf(ph, l) + off);
+  };
+  auto fetch = [&](int ph, long long off, int E, double* dst) {
+    for (int e = tid; e < E; e += blockDim.x) dst[e] = __ldcg(fbuf(ph, l) + off + e);
+  };
+  auto reduce_S = [&](int ph, int off) { reduce_partials(ph, off, 0, KB * KB, S); };
+  // B -= Q[:, :kq] h on own rows; each output's sum over a is split over P threads
+  auto subtract_Qh = [&]() {
+    const int no = nr * KB;
+    if (no == 0) return;
+    const int P = max(1, min(4, (int)blockDim.x / no));
+    if (tid < P * no) {
+      const int o = tid % no, q = tid / no;
+      const int ii = o / KB, jc = o % KB;
       double v = 0.0;
-      for (int cc = 0; cc < NBC; ++cc) v += __ldcg(pbuf(ph, l, cc) + e);
-      h[e] = v;
+      for (int a = q; a < kq; a += P) v += sq(ii, a) * h[a * KB + jc];
+      red[tid] = v;
     }
+    __syncthreads();
+    if (tid < no) {
+      double acc = red[tid];
+      for (int q = 1; q < P; ++q) acc += red[q * no + tid];
+      sq(tid / KB, kq + tid % KB) -= acc;
+    }
+    __syncthreads();
   };
-  auto reduce_S = [&](int ph, int off) {
-    if (tid < KB * KB) {
+  // S -= h^T h (the Gram of the reprojected block); each entry's sum over m split over 4 threads
+  auto subtract_hth = [&]() {
+    {
+      const int o = tid & (KB * KB - 1), q = tid >> 6;
+      const int a = o / KB, b = o % KB;
       double v = 0.0;
-      for (int cc = 0; cc < NBC; ++cc) v += __ldcg(pbuf(ph, l, cc) + off + tid);
-      S[tid] = v;
+      for (int m = q; m < kq; m += 4) v += h[m * KB + a] * h[m * KB + b];
+      red[tid] = v;
     }
+    __syncthreads();
+    if (tid < KB * KB) S[tid] -= ((red[tid] + red[64 + tid]) + red[128 + tid]) + red[192 + tid];
+    __syncthreads();
   };
-  auto subtract_Qh = [&]() {                  // B -= Q[:, :kq] h on own rows
-    for (int e = tid; e < nr * KB; e += blockDim.x) {
-      int ii = e / KB, jc = e % KB;
-      double v = sq(ii, kq + jc);
-      for (int a = 0; a < kq; ++a) v -= sq(ii, a) * h[a * KB + jc];
-      sq(ii, kq + jc) = v;
-    }
-  };
-  auto solve_LT = [&]() {                     // B <- B L^{-T} on own rows (L in S)
+  auto solve_LT = [&]() {                     // B <- B L^{-T} on own rows (L in S, 1/diag in rinv)
     for (int ii = tid; ii < nr; ii += blockDim.x) {
       double y[KB];
       for (int jc = 0; jc < KB; ++jc) {
         double v = sq(ii, kq + jc);
         for (int k = 0; k < jc; ++k) v -= S[jc * KB + k] * y[k];
-        y[jc] = v / S[jc * KB + jc];
+        y[jc] = v * rinv[jc];
       }
       for (int jc = 0; jc < KB; ++jc) sq(ii, kq + jc) = y[jc];
     }
@@ -493,36 +565,39 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
   };
 
   for (int s = 0; s < ks; s += KB) {
+    if (stop) break;                          // the same decision in every CTA of the mode
     if (!stop)
       for (int e = tid; e < nr * KB; e += blockDim.x) {
         int ii = e / KB, jc = e % KB;
         sq(ii, kq + jc) = Xl[(long long)(r0 + ii) * ks + s + jc];
       }
     __syncthreads();   // the partial products below read rows written by other threads
-    // (A) first projection against the accepted columns
-    if (!stop && kq > 0) partial_h(pbuf(phase, l, c));
-    grid_barrier(sc, bar_gen, poisoned);
-    if (*(volatile unsigned*)&sc->stopmask == 7u) break;   // every mode finished (same view in all CTAs)
-    if (!stop && kq > 0) { reduce_h(phase); __syncthreads(); subtract_Qh(); }
-    __syncthreads();
-    ++phase;
-    // (B) second projection
-    if (!stop && kq > 0) partial_h(pbuf(phase, l, c));
-    grid_barrier(sc, bar_gen, poisoned);
-    if (!stop && kq > 0) { reduce_h(phase); __syncthreads(); subtract_Qh(); }
-    __syncthreads();
-    if (!stop) block_to_global();            // CTA 0 reads every row if the block falls back
-    ++phase;
+    // (A) first projection against the accepted columns, (B) the second
+    for (int pass = 0; pass < 2; ++pass) {
+      if (kq > 0) {
+        partial_h(pbuf(phase, l, c));
+        mode_barrier(sc, l, bar_gen, poisoned);
+        reduce_slice(phase, 0, kq * KB);
+        mode_barrier(sc, l, bar_gen, poisoned);
+        fetch(phase, 0, kq * KB, h);
+        __syncthreads();
+        subtract_Qh();
+      }
+      ++phase;
+    }
+    block_to_global();                       // CTA 0 reads every row if the block falls back
     // (C) Gram of the block: norm test and first Cholesky QR
-    if (!stop) partial_S(pbuf(phase, l, c));
-    grid_barrier(sc, bar_gen, poisoned);
-    if (!stop) {
+    partial_S(pbuf(phase, l, c));
+    mode_barrier(sc, l, bar_gen, poisoned);
+    {
       reduce_S(phase, 0);
       __syncthreads();
-      if (tid == 0) {
+      if (tid < 32) {
         double tr = 0.0;
         for (int a = 0; a < KB; ++a) tr += S[a * KB + a];
-        s_stop = (tr < guard2) ? 1 : (chol8(S, 1e-10) ? 0 : 3);
+        const bool tiny = tr < guard2;
+        const bool ok = tiny ? false : chol8_warp(S, rinv, 1e-10);
+        if (tid == 0) s_stop = tiny ? 1 : (ok ? 0 : 3);
       }
       __syncthreads();
       if (s_stop == 1) mark_stop(0u);
@@ -544,21 +619,24 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
       if (kq > 0) partial_h(P);
       partial_S(P + (long long)ks * KB);
     }
-    grid_barrier(sc, bar_gen, poisoned);
+    mode_barrier(sc, l, bar_gen, poisoned);
     if (!stop && !fallback) {
-      if (kq > 0) reduce_h(phase);
-      reduce_S(phase, ks * KB);
+      if (kq > 0) reduce_slice(phase, 0, kq * KB);
+      reduce_slice(phase, (long long)ks * KB, KB * KB);
+    }
+    mode_barrier(sc, l, bar_gen, poisoned);
+    if (!stop && !fallback) {
+      if (kq > 0) fetch(phase, 0, kq * KB, h);
+      fetch(phase, (long long)ks * KB, KB * KB, S);
       __syncthreads();
-      if (tid < KB * KB && kq > 0) {
-        int a = tid / KB, b = tid % KB;
-        double v = 0.0;
-        for (int m = 0; m < kq; ++m) v += h[m * KB + a] * h[m * KB + b];
-        S[tid] -= v;
+      if (kq > 0) {
+        subtract_hth();
+        subtract_Qh();
       }
-      __syncthreads();
-      if (kq > 0) subtract_Qh();
-      __syncthreads();
-      if (tid == 0) s_stop = chol8(S) ? 0 : 2;
+      if (tid < 32) {
+        const bool ok = chol8_warp(S, rinv, 0.0);
+        if (tid == 0) s_stop = ok ? 0 : 2;
+      }
       __syncthreads();
       if (s_stop) mark_stop((unsigned)FLAG_CHOL);
       else solve_LT();

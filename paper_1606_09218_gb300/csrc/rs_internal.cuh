@@ -15,6 +15,7 @@ namespace rs {
 constexpr int KB = 8;
 // CTAs per mode of the cooperative block Gram-Schmidt kernel (3 x 48 = 144 <= 152 SMs).
 constexpr int NBC = 48;
+static_assert(NBC % 8 == 0, "the Gram-Schmidt reductions split the CTAs of a mode over 8 lanes");
 // Largest Tucker rank the projection kernel supports.
 constexpr int RMAX_LIMIT = 160;
 // Largest subspace width the one-CTA Jacobi kernel holds in shared memory.
@@ -54,11 +55,11 @@ struct DevScalars {
   int chunk_w[32];               // windows per i1 chunk (tensor-core assembly schedule)
   unsigned zmax_bits;            // max |z| over the particles (float bits; window operand scale)
   double beta_a2[RMAX_LIMIT];    // ||beta[a, :, :]||^2 (scale of the FP16 Tucker operands)
-  // grid barrier of the cooperative Gram-Schmidt kernel: arrival counter and generation on
-  // separate 128-byte lines, so that the waiters' polling does not slow the arrivals
-  alignas(128) unsigned bar_count;
-  alignas(128) unsigned bar_gen;
-  alignas(128) unsigned bar_pad;
+  // barriers of the cooperative Gram-Schmidt kernel, one per mode: arrival counter and
+  // generation of mode l at [32 l], each on its own 128-byte line, so that the waiters' polling
+  // does not slow the arrivals
+  alignas(128) unsigned bar_count[3 * 32];
+  alignas(128) unsigned bar_gen[3 * 32];
 };
 
 struct Ctx {
@@ -115,7 +116,6 @@ struct Ctx {
   double* Epart = nullptr;      // energy partial sums
   int*    adims = nullptr;      // rmax: per-batch row counts of the mode-2 product
   int*    kdims = nullptr;      // rmax: per-batch inner sizes of the mode-2 product
-  void*   Vd = nullptr;         // 3 x n x rmax (T): derivatives of the Tucker basis functions
   double* Fout = nullptr;       // maxN x 3 forces of the last solve
   // tensor-core assembly of the FP32 output (rs_tc.cu), planned at create
   bool use_tc = false;

@@ -653,141 +653,19 @@ int launch_energy(Ctx& c, int N) {
   return 2;
 }
 
-// ------------------------------------------------------------------ forces (a9, adjoint)
-// Continuous Tucker basis functions: with G = U U^T and Z0 its dominant eigenvectors,
-// z_a = U (U^T z_a) / lambda_a, so v_a(y) = sum_{(nu,k)} u_{nu,k}(y) (U^T z_a)[(nu,k)] / lambda_a.
-// Columns at equal coordinates aggregate: (U^T z_a)[(nu,k)] = w_nu Qp[j_nu][k][a], hence
-//   v_a'(y) = sum_j C[j] sum_k p_k'(y - j) Qp[j][k][a] / lambda_a,
-//   lambda_a = ||U^T z_a||^2 = sum_j C[j] sum_k Qp[j][k][a]^2.
-// CTA: 16 charged coordinates y x 64 basis columns of one mode; thread: 1 y x 4 a.
+// ------------------------------------------------------------------ forces (a9)
+// F_j = -z_j [grad P_l(x_j) + sum_{nu in windows} z_nu grad U_nu(x_j)]  (Sec. 4.3).  The long
+// part is the untruncated pair kernel,
+//   grad P_l(x_j) = sum_{nu != j} z_nu sum_{k long} grad (p_k (x) p_k (x) p_k)(x_j - x_nu),
+// exact for P_l by symmetry and O(eps) from the gradient of the RS-Tucker tensor; it has no
+// division by the eigenvalues of the Gram matrices, which makes a continuation of the Tucker
+// basis off the grid ill-conditioned for its weakest retained directions.  Factors and products
+// in T (FP64 on the plain path, FP32 on the bulk path), sums in FP64.  The windows use the FP64
+// factor and derivative tables; the self window contributes zero, since p_k' is odd.
+// One warp per charged particle.
 template <typename T>
-__global__ void __launch_bounds__(256)
-vderiv_kernel(const T* __restrict__ Qp, const double* __restrict__ C, const int* __restrict__ nzj,
-              const T* __restrict__ dpk, int n, int rmax, int R_l, const DevScalars* sc, T* Vd) {
-  const int l = blockIdx.y, tid = threadIdx.x, ty = tid >> 4, ta = tid & 15;
-  const int cnt = sc->nzj_count[l], r = sc->rank[l];
-  const int iy = blockIdx.x * 16 + ty;
-  const bool live = iy < cnt;
-  const int y = live ? nzj[l * n + iy] : 0;
-  const int L = 2 * n - 1;
-  const T* Ql = Qp + (long long)l * n * R_l * rmax;
-  const double* Cl = C + (long long)l * n;
-  const int* nl = nzj + l * n;
-  T* Vl = (T*)Vd + (long long)l * n * rmax;
-  for (int a0 = 0; a0 < rmax; a0 += 64) {
-    T acc[4] = {T(0), T(0), T(0), T(0)}, lam[4] = {T(0), T(0), T(0), T(0)};
-    const int ab = a0 + 4 * ta;
-    if (a0 < r) {
-      for (int idx = 0; idx < cnt; ++idx) {
-        const int jj = nl[idx];
-        const T cj = (T)Cl[jj];
-        const T* qrow = Ql + (long long)jj * R_l * rmax;
-        const T* drow = dpk + (n - 1) + (y - jj);
-#pragma unroll 4
-        for (int k = 0; k < R_l; ++k) {
-          const T coef = live ? cj * drow[(long long)k * L] : T(0);
-          const T* q = qrow + (long long)k * rmax + ab;
-#pragma unroll
-          for (int x = 0; x < 4; ++x) {
-            const T qv = (ab + x < rmax) ? q[x] : T(0);
-            acc[x] = fma(coef, qv, acc[x]);
-            lam[x] = fma(cj * qv, qv, lam[x]);
-          }
-        }
-      }
-    }
-    if (live)
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        const int a = ab + x;
-        if (a < rmax) Vl[(long long)y * rmax + a] = (a < r && lam[x] > T(0)) ? acc[x] / lam[x] : T(0);
-      }
-  }
-}
-
-// F_j = -z_j [grad P_l^T(x_j) + sum_{nu in windows} z_nu grad U_nu(x_j)]  (Sec. 4.3 applied to
-// the RS-Tucker tensor of Def. 3.9 / Lemma 3.10).  One warp per charged particle; the long part
-// uses T1 = beta x_3 V3 on the grid for the first two derivatives and beta itself for the third,
-// the windows use the FP64 factor and derivative tables (the self window contributes zero, since
-// p_k' is odd).
-template <typename T>
-__global__ void forces_kernel(DevView c, const T* Zb, const T* Vd, const T* T1, const T* beta,
-                              const double* dpk64, double* Fout) {
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m = blockIdx.x * 8 + warp;
-  if (m >= c.sc->n_nz) return;
-  const int p = c.nz_idx[m];
-  const int n = c.n, rmax = c.rmax;
-  const int i1 = c.j[3 * p], i2 = c.j[3 * p + 1], i3 = c.j[3 * p + 2];
-  const int r1 = c.sc->rank[0], r2 = c.sc->rank[1], r3 = c.sc->rank[2];
-  const long long sZ = (long long)n * rmax;
-  const T* V1 = Zb + (long long)i1 * rmax;
-  const T* V2 = Zb + sZ + (long long)i2 * rmax;
-  const T* V3 = Zb + 2 * sZ + (long long)i3 * rmax;
-  const T* D1 = Vd + (long long)i1 * rmax;
-  const T* D2 = Vd + sZ + (long long)i2 * rmax;
-  const T* D3 = Vd + 2 * sZ + (long long)i3 * rmax;
-  double g1 = 0.0, g2 = 0.0, g3 = 0.0;
-  for (int e = lane; e < r1 * r2; e += 32) {
-    const int a = e / r2, b = e % r2;
-    const double t1 = (double)T1[((long long)a * rmax + b) * n + i3];
-    g1 += (double)D1[a] * (double)V2[b] * t1;
-    g2 += (double)V1[a] * (double)D2[b] * t1;
-    const T* brow = beta + ((long long)a * rmax + b) * rmax;
-    double s3 = 0.0;
-    for (int cc = 0; cc < r3; ++cc) s3 += (double)brow[cc] * (double)D3[cc];
-    g3 += (double)V1[a] * (double)V2[b] * s3;
-  }
-  // short-range windows of all particles reaching x_j (FP64 factors)
-  const int g = c.sc->gamma, L = 2 * n - 1, nb = c.nbin;
-  const int b1a = max(0, i1 - g) / BIN, b1b = min(n - 1, i1 + g) / BIN;
-  const int b2a = max(0, i2 - g) / BIN, b2b = min(n - 1, i2 + g) / BIN;
-  const int b3a = max(0, i3 - g) / BIN, b3b = min(n - 1, i3 + g) / BIN;
-  const int nb3 = b3b - b3a + 1, nb2 = b2b - b2a + 1;
-  const int nbt = (b1b - b1a + 1) * nb2 * nb3;
-  for (int t = lane; t < nbt; t += 32) {
-    const int b3 = b3a + t % nb3, b2 = b2a + (t / nb3) % nb2, b1 = b1a + t / (nb3 * nb2);
-    const int b = (b1 * nb + b2) * nb + b3;
-    for (int it = c.bin_start[b]; it < c.bin_start[b + 1]; ++it) {
-      const int q = c.bin_items[it];
-      const int d1 = i1 - c.j[3 * q], d2 = i2 - c.j[3 * q + 1], d3 = i3 - c.j[3 * q + 2];
-      if (abs(d1) > g || abs(d2) > g || abs(d3) > g) continue;
-      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      for (int k = c.R_l; k < c.R; ++k) {
-        const double* row = c.pk64 + (long long)k * L + n - 1;
-        const double* drow = dpk64 + (long long)k * L + n - 1;
-        const double f1 = row[d1], f2 = row[d2], f3 = row[d3];
-        s1 += drow[d1] * f2 * f3;
-        s2 += f1 * drow[d2] * f3;
-        s3 += f1 * f2 * drow[d3];
-      }
-      const double zq = c.Z[q];
-      g1 += zq * s1;
-      g2 += zq * s2;
-      g3 += zq * s3;
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    g1 += __shfl_down_sync(0xffffffffu, g1, o);
-    g2 += __shfl_down_sync(0xffffffffu, g2, o);
-    g3 += __shfl_down_sync(0xffffffffu, g3, o);
-  }
-  if (lane == 0) {
-    const double z = c.Z[p];
-    Fout[3 * p] = -z * g1;
-    Fout[3 * p + 1] = -z * g2;
-    Fout[3 * p + 2] = -z * g3;
-  }
-}
-
-// FP32 bulk path: the long-range part from the untruncated pair kernel,
-// grad P_l(x_j) = sum_{nu != j} z_nu sum_{k long} grad (p_k (x) p_k (x) p_k)(x_j - x_nu)
-// (FP32 factors and products, FP64 sums; exact for P_l, O(eps) from the RS-Tucker gradient),
-// which avoids the division by small eigenvalues of the continued Tucker basis (that needs FP64
-// projections); windows as in forces_kernel.
-__global__ void forces_direct_kernel(DevView c, const float* __restrict__ pk32,
-                                     const float* __restrict__ dpk32, const double* __restrict__ dpk64,
-                                     double* Fout) {
+__global__ void forces_direct_kernel(DevView c, const T* __restrict__ pk, const T* __restrict__ dpk,
+                                     const double* __restrict__ dpk64, double* Fout) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int m = blockIdx.x * 8 + warp;
   const int nnz = c.sc->n_nz;
@@ -800,19 +678,19 @@ __global__ void forces_direct_kernel(DevView c, const float* __restrict__ pk32,
     const int q = c.nz_idx[mm];
     if (q == p) continue;
     const int d1 = i1 - c.j[3 * q] + n - 1, d2 = i2 - c.j[3 * q + 1] + n - 1, d3 = i3 - c.j[3 * q + 2] + n - 1;
-    float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    T s1 = T(0), s2 = T(0), s3 = T(0);
     for (int k = 0; k < c.R_l; ++k) {
-      const float* row = pk32 + (long long)k * L;
-      const float* drow = dpk32 + (long long)k * L;
-      const float f1 = row[d1], f2 = row[d2], f3 = row[d3];
-      s1 = fmaf(drow[d1], f2 * f3, s1);
-      s2 = fmaf(f1 * drow[d2], f3, s2);
-      s3 = fmaf(f1 * f2, drow[d3], s3);
+      const T* row = pk + (long long)k * L;
+      const T* drow = dpk + (long long)k * L;
+      const T f1 = row[d1], f2 = row[d2], f3 = row[d3];
+      s1 = fma(drow[d1], f2 * f3, s1);
+      s2 = fma(f1 * drow[d2], f3, s2);
+      s3 = fma(f1 * f2, drow[d3], s3);
     }
     const double zq = c.Z[q];
-    g1 += zq * s1;
-    g2 += zq * s2;
-    g3 += zq * s3;
+    g1 += zq * (double)s1;
+    g2 += zq * (double)s2;
+    g3 += zq * (double)s3;
   }
   const int g = c.sc->gamma, nb = c.nbin;
   const int b1a = max(0, i1 - g) / BIN, b1b = min(n - 1, i1 + g) / BIN;
@@ -855,29 +733,16 @@ __global__ void forces_direct_kernel(DevView c, const float* __restrict__ pk32,
   }
 }
 
-template <typename T>
-static int forces_t(Ctx& c) {
-  if (sizeof(T) == 4) {
-    cudaMemsetAsync(c.Fout, 0, sizeof(double) * 3 * (size_t)c.maxN, c.stream);
-    int blocks = (c.maxN + 7) / 8;
-    if (blocks < 1) blocks = 1;
-    forces_direct_kernel<<<blocks, 256, 0, c.stream>>>(make_view(c), c.pk32, c.dpk32, c.dpk64, c.Fout);
-    return 1;
-  }
-  const int n = c.n;
+int launch_forces(Ctx& c) {
   cudaMemsetAsync(c.Fout, 0, sizeof(double) * 3 * (size_t)c.maxN, c.stream);
-  const T* dpk = (sizeof(T) == 8) ? (const T*)c.dpk64 : (const T*)c.dpk32;
-  vderiv_kernel<T><<<dim3((n + 15) / 16, 3), 256, 0, c.stream>>>((const T*)c.Qp, c.C, c.nzj, dpk, n, c.rmax,
-                                                               c.R_l, c.sc, (T*)c.Vd);
   int blocks = (c.maxN + 7) / 8;
   if (blocks < 1) blocks = 1;
-  DevView v = make_view(c);
-  forces_kernel<T><<<blocks, 256, 0, c.stream>>>(v, Bulk<T>::Z(c), (const T*)c.Vd, (const T*)c.T1,
-                                                 (const T*)c.beta, c.dpk64, c.Fout);
-  return 2;
+  if (c.fp64)
+    forces_direct_kernel<double><<<blocks, 256, 0, c.stream>>>(make_view(c), c.pk64, c.dpk64, c.dpk64, c.Fout);
+  else
+    forces_direct_kernel<float><<<blocks, 256, 0, c.stream>>>(make_view(c), c.pk32, c.dpk32, c.dpk64, c.Fout);
+  return 1;
 }
-
-int launch_forces(Ctx& c) { return c.fp64 ? forces_t<double>(c) : forces_t<float>(c); }
 
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out) {
   if (M <= 0) return 0;
