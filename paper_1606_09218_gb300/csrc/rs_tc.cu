@@ -65,7 +65,7 @@ constexpr long long WAIT_LIMIT = 4000000;
 constexpr int SMEM_LIMIT = 232448;         // opt-in shared memory per CTA on this GPU family
 constexpr int SMEM_RESERVE = 1024;         // static shared memory of the kernel
 constexpr double COST_TILE = 2500.0;       // relative cost of one tile job (output bound)
-constexpr double COST_WINDOW = 60.0;       // relative cost of one window of a job
+constexpr double COST_WINDOW = 250.0;      // relative cost of one window of a job (fitted to role traces)
 constexpr int TT_ROWS = 32;                // i2 rows per CTA of the T2 tile kernel
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -598,13 +598,43 @@ assemble_kernel(const AsmArgs g) {
     __syncwarp();
   } else if (warp < WARP_EPI) {
     // ------------------------------------------------------------ producers
+    // Thread pt builds row m = pt of the A operands; up to two pairs of windows (two slots) per
+    // step, with every load issued before the arithmetic, so the latency of one pair hides
+    // behind the other.  The descriptors of pair q are written by lane 0 of producer warp q mod 4.
     const int pt = tid - WARP_PROD * 32;       // operand row m
+    const int pw = warp - WARP_PROD;           // producer warp
     unsigned char* slot_base = smem + g.off_slot;
     const float sA = ldexpf(1.0f, s_shiftA);
     const uint32_t tbl_h = smem_addr(Th), tbl_l = smem_addr(Tl);
+    const float4* tab4 = (const float4*)tab;
     int pg = 0, sl = 0;
     uint32_t slph = 0;
     int used = 0;                              // pair slots filled so far (first ns need no wait)
+    // 16-column groups of the chunk that a pair reaches (all of them for the first pair of a
+    // job, which overwrites the window accumulator), the table rows of its first row for each
+    // window, and the descriptors
+    auto header = [&](int slot, int q, int4 wa, int4 wb, bool has_b) {
+      int s0, s1;
+      if (q == 0) {
+        s0 = 0;
+        s1 = (g.Nc >> 4) - 1;
+      } else {
+        int lo1 = max(c0, wa.x - gam) - c0, hi1 = min(cl, wa.x + gam) - c0;
+        if (has_b) {
+          lo1 = min(lo1, max(c0, wb.x - gam) - c0);
+          hi1 = max(hi1, min(cl, wb.x + gam) - c0);
+        }
+        s0 = lo1 >> 4;
+        s1 = hi1 >> 4;
+      }
+      const int rho_a = c0 + 16 * s0 - wa.x + g.D0;
+      const int rho_b = c0 + 16 * s0 - wb.x + g.D0;        // >= rho_a
+      const uint32_t lbo = (uint32_t)(rho_b - rho_a) * 16u;
+      hdr_db[slot][0] = smem_desc(tbl_h + (uint32_t)rho_a * 16u, lbo, 128);
+      hdr_db[slot][1] = smem_desc(tbl_l + (uint32_t)rho_a * 16u, lbo, 128);
+      hdr_id[slot][0] = idesc_f16(16 * (s1 - s0 + 1));
+      hdr_id[slot][1] = (uint32_t)(16 * s0);
+    };
     for (int t = 0; t < njobs; ++t) {
       const int T = j0 + t * jstride;
       int b = pg & 1;
@@ -615,7 +645,7 @@ assemble_kernel(const AsmArgs g) {
       const int i2 = valid ? (int)(p / n) : 0, i3 = valid ? (int)(p - (long long)i2 * n) : 0;
       bool ok = true;
       int pos = 0, pn = page_n[b];
-      for (int q = 0; 2 * q < nw; ++q) {
+      for (int q = 0; 2 * q < nw;) {
         if (pos == pn) {                       // pages hold an even number of records
           __syncwarp();
           if (lane == 0) mbar_arrive(&bar_list_empty[b]);
@@ -625,64 +655,74 @@ assemble_kernel(const AsmArgs g) {
           pos = 0;
           pn = page_n[b];
         }
-        int4 wa = lists[b * LIST_CAP + pos];
-        const bool has_b = pos + 1 < pn;
-        int4 wb = has_b ? lists[b * LIST_CAP + pos + 1] : wa;
-        pos += 2;
-        if (has_b && wb.x > wa.x) { const int4 tmp = wa; wa = wb; wb = tmp; }   // chunk 0: larger j1
-        if (used >= g.ns && !warp_wait(&bar_slot_free[sl], slph ^ 1u, abort_flag, sc)) { ok = false; break; }
-        unsigned char* sbh = slot_base + (size_t)sl * 2 * SLOT_HALF;
-        unsigned char* sbl = sbh + SLOT_HALF;
+        const int np_ = (2 * (q + 1) < nw && pos + 2 < pn) ? 2 : 1;   // pairs in this step
+        int4 w[4];
+        bool live[4];
 #pragma unroll
-        for (int w = 0; w < 2; ++w) {
-          const int4 rc = w == 0 ? wa : wb;
-          const bool live = (w == 0 || has_b) && valid;
-          const float z = __int_as_float(rc.w) * sA;
-          const int d2 = i2 - rc.y, d3 = i3 - rc.z;
-          const bool in23 = live && d2 >= -gam && d2 <= gam && d3 >= -gam && d3 <= gam;
-          const float4* r2 = (const float4*)tab + 2 * (in23 ? d2 + g.gcap : 0);
-          const float4* r3 = (const float4*)tab + 2 * (in23 ? d3 + g.gcap : 0);
-          const float4 a0 = r2[0], a1 = r2[1], b0 = r3[0], b1 = r3[1];
-          const float zz = in23 ? z : 0.f;
-          uint4 hi, lo;
-          split_h2(zz * a0.x * b0.x, zz * a0.y * b0.y, hi.x, lo.x);
-          split_h2(zz * a0.z * b0.z, zz * a0.w * b0.w, hi.y, lo.y);
-          split_h2(zz * a1.x * b1.x, zz * a1.y * b1.y, hi.z, lo.z);
-          split_h2(zz * a1.z * b1.z, zz * a1.w * b1.w, hi.w, lo.w);
-          const uint32_t off = kmajor_offset(pt, w, 2);
-          *(uint4*)(sbh + off) = hi;
-          *(uint4*)(sbl + off) = lo;
+        for (int u = 0; u < 4; ++u) {
+          live[u] = (u >> 1) < np_ && pos + u < pn;
+          // a missing second window repeats the first of its pair (zero operand, lbo 0)
+          const int r = live[u] ? pos + u : ((u >> 1) < np_ ? pos + (u & 2) : pos);
+          w[u] = lists[b * LIST_CAP + r];
         }
-        if (pt == 0) {
-          // 16-column groups of the chunk that the pair reaches (all of them for the first
-          // pair of a job, which overwrites the window accumulator), the table rows of the
-          // first row for each window, and the descriptors
-          int s0, s1;
-          if (q == 0) {
-            s0 = 0;
-            s1 = (g.Nc >> 4) - 1;
-          } else {
-            int lo1 = max(c0, wa.x - gam) - c0, hi1 = min(cl, wa.x + gam) - c0;
-            if (has_b) {
-              lo1 = min(lo1, max(c0, wb.x - gam) - c0);
-              hi1 = max(hi1, min(cl, wb.x + gam) - c0);
-            }
-            s0 = lo1 >> 4;
-            s1 = hi1 >> 4;
+#pragma unroll
+        for (int v = 0; v < 2; ++v)            // chunk 0 of a pair: the window with the larger j1
+          if (live[2 * v + 1] && w[2 * v + 1].x > w[2 * v].x) {
+            const int4 tmp = w[2 * v];
+            w[2 * v] = w[2 * v + 1];
+            w[2 * v + 1] = tmp;
           }
-          const int rho_a = c0 + 16 * s0 - wa.x + g.D0;
-          const int rho_b = c0 + 16 * s0 - wb.x + g.D0;        // >= rho_a
-          const uint32_t lbo = (uint32_t)(rho_b - rho_a) * 16u;
-          hdr_db[sl][0] = smem_desc(tbl_h + (uint32_t)rho_a * 16u, lbo, 128);
-          hdr_db[sl][1] = smem_desc(tbl_l + (uint32_t)rho_a * 16u, lbo, 128);
-          hdr_id[sl][0] = idesc_f16(16 * (s1 - s0 + 1));
-          hdr_id[sl][1] = (uint32_t)(16 * s0);
+        // factor rows of the four windows, loaded before any slot wait
+        float4 ra[4][2], rb[4][2];
+        float zz[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int d2 = i2 - w[u].y, d3 = i3 - w[u].z;
+          const bool in23 = live[u] && valid && d2 >= -gam && d2 <= gam && d3 >= -gam && d3 <= gam;
+          const float4* r2 = tab4 + 2 * (in23 ? d2 + g.gcap : 0);
+          const float4* r3 = tab4 + 2 * (in23 ? d3 + g.gcap : 0);
+          ra[u][0] = r2[0];
+          ra[u][1] = r2[1];
+          rb[u][0] = r3[0];
+          rb[u][1] = r3[1];
+          zz[u] = in23 ? __int_as_float(w[u].w) * sA : 0.f;
         }
+        const int sl1 = (sl + 1 == g.ns) ? 0 : sl + 1;
+        const uint32_t slph1 = (sl + 1 == g.ns) ? (slph ^ 1u) : slph;
+        if (used >= g.ns && !warp_wait(&bar_slot_free[sl], slph ^ 1u, abort_flag, sc)) { ok = false; break; }
+        if (np_ == 2 && used + 1 >= g.ns && !warp_wait(&bar_slot_free[sl1], slph1 ^ 1u, abort_flag, sc)) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if ((u >> 1) < np_) {
+            unsigned char* sbh = slot_base + (size_t)((u >> 1) ? sl1 : sl) * 2 * SLOT_HALF;
+            unsigned char* sbl = sbh + SLOT_HALF;
+            const float z = zz[u];
+            uint4 hi, lo;
+            split_h2(z * ra[u][0].x * rb[u][0].x, z * ra[u][0].y * rb[u][0].y, hi.x, lo.x);
+            split_h2(z * ra[u][0].z * rb[u][0].z, z * ra[u][0].w * rb[u][0].w, hi.y, lo.y);
+            split_h2(z * ra[u][1].x * rb[u][1].x, z * ra[u][1].y * rb[u][1].y, hi.z, lo.z);
+            split_h2(z * ra[u][1].z * rb[u][1].z, z * ra[u][1].w * rb[u][1].w, hi.w, lo.w);
+            const uint32_t off = kmajor_offset(pt, u & 1, 2);
+            *(uint4*)(sbh + off) = hi;
+            *(uint4*)(sbl + off) = lo;
+          }
+        }
+        if (lane == 0 && (q & 3) == pw) header(sl, q, w[0], w[1], live[1]);
+        if (np_ == 2 && lane == 0 && ((q + 1) & 3) == pw) header(sl1, q + 1, w[2], w[3], live[3]);
         fence_proxy_async();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&bar_slot_full[sl]);
-        if (++sl == g.ns) { sl = 0; slph ^= 1u; }
-        ++used;
+        if (lane == 0) {
+          mbar_arrive(&bar_slot_full[sl]);
+          if (np_ == 2) mbar_arrive(&bar_slot_full[sl1]);
+        }
+        for (int u = 0; u < np_; ++u)
+          if (++sl == g.ns) { sl = 0; slph ^= 1u; }
+        used += np_;
+        q += np_;
+        pos += 2 * np_;
       }
       if (!ok) break;
       __syncwarp();
