@@ -127,6 +127,7 @@ struct Ctx {
   int tc_na = 0, tc_ns = 0;     // stages of the T2 tiles and of the window operand pairs
   int tc_grid = 0;
   size_t tc_smem = 0;           // dynamic shared memory of the assembly kernel
+  bool tc_staged = false;       // assembly epilogue through shared staging rows
   long long wl_cap = 0;         // capacity of the window lists (entries)
   int*       wl_count = nullptr;   // ntiles + 1
   int*       wl_start = nullptr;   // ntiles + 1

@@ -29,9 +29,10 @@
 // CTA (persistent, one per SM, 14 warps):
 //   warp 0     tensor-memory owner; lane 0 issues the MMAs (straight-line, descriptors precomputed)
 //   warp 1     scheduler: bulk copy of the T2 tiles of the next jobs, window list pages
-//   warps 2-5  producers: window operand pairs -> ring of slots (+ ready-made descriptors)
-//   warps 6-13 epilogue: tensor memory -> registers -> shared staging -> bulk stores of the
-//              16-byte aligned middle of each plane row, scalar stores at its two ends
+//   warps 2-5  producers: window operand pairs -> ring of slots (+ ready-made descriptors),
+//              two pairs per step when two slots are free
+//   warps 6-13 epilogue: tensor memory -> registers -> global, each warp writing 128-byte
+//              runs of a plane row (streaming stores)
 // A CTA keeps one i1 chunk (its V1 rows, split, as the B operand of the Tucker part) and walks
 // over the tiles; the CTAs are spread over the chunks in proportion to their work (tiles plus
 // windows).  Both accumulators are double-buffered so that the stores of one tile overlap the
@@ -139,17 +140,6 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 }
 
 // shared -> global bulk copy (16-byte aligned, size % 16 == 0), tracked by bulk groups
-__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"((uint64_t)dst),
-               "r"(smem_addr(src)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
 
 // split a pair of FP32 values into FP16 hi / lo pairs (first value in the low half)
 __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
@@ -210,6 +200,17 @@ __device__ __forceinline__ void fence_before_sync() {
 __device__ __forceinline__ void fence_after_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"((uint64_t)dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -255,6 +256,7 @@ struct AsmArgs {
   int n, L, R_l, R_s;
   int nch, Nc, kp, gcap, TR, D0, ntiles, dstride, tmem_cols, na, ns;
   uint32_t off_bv, off_a, off_slot, off_tbl, off_tab, off_list, off_stage;
+  int staged;                  // epilogue through shared staging rows and bulk stores
   uint32_t bv_half, a_half, tbl_half;   // bytes of each hi part (the lo part follows)
 };
 
@@ -655,7 +657,8 @@ assemble_kernel(const AsmArgs g) {
           pos = 0;
           pn = page_n[b];
         }
-        const int np_ = (2 * (q + 1) < nw && pos + 2 < pn) ? 2 : 1;   // pairs in this step
+        // pairs in this step: two need two distinct slots
+        const int np_ = (g.ns >= 2 && 2 * (q + 1) < nw && pos + 2 < pn) ? 2 : 1;
         int4 w[4];
         bool live[4];
 #pragma unroll
@@ -737,8 +740,8 @@ assemble_kernel(const AsmArgs g) {
     const int hw = g.Nc >> 1;
     const int cb = half * hw, ce = cb + hw;
     const float uT = ldexpf(1.0f, -s_shiftT), uW = ldexpf(1.0f, -(s_shiftA + s_shiftB));
-    float* stage = (float*)(smem + g.off_stage) + half * 32 * STG_ROW;
     const int m = 32 * q + lane;
+    float* stage = (float*)(smem + g.off_stage) + half * 32 * STG_ROW;
     for (int t = 0; t < njobs; ++t) {
       const int T = j0 + t * jstride;
       bool has_w = false;
@@ -761,37 +764,53 @@ assemble_kernel(const AsmArgs g) {
             if (8 * u < ncol) tmem_ld8(baseW + (uint32_t)(c + 8 * u), vw + 8 * u);
         }
         tmem_wait_ld();
-        // the bulk stores of the previous group have read the staging rows
-        if (lane < 8) bulk_wait_read();
-        named_sync(1 + half, 128);
-        const int o0 = (int)((((long long)(c0 + c)) * np + p0) & 3), ostep = (int)(np & 3);
+        if (g.staged) {
+          // rows shifted to their 16-byte alignment in shared memory, then one bulk store of
+          // the aligned middle of each plane row and scalar stores at its two ends; first, the
+          // bulk stores of the previous group have read the staging rows
+          if (lane < 8) bulk_wait_read();
+          named_sync(1 + half, 128);
+          const int o0 = (int)((((long long)(c0 + c)) * np + p0) & 3), ostep = (int)(np & 3);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (j < ncol) {
-            float v = __uint_as_float(vt[j]) * uT;
-            if (has_w) v = fmaf(__uint_as_float(vw[j]), uW, v);
-            stage[j * STG_ROW + ((o0 + j * ostep) & 3) + m] = v;
+          for (int j = 0; j < 32; ++j) {
+            if (j < ncol) {
+              float v = __uint_as_float(vt[j]) * uT;
+              if (has_w) v = fmaf(__uint_as_float(vw[j]), uW, v);
+              stage[j * STG_ROW + ((o0 + j * ostep) & 3) + m] = v;
+            }
           }
-        }
-        fence_proxy_async();
-        named_sync(1 + half, 128);
-        const int j = 8 * q + lane;                // staging row written out by this lane
-        if (lane < 8 && j < ncol && c0 + c + j < n) {
-          const long long a = (long long)(c0 + c + j) * np + p0;
-          const int o = (int)(a & 3);
-          const long long as = a + ((4 - o) & 3), ae = (a + cnt) & ~3ll;
-          const float* row = stage + j * STG_ROW + o;
-          for (long long x = a; x < min(as, a + cnt); ++x) g.P[x] = row[x - a];
-          if (ae > as) bulk_store(g.P + as, row + (as - a), (uint32_t)((ae - as) * 4));
-          for (long long x = max(ae, as); x < a + cnt; ++x) g.P[x] = row[x - a];
-          bulk_commit();
+          fence_proxy_async();
+          named_sync(1 + half, 128);
+          const int j = 8 * q + lane;                // staging row written out by this lane
+          if (lane < 8 && j < ncol && c0 + c + j < n) {
+            const long long a = (long long)(c0 + c + j) * np + p0;
+            const int o = (int)(a & 3);
+            const long long as = a + ((4 - o) & 3), ae = (a + cnt) & ~3ll;
+            const float* row = stage + j * STG_ROW + o;
+            for (long long x = a; x < min(as, a + cnt); ++x) g.P[x] = row[x - a];
+            if (ae > as) bulk_store(g.P + as, row + (as - a), (uint32_t)((ae - as) * 4));
+            for (long long x = max(ae, as); x < a + cnt; ++x) g.P[x] = row[x - a];
+            bulk_commit();
+          }
+        } else if (m < cnt) {
+          // lane m writes point p0 + m of the rows i1 = c0 + c + j: one 128-byte run per warp
+          // and row (when the staging rows do not fit next to the operand rings)
+          float* out = g.P + (long long)(c0 + c) * np + p0 + m;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j < ncol && c0 + c + j < n) {
+              float v = __uint_as_float(vt[j]) * uT;
+              if (has_w) v = fmaf(__uint_as_float(vw[j]), uW, v);
+              __stcs(out + (long long)j * np, v);
+            }
+          }
         }
       }
       fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_d_empty[t & 1]);
     }
-    if (lane < 8) bulk_wait_all();
+    if (g.staged && lane < 8) bulk_wait_all();
   }
   fence_before_sync();
   __syncthreads();
@@ -981,9 +1000,9 @@ Layout layout_of(const Ctx& c) {
   return L;
 }
 
-size_t smem_total(const Layout& L, int na, int ns) {
+size_t smem_total(const Layout& L, int na, int ns, bool staged) {
   return 2 * L.bv_half + (size_t)na * 2 * L.a_half + (size_t)ns * 2 * SLOT_HALF + 2 * L.tbl_half + L.tab +
-         L.list + L.stage;
+         L.list + (staged ? L.stage : 0);
 }
 
 }  // namespace
@@ -1004,12 +1023,22 @@ bool plan_assemble(Ctx& c) {
   if (c.tc_nch > 32) return false;
   const Layout L = layout_of(c);
   const size_t limit = (size_t)(SMEM_LIMIT - SMEM_RESERVE);
+  // deepest operand rings that fit, with the staged epilogue (faster stores) unless dropping
+  // its staging rows buys a deeper ring (large ranks)
   const int choices[6][2] = {{2, 8}, {2, 6}, {2, 4}, {1, 4}, {1, 2}, {1, 1}};
-  c.tc_na = 0;
-  for (auto& ch : choices)
-    if (smem_total(L, ch[0], ch[1]) <= limit) { c.tc_na = ch[0]; c.tc_ns = ch[1]; break; }
-  if (c.tc_na == 0) return false;
-  c.tc_smem = smem_total(L, c.tc_na, c.tc_ns);
+  int best[2] = {-1, -1};
+  for (int staged = 1; staged >= 0; --staged)
+    for (int i = 0; i < 6; ++i)
+      if (smem_total(L, choices[i][0], choices[i][1], staged != 0) <= limit) {
+        best[staged] = i;
+        break;
+      }
+  if (best[0] < 0) return false;
+  c.tc_staged = best[1] >= 0 && best[1] <= best[0];
+  const int pick = c.tc_staged ? best[1] : best[0];
+  c.tc_na = choices[pick][0];
+  c.tc_ns = choices[pick][1];
+  c.tc_smem = smem_total(L, c.tc_na, c.tc_ns, c.tc_staged);
   // the T2 tile kernel stages 8 rank slices of T1 for 32 i3 plus 32 rows of V2
   if ((size_t)1152 * c.rmax > limit) return false;
   // window list entries: every particle reaches at most the tiles of 2 gamma + 1 rows of
@@ -1071,6 +1100,7 @@ int launch_assemble(Ctx& c, float* out) {
   g.off_tab = (uint32_t)(g.off_tbl + 2 * L.tbl_half);
   g.off_list = (uint32_t)(g.off_tab + L.tab);
   g.off_stage = (uint32_t)(g.off_list + L.list);
+  g.staged = c.tc_staged ? 1 : 0;
   g.bv_half = (uint32_t)L.bv_half;
   g.a_half = (uint32_t)L.a_half;
   g.tbl_half = (uint32_t)L.tbl_half;

@@ -240,6 +240,35 @@ def test_c2_full_size_sampled_against_canonical_sum():
     ctx.close()
 
 
+def test_c3_full_size_sampled_against_canonical_sum():
+    """Config 3 at full size (n = 1025, N = 19,757 lattice sites, eps = 1e-5, FP32 bulk; the
+    large Tucker rank leaves room for one T2 stage and four window slots, with the epilogue
+    storing from registers): the grid against the oracle's full-rank canonical sum on sampled
+    sites and points, and the energy against the grid at all sites (E = 1/2 sum_j z_j (P(x_j) -
+    z_j P_R(0)), Eq. (4.7), a property that holds at any size)."""
+    cfg = load_config("c3_nacl28_n1025")
+    p = make_particles(cfg)
+    pr = O.Problem(cfg, p.xyz, p.Z)
+    ctx = _solve(cfg, p.xyz, p.Z)
+    rep = ctx.report()
+    assert rep["status"] == 0
+    assert max(rep["tail_rel"]) <= cfg["eps"] ** 2 / 3 * 1.0001
+    P = ctx.potential
+    rng = np.random.default_rng(23)
+    idx = np.concatenate([pr.j[rng.choice(len(p.Z), 300, replace=False)], rng.integers(0, pr.n, (300, 3))])
+    it = torch.tensor(idx, device="cuda", dtype=torch.long)
+    g = P[it[:, 0], it[:, 1], it[:, 2]].double().cpu().numpy()
+    ref = pr.P0_points(idx)
+    err = _rel(g, ref)
+    assert err < cfg["eps"], err
+    js = torch.tensor(pr.j, device="cuda", dtype=torch.long)
+    at_sites = P[js[:, 0], js[:, 1], js[:, 2]].double().cpu().numpy()
+    E_grid = 0.5 * float(np.sum(pr.z * (at_sites - pr.z * rep["P_R0"])))
+    scale = float(np.abs(pr.z).sum() * np.abs(at_sites).max())
+    assert abs(ctx.energy() - E_grid) <= 1e-6 * scale
+    ctx.close()
+
+
 @pytest.mark.parametrize("name", ["c2_protein1000_n513"])
 def test_tensor_core_reconstruction_matches_cuda_core_path(name, monkeypatch):
     """The tcgen05 (3xTF32) assembly (Tucker product and windows in one kernel) against the
