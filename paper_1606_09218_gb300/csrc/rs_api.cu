@@ -62,6 +62,14 @@ bool derive(const rs_config& cfg, Ctx& c, std::string& err) {
   c.maxN = cfg.max_particles;
   c.t2_ld = cfg.n;
   c.use_tc = plan_assemble(c);
+  {
+    // core contraction: tensor cores where the tolerance allows their FP32 accumulation
+    // (eps >= 1e-5), the CUDA-core two-sum contraction below; RS_CORE_PATH=cuda|tc overrides
+    const char* env = std::getenv("RS_CORE_PATH");
+    c.use_tc_core = !c.fp64 && cfg.eps >= 1e-5;
+    if (env && std::strcmp(env, "cuda") == 0) c.use_tc_core = false;
+    if (env && std::strcmp(env, "tc") == 0) c.use_tc_core = !c.fp64;
+  }
   return true;
 }
 
@@ -103,6 +111,7 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.Z64, 8 * 3 * n * rm);
   add(v, c.Z32, 4 * 3 * n * rm);
   add(v, c.Qp, ts * 3 * n * Rl * rm);
+  if (c.use_tc_core) add(v, c.kmeta, 16 * (size_t)N * Rl);
   add(v, c.beta64, 8 * rm * rm * rm);
   add(v, c.beta, ts * rm * rm * rm);
   add(v, c.T1, ts * rm * rm * n);
@@ -220,6 +229,7 @@ bool ensure_kernel_attributes(std::string& err) {
   if (e == cudaSuccess) e = set_attributes_eigen(optin);
   if (e == cudaSuccess) e = set_attributes_tucker(optin);
   if (e == cudaSuccess) e = set_attributes_tc(optin);
+  if (e == cudaSuccess) e = set_attributes_core(optin);
   if (e != cudaSuccess) {
     err = std::string("kernel attributes: ") + cudaGetErrorString(e);
     cudaGetLastError();

@@ -54,6 +54,7 @@ struct DevScalars {
   int fallbacks;                 // blocks that took the one-CTA Gram-Schmidt fallback
   int chunk_w[32];               // windows per i1 chunk (tensor-core assembly schedule)
   unsigned zmax_bits;            // max |z| over the particles (float bits; window operand scale)
+  unsigned qmax_bits;            // max |Qp| of the FP32 projections (float bits; core operand scale)
   double beta_a2[RMAX_LIMIT];    // ||beta[a, :, :]||^2 (scale of the FP16 Tucker operands)
   // barriers of the cooperative Gram-Schmidt kernel, one per mode: arrival counter and
   // generation of mode l at [32 l], each on its own 128-byte line, so that the waiters' polling
@@ -128,6 +129,8 @@ struct Ctx {
   int tc_grid = 0;
   size_t tc_smem = 0;           // dynamic shared memory of the assembly kernel
   bool tc_staged = false;       // assembly epilogue through shared staging rows
+  bool use_tc_core = false;     // tensor-core core contraction (FP32 bulk path)
+  void*   kmeta = nullptr;      // per K term of the core: Qp row offsets and charge (int4)
   long long wl_cap = 0;         // capacity of the window lists (entries)
   int*       wl_count = nullptr;   // ntiles + 1
   int*       wl_start = nullptr;   // ntiles + 1
@@ -201,6 +204,8 @@ inline cudaError_t allow_max_dynamic_smem(const void* f, int optin) {
 cudaError_t set_attributes_eigen(int optin);
 cudaError_t set_attributes_tucker(int optin);
 cudaError_t set_attributes_tc(int optin);
+cudaError_t set_attributes_core(int optin);
+int launch_core_tc(Ctx& c);
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out);
 
 // generic batched GEMM on row-major matrices:

@@ -22,7 +22,7 @@ template <> struct Bulk<double> { static const double* pk(const Ctx& c) { return
 template <typename T>
 __global__ void __launch_bounds__(256)
 proj_kernel(const T* __restrict__ Zb, const T* __restrict__ pk, const int* __restrict__ nzj, int n,
-            int rmax, int R_l, const DevScalars* sc, T* Qp) {
+            int rmax, int R_l, DevScalars* sc, T* Qp) {
   extern __shared__ __align__(16) unsigned char psm[];
   T* sp = (T*)psm;                                   // p_k[d], d = -(n-1) .. n-1
   T* sV = sp + ((2 * n - 1 + 3) & ~3);               // [32][64] slice of Z_l
@@ -70,6 +70,7 @@ proj_kernel(const T* __restrict__ Zb, const T* __restrict__ pk, const int* __res
       }
     }
   }
+  float qm = 0.f;
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
     if (jj[x] < 0) continue;
@@ -77,8 +78,12 @@ proj_kernel(const T* __restrict__ Zb, const T* __restrict__ pk, const int* __res
     for (int y = 0; y < 4; ++y) {
       const int a = a0 + 4 * ta + y;
       if (a < rmax) Qp[(((long long)l * n + jj[x]) * R_l + k) * rmax + a] = (a < r) ? acc[x][y] : T(0);
+      if (a < r) qm = fmaxf(qm, fabsf((float)acc[x][y]));
     }
   }
+  // largest |Qp| (operand scale of the tensor-core core contraction)
+  for (int o = 16; o > 0; o >>= 1) qm = fmaxf(qm, __shfl_xor_sync(0xffffffffu, qm, o));
+  if ((threadIdx.x & 31) == 0 && qm > 0.f) atomicMax(&sc->qmax_bits, __float_as_uint(qm));
 }
 
 // ------------------------------------------------------------------ core
@@ -278,8 +283,12 @@ static int projection_core_t(Ctx& c) {
   const int kmin_split = (int)((kmax + CORE_KMAX - 1) / CORE_KMAX);
   if (ksplit < kmin_split) ksplit = kmin_split;
   dim3 g2(ntile, ksplit);
-  core_kernel<T><<<g2, 256, core_smem_bytes<T>(), c.stream>>>(Qp, c.j, c.nz_idx, c.Z, n, rmax, c.R_l, c.sc,
-                                                               c.beta64);
+  int kcore = 1;
+  if (sizeof(T) == 4 && c.use_tc_core)
+    kcore = launch_core_tc(c);                       // tcgen05, FP16-split operands
+  else
+    core_kernel<T><<<g2, 256, core_smem_bytes<T>(), c.stream>>>(Qp, c.j, c.nz_idx, c.Z, n, rmax, c.R_l, c.sc,
+                                                                 c.beta64);
   convert_beta_kernel<T><<<rmax, 256, 0, c.stream>>>(c.beta64, (T*)c.beta, rmax, c.sc);
   // T1[a][b][i3] = sum_c beta[a][b][c] V3[i3][c]      (rows (a,b), K = r3)
   const T* Zb = Bulk<T>::Z(c);
@@ -287,12 +296,12 @@ static int projection_core_t(Ctx& c) {
   gemm_batched<T>(c.stream, false, true, rmax * rmax, n, rmax, T(1), (const T*)c.beta, rmax, 0,
                   Zb + 2 * sZ, rmax, 0, T(0), (T*)c.T1, n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 2);
   // T2[a][i2][i3] = sum_b V2[i2][b] T1[a][b][i3]        (batch a < r1, K = r2)
-  if (c.use_tc && !c.fp64) return 4 + launch_t2_tiles(c);   // tiled FP16 operands
+  if (c.use_tc && !c.fp64) return 3 + kcore + launch_t2_tiles(c);   // tiled FP16 operands
   batch_dims_kernel<<<(rmax + 127) / 128, 128, 0, c.stream>>>(c.adims, c.kdims, rmax, n, c.sc);
   gemm_batched<T>(c.stream, false, false, n, n, rmax, T(1), Zb + sZ, rmax, 0, (const T*)c.T1, n,
                   (long long)rmax * n, T(0), (T*)c.T2, c.t2_ld, (long long)n * c.t2_ld, rmax, 1,
                   c.adims, nullptr, c.kdims);
-  return 6;
+  return 5 + kcore;
 }
 
 int launch_projection_core(Ctx& c) {

@@ -305,6 +305,37 @@ def test_tensor_core_reconstruction_matches_cuda_core_path(name, monkeypatch):
     ctx.close()
 
 
+def test_tensor_core_core_matches_cuda_core_path(monkeypatch):
+    """The tcgen05 core contraction (FP16-split operands, 64-term FP32 segments folded into
+    two-sums, FP64 across units; chosen by default for eps >= 1e-5) forced on config 2 against
+    the CUDA-core FP32 contraction with two-sum chunks (the default at eps = 1e-6): the same
+    Tucker ranks, and potentials within 1e-6 (the tensor cores' FP32 accumulation costs about
+    4e-7 here)."""
+    cfg = load_config("c2_protein1000_n513")
+    p = make_particles(cfg)
+    xyz = torch.tensor(p.xyz, device="cuda")
+    Z = torch.tensor(p.Z, device="cuda")
+    monkeypatch.setenv("RS_CORE_PATH", "cuda")
+    cref = _ctx(cfg, len(p.Z))
+    cref.solve(xyz, Z, energy=True)
+    ref = cref.potential.clone()
+    Eref = cref.energy()
+    rref = cref.report()
+    cref.close()
+    monkeypatch.setenv("RS_CORE_PATH", "tc")
+    ctx = _ctx(cfg, len(p.Z))
+    ctx.solve(xyz, Z, energy=True)
+    rep = ctx.report()
+    assert rep["status"] == 0 and rep["ranks"] == rref["ranks"]
+    assert rep["kernel_launches"] == rref["kernel_launches"] + 1       # + the K-term table
+    d = float((ctx.potential.double() - ref.double()).norm() / ref.double().norm())
+    assert d < 1e-6, d
+    pr = O.Problem(cfg, p.xyz, p.Z)
+    scale = O.energy_scale(pr.xyz_snapped, pr.z)
+    assert abs(ctx.energy() - Eref) <= 3e-7 * scale
+    ctx.close()
+
+
 # ---------------------------------------------------------------- adjoint forces (Sec. 4.3)
 def _forces_tol(cfg, rounding):
     """Both the GPU and the oracle RS-Tucker forces are within O(eps) of the untruncated forces
