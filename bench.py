@@ -349,6 +349,32 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_launch": per_launch_ms, "algorithmic_bytes": bytes_alg,
             "bytes_formula": "4*n^3 (output) + 4*r1*n^2 (T2 slab)"}
 
+    # plain-method GPU paths on the same particles and grid: direct sum and full-rank
+    # canonical sum (one timed run each after a warm-up), with the RS grid's relative
+    # difference from the canonical sum over the whole grid
+    plain_methods = None
+    if rank == 0 and not args.no_plain:
+        plain_methods = {}
+        ctx.solve(xyz, Z, potential=pot, energy=True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        outp = torch.empty((n,) * 3, dtype=torch.float32, device="cuda")
+        for name, fn, flops in (("direct_sum", ctx.plain_direct, "n^3 N pair terms"),
+                                ("canonical_sum", ctx.plain_canonical, "2 n^3 N R")):
+            fn(outp)
+            torch.cuda.synchronize()
+            flush.zero_()
+            a.record(stream)
+            fn(outp)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            entry = {"ms_per_step": ms, "value": n ** 3 / (ms * 1e-3), "unit": UNIT, "work": flops}
+            if name == "canonical_sum":
+                entry["rs_rel_diff_full_grid"] = float((pot.double() - outp.double()).norm() / outp.double().norm())
+            plain_methods[name] = entry
+        del outp
+
     serving = None
     if not args.no_serving:
         serving = serving_report()
@@ -377,6 +403,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "stages_ms_per_step": {k: v / max(nsolves, 1) for k, v in stages.items()},
         "plain_gpu": plain,
+        "plain_methods": plain_methods,
         "serving": serving,
         "energy": E,
     }

@@ -234,6 +234,23 @@ rs_status rs_server_info(rs_server* srv, int* slots, size_t* bytes_in_use, int* 
 /* Finish queued and running requests, free every slot and stop the worker.  Safe on NULL. */
 void rs_server_destroy(rs_server* srv);
 
+/* ---------------------------------------------------------------- plain-method GPU paths
+ * The potential of the last solve's particles (snapped centres x_nu = -b + j_nu h, charges
+ * Z_nu) on the same grid without the RS format: the comparisons of the RS path on one GPU.
+ *   rs_plain_direct:    P[i] = sum_nu Z_nu / |x_i - x_nu| (Sec. 1, Eq. (1.1)); terms with
+ *                       x_i = x_nu are skipped.  n^3 N pair terms; n <= 640.
+ *   rs_plain_canonical: the full-rank canonical sum P_0[i] = sum_nu Z_nu sum_{k<R}
+ *                       p_k[i1-j1] p_k[i2-j2] p_k[i3-j3] with the context's Galerkin factors
+ *                       (Eqs. (2.5), (3.4); no split, no truncation).  2 n^3 N R operations;
+ *                       n <= 1280 and R (2n-1) factors within one CTA's shared memory.
+ * out: caller-owned device buffer of n^3 float32 (C order, i3 fastest).  Products and square
+ * roots in FP32, each output's sum compensated (two-sum of 32-term chunks).  Asynchronous on the
+ * context stream.  Errors: RS_ERR_NOT_READY without a solve, RS_ERR_INVALID_ARG for a null or
+ * misaligned out, RS_ERR_CAPACITY for a grid beyond the limits above.  The paper has no GPU
+ * counterpart; these are the plain methods its RS format is measured against. */
+rs_status rs_plain_direct(rs_ctx* ctx, float* out);
+rs_status rs_plain_canonical(rs_ctx* ctx, float* out);
+
 /* Text of the last error of this context (or of rs_create when ctx is NULL). */
 const char* rs_last_error(rs_ctx* ctx);
 

@@ -143,6 +143,24 @@ class RSContext:
         _lib.check(self.lib.rs_forces(self.h, C.c_void_p(F.data_ptr()), 0), self.h)
         return F
 
+    def plain_direct(self, out=None):
+        """Direct sum sum_nu Z_nu / |x - x_nu| of the last solve's particles on the grid
+        (plain-method GPU path, no RS format); returns the (n, n, n) float32 CUDA tensor."""
+        return self._plain(self.lib.rs_plain_direct, out)
+
+    def plain_canonical(self, out=None):
+        """Full-rank canonical sum P_0 of the last solve's particles on the grid (plain-method
+        GPU path: all R terms, no split, no truncation); (n, n, n) float32 CUDA tensor."""
+        return self._plain(self.lib.rs_plain_canonical, out)
+
+    def _plain(self, fn, out):
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.n,) * 3, dtype=torch.float32, device="cuda")
+        assert out.dtype == torch.float32 and out.is_cuda and out.numel() == self.n ** 3
+        _lib.check(fn(self.h, C.c_void_p(out.data_ptr())), self.h)
+        return out
+
     def report(self) -> dict:
         s = _lib.RSStatsC()
         st = self.lib.rs_report(self.h, C.byref(s))

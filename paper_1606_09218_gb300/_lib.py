@@ -35,7 +35,7 @@ RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_FORCES, RS_VALIDATE_SEPARATION = 1, 2
 #: every symbol ``include/rs.h`` declares
 EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_energy", "rs_forces", "rs_report",
             "rs_get_tucker", "rs_eval_points", "rs_profile_enable", "rs_profile_read", "rs_stage_name",
-            "rs_debug_buffer", "rs_gram_noalloc",
+            "rs_debug_buffer", "rs_gram_noalloc", "rs_plain_direct", "rs_plain_canonical",
             "rs_server_create", "rs_submit", "rs_wait", "rs_server_info", "rs_server_destroy",
             "rs_last_error", "rs_version"]
 RS_NSTAGE = 9
@@ -96,6 +96,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.rs_energy.restype = C.c_int
     lib.rs_forces.argtypes = [vp, vp, C.c_int]
     lib.rs_forces.restype = C.c_int
+    for nm in ("rs_plain_direct", "rs_plain_canonical"):
+        getattr(lib, nm).argtypes = [vp, vp]
+        getattr(lib, nm).restype = C.c_int
     lib.rs_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
     lib.rs_server_create.restype = C.c_int
     lib.rs_submit.argtypes = [vp, C.POINTER(RSRequestC), C.POINTER(C.c_ulonglong)]

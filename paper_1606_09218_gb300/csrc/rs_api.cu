@@ -230,6 +230,7 @@ bool ensure_kernel_attributes(std::string& err) {
   if (e == cudaSuccess) e = set_attributes_tucker(optin);
   if (e == cudaSuccess) e = set_attributes_tc(optin);
   if (e == cudaSuccess) e = set_attributes_core(optin);
+  if (e == cudaSuccess) e = set_attributes_plain(optin);
   if (e != cudaSuccess) {
     err = std::string("kernel attributes: ") + cudaGetErrorString(e);
     cudaGetLastError();
@@ -557,6 +558,19 @@ const char* rs_stage_name(int stage) {
                                       "bins", "reconstruct", "windows", "energy"};
   return (stage >= 0 && stage < NSTAGE) ? names[stage] : nullptr;
 }
+
+static rs_status plain_entry(rs_ctx* h, float* out, int which) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.solved) return fail(c, RS_ERR_NOT_READY, "no solve");
+  if (!out || ((uintptr_t)out & 3u)) return fail(c, RS_ERR_INVALID_ARG, "out must be a 4-byte aligned device buffer");
+  const rs_status st = launch_plain(c, which, out);
+  if (st != RS_OK) return fail(c, st, "grid too large for this plain-method kernel");
+  return check_launch(c, which == 0 ? "plain_direct" : "plain_canonical");
+}
+
+rs_status rs_plain_direct(rs_ctx* h, float* out) { return plain_entry(h, out, 0); }
+rs_status rs_plain_canonical(rs_ctx* h, float* out) { return plain_entry(h, out, 1); }
 
 const char* rs_last_error(rs_ctx* h) {
   if (!h) return g_create_err.c_str();

@@ -206,6 +206,8 @@ cudaError_t set_attributes_tucker(int optin);
 cudaError_t set_attributes_tc(int optin);
 cudaError_t set_attributes_core(int optin);
 int launch_core_tc(Ctx& c);
+cudaError_t set_attributes_plain(int optin);
+rs_status launch_plain(Ctx& c, int which, float* out);
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out);
 
 // generic batched GEMM on row-major matrices:

@@ -336,6 +336,33 @@ def test_tensor_core_core_matches_cuda_core_path(monkeypatch):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
+def test_plain_method_paths_match_oracle(prec):
+    """The plain-method GPU paths on the last solve's particles: the direct sum Z / r against
+    the oracle's direct analytic sum (terms at r = 0 skipped) and the full-rank canonical sum
+    against the oracle's P_0, both on the whole grid (FP32 products, compensated sums)."""
+    rng = np.random.default_rng(31)
+    cfg = dict(b=4.0, n=33, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8,
+               precision=prec, snap=True)
+    N = 12
+    xyz = rng.uniform(-3.0, 3.0, (N, 3))
+    Z = rng.uniform(-1, 1, N)
+    Z[5] = 0.0
+    pr = O.Problem(cfg, xyz, Z)
+    ctx = _solve(cfg, xyz, Z)
+    D = ctx.plain_direct().double().cpu().numpy().ravel()
+    C0 = ctx.plain_canonical().double().cpu().numpy().ravel()
+    n = cfg["n"]
+    idx = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), -1).reshape(-1, 3)
+    Dref = O.direct_sum_points(pr.xyz_snapped, pr.z, pr.x[idx])
+    Cref = pr.P0_grid().ravel()
+    assert _rel(D, Dref) < 1e-6
+    assert np.abs(D - Dref).max() <= 2e-6 * np.abs(Dref).max()
+    assert _rel(C0, Cref) < 1e-6
+    assert np.abs(C0 - Cref).max() <= 2e-6 * np.abs(Cref).max()
+    ctx.close()
+
+
 # ---------------------------------------------------------------- adjoint forces (Sec. 4.3)
 def _forces_tol(cfg, rounding):
     """Both the GPU and the oracle RS-Tucker forces are within O(eps) of the untruncated forces
