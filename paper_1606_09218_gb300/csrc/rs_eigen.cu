@@ -715,10 +715,15 @@ jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* s
         qq[m] = q;
         float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
         float c = 1.f, s = 0.f, t = 0.f;
-        if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq))) {
-          float theta = (aqq - app) / (2.f * apq);
-          t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
-          c = rsqrtf(1.f + t * t);
+        // this phase runs on one warp while the others wait: fast division and reciprocal
+        // square root (about 2 ulp) instead of IEEE division and square root; the
+        // rotation stays orthogonal (c = 1/sqrt(1 + t^2), s = t c) and the diagonal update below
+        // uses the t that is applied
+        if (apq != 0.f && apq * apq > tol * tol * fabsf(app * aqq)) {
+          const float theta = __fdividef(aqq - app, 2.f * apq);
+          const float w = fmaf(theta, theta, 1.f);
+          t = copysignf(__fdividef(1.f, fabsf(theta) + w * rsqrtf(w)), theta);
+          c = rsqrtf(fmaf(t, t, 1.f));
           s = t * c;
           s_rot = 1;
         }
