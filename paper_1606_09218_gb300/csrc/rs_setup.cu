@@ -208,7 +208,7 @@ gram_kernel(const double* __restrict__ F, const double* __restrict__ C, const in
             const DevScalars* sc, int n, double* G) {
   const int l = blockIdx.y;
   const int nt = (n + 31) / 32;
-  // map blockIdx.x -> (ti <= tj)
+  // map blockIdx.x -> (ti <= tj); blockIdx.z takes half of the charged coordinates
   int t = blockIdx.x, ti = 0;
   while (t >= nt - ti) { t -= nt - ti; ++ti; }
   const int tj = ti + t;
@@ -218,11 +218,14 @@ gram_kernel(const double* __restrict__ F, const double* __restrict__ C, const in
   __shared__ double sw[256];
   __shared__ int sj[256];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const int cnt = sc->nzj_count[l];
+  const int cnt_all = sc->nzj_count[l];
+  const int split = gridDim.z;                 // 1: whole sum stored; 2: halves added
+  const int mh = (cnt_all + split - 1) / split;
+  const int mbeg = min(cnt_all, (int)blockIdx.z * mh), cnt = min(cnt_all, mbeg + mh);
   const double* Cl = C + l * n;
   const int* nl = nzj + l * n;
   const int ip = J0 + tx;
-  for (int m0 = 0; m0 < cnt; m0 += 256) {
+  for (int m0 = mbeg; m0 < cnt; m0 += 256) {
     int m = m0 + threadIdx.x;
     if (m < cnt) {
       int jv = nl[m];
@@ -243,13 +246,19 @@ gram_kernel(const double* __restrict__ F, const double* __restrict__ C, const in
     }
     __syncthreads();
   }
+  // with two halves, both add into the zeroed G: 0 + a + b in either order is the same sum
   double* Gl = G + (long long)l * n * n;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     int i = I0 + ty + 8 * r;
     if (i < n && ip < n) {
-      Gl[(long long)i * n + ip] = acc[r];
-      if (ti != tj) Gl[(long long)ip * n + i] = acc[r];
+      if (split == 1) {
+        Gl[(long long)i * n + ip] = acc[r];
+        if (ti != tj) Gl[(long long)ip * n + i] = acc[r];
+      } else {
+        atomicAdd(&Gl[(long long)i * n + ip], acc[r]);
+        if (ti != tj) atomicAdd(&Gl[(long long)ip * n + i], acc[r]);
+      }
     }
   }
 }
@@ -257,7 +266,8 @@ gram_kernel(const double* __restrict__ F, const double* __restrict__ C, const in
 int launch_gram(Ctx& c) {
   launch_fmatrix(c);
   int nt = (c.n + 31) / 32;
-  dim3 grid(nt * (nt + 1) / 2, 3);
+  dim3 grid(nt * (nt + 1) / 2, 3, 2);
+  cudaMemsetAsync(c.G, 0, sizeof(double) * 3 * (size_t)c.n * c.n, c.stream);
   gram_kernel<<<grid, 256, 0, c.stream>>>(c.F, c.C, c.nzj, c.sc, c.n, c.G);
   return 2;
 }
