@@ -173,6 +173,7 @@ def run_reference(args, rank, world):
 
 
 SERVING_WORKLOAD = "c4_serving256"
+FORCES_WORKLOAD = "c5_forces4096_n513"
 
 
 def serving_report(max_slots: int = 8, hbm_budget: int = 16 << 30):
@@ -375,6 +376,30 @@ def run_ours(args, rank, world, local_rank):
             plain_methods[name] = entry
         del outp
 
+    # energy and forces at centres off the grid (forces workload, N = 4096): the RS kernel in
+    # pair form, one timed call after a warm-up
+    forces = None
+    if rank == 0 and not args.no_plain:
+        fcfg = load_config(FORCES_WORKLOAD)
+        fp = make_particles(fcfg)
+        fN = int(len(fp.Z))
+        fctx = RSContext(config_from_workload(dict(fcfg, snap=True), max_particles=fN))
+        fx = torch.tensor(fp.xyz, device="cuda")
+        fz = torch.tensor(fp.Z, device="cuda")
+        fctx.pair_energy_forces(fx, fz)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(torch.cuda.current_stream())
+        fE, _ = fctx.pair_energy_forces(fx, fz)
+        b.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        fms = a.elapsed_time(b)
+        forces = {"workload": FORCES_WORKLOAD, "N": fN, "ms": fms, "pairs_per_s": fN * (fN - 1) / (fms * 1e-3),
+                  "energy": fE, "path": "rs_pair_energy_forces: RS kernel in pair form at unsnapped centres, "
+                                        "FP32 factors, FP64 sums (energy and adjoint forces, one call)"}
+        fctx.close()
+
     serving = None
     if not args.no_serving:
         serving = serving_report()
@@ -404,6 +429,7 @@ def run_ours(args, rank, world, local_rank):
         "stages_ms_per_step": {k: v / max(nsolves, 1) for k, v in stages.items()},
         "plain_gpu": plain,
         "plain_methods": plain_methods,
+        "forces": forces,
         "serving": serving,
         "energy": E,
     }

@@ -251,6 +251,18 @@ void rs_server_destroy(rs_server* srv);
 rs_status rs_plain_direct(rs_ctx* ctx, float* out);
 rs_status rs_plain_canonical(rs_ctx* ctx, float* out);
 
+/* Energy and forces of N centres anywhere in the box (not snapped) with the RS kernel of the
+ * context in pair form: E = 1/2 sum_{j != nu} Z_j Z_nu K_h(x_j - x_nu), K_h(r) =
+ * sum_{k<R} p_k(r1) p_k(r2) p_k(r3) with the Galerkin factors p_k continued to any offset (cell
+ * averages of a_k^{1/3} exp(-t_k^2 x^2), Eq. (2.10); on grid offsets the kernel of the RS grid
+ * tensor), and F_j = -dE/dx_j (Secs. 4.2, 4.3; no factor 1/2).  All pairs and all R terms, so E
+ * is smooth in the centres and F is its exact gradient.  xyz (N x 3), Z (N): device float64;
+ * E: device pointer to one float64; F: device N x 3 float64, or NULL for the energy alone.
+ * Factors in FP32, sums in FP64.  Asynchronous on the context stream; needs no prior solve.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_CAPACITY for N > max_particles.  The paper evaluates
+ * off-grid energies through the RS tensor; this is the reading used for centres off the grid. */
+rs_status rs_pair_energy_forces(rs_ctx* ctx, int N, const double* xyz, const double* Z, double* E, double* F);
+
 /* Text of the last error of this context (or of rs_create when ctx is NULL). */
 const char* rs_last_error(rs_ctx* ctx);
 

@@ -143,6 +143,22 @@ class RSContext:
         _lib.check(self.lib.rs_forces(self.h, C.c_void_p(F.data_ptr()), 0), self.h)
         return F
 
+    def pair_energy_forces(self, xyz, Z, forces: bool = True):
+        """Energy (and forces) of centres anywhere in the box with the RS kernel in pair form
+        (rs_pair_energy_forces); xyz (N, 3) and Z (N,) float64 CUDA tensors.  Returns
+        (E, F) with F an (N, 3) float64 CUDA tensor or None."""
+        torch = self._torch
+        xyz = xyz.contiguous()
+        Z = Z.contiguous()
+        assert xyz.is_cuda and Z.is_cuda and xyz.dtype == torch.float64 and Z.dtype == torch.float64
+        N = int(Z.numel())
+        E = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F = torch.empty((N, 3), dtype=torch.float64, device="cuda") if forces else None
+        _lib.check(self.lib.rs_pair_energy_forces(self.h, N, C.c_void_p(xyz.data_ptr()), C.c_void_p(Z.data_ptr()),
+                                                  C.c_void_p(E.data_ptr()),
+                                                  C.c_void_p(F.data_ptr()) if F is not None else None), self.h)
+        return float(E.item()), F
+
     def plain_direct(self, out=None):
         """Direct sum sum_nu Z_nu / |x - x_nu| of the last solve's particles on the grid
         (plain-method GPU path, no RS format); returns the (n, n, n) float32 CUDA tensor."""

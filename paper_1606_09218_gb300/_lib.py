@@ -36,6 +36,7 @@ RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_FORCES, RS_VALIDATE_SEPARATION = 1, 2
 EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_energy", "rs_forces", "rs_report",
             "rs_get_tucker", "rs_eval_points", "rs_profile_enable", "rs_profile_read", "rs_stage_name",
             "rs_debug_buffer", "rs_gram_noalloc", "rs_plain_direct", "rs_plain_canonical",
+            "rs_pair_energy_forces",
             "rs_server_create", "rs_submit", "rs_wait", "rs_server_info", "rs_server_destroy",
             "rs_last_error", "rs_version"]
 RS_NSTAGE = 9
@@ -96,6 +97,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.rs_energy.restype = C.c_int
     lib.rs_forces.argtypes = [vp, vp, C.c_int]
     lib.rs_forces.restype = C.c_int
+    lib.rs_pair_energy_forces.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    lib.rs_pair_energy_forces.restype = C.c_int
     for nm in ("rs_plain_direct", "rs_plain_canonical"):
         getattr(lib, nm).argtypes = [vp, vp]
         getattr(lib, nm).restype = C.c_int

@@ -112,6 +112,7 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.Z32, 4 * 3 * n * rm);
   add(v, c.Qp, ts * 3 * n * Rl * rm);
   if (c.use_tc_core) add(v, c.kmeta, 16 * (size_t)N * Rl);
+  add(v, c.pe, 8 * (size_t)N);
   add(v, c.beta64, 8 * rm * rm * rm);
   add(v, c.beta, ts * rm * rm * rm);
   add(v, c.T1, ts * rm * rm * n);
@@ -567,6 +568,16 @@ static rs_status plain_entry(rs_ctx* h, float* out, int which) {
   const rs_status st = launch_plain(c, which, out);
   if (st != RS_OK) return fail(c, st, "grid too large for this plain-method kernel");
   return check_launch(c, which == 0 ? "plain_direct" : "plain_canonical");
+}
+
+rs_status rs_pair_energy_forces(rs_ctx* h, int N, const double* xyz, const double* Z, double* E, double* F) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (N < 0 || !E || (N > 0 && (!xyz || !Z))) return fail(c, RS_ERR_INVALID_ARG, "bad pair energy arguments");
+  if (N > c.maxN) return fail(c, RS_ERR_CAPACITY, "N above max_particles of this context");
+  const rs_status st = launch_pair_energy_forces(c, N, xyz, Z, E, F);
+  if (st != RS_OK) return fail(c, st, "more quadrature terms than the pair kernel supports");
+  return check_launch(c, "pair_energy_forces");
 }
 
 rs_status rs_plain_direct(rs_ctx* h, float* out) { return plain_entry(h, out, 0); }

@@ -131,6 +131,7 @@ struct Ctx {
   bool tc_staged = false;       // assembly epilogue through shared staging rows
   bool use_tc_core = false;     // tensor-core core contraction (FP32 bulk path)
   void*   kmeta = nullptr;      // per K term of the core: Qp row offsets and charge (int4)
+  double* pe = nullptr;         // per-particle pair energies (off-grid energy and forces)
   long long wl_cap = 0;         // capacity of the window lists (entries)
   int*       wl_count = nullptr;   // ntiles + 1
   int*       wl_start = nullptr;   // ntiles + 1
@@ -208,6 +209,7 @@ cudaError_t set_attributes_core(int optin);
 int launch_core_tc(Ctx& c);
 cudaError_t set_attributes_plain(int optin);
 rs_status launch_plain(Ctx& c, int which, float* out);
+rs_status launch_pair_energy_forces(Ctx& c, int N, const double* xyz, const double* Z, double* E, double* F);
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out);
 
 // generic batched GEMM on row-major matrices:
