@@ -154,6 +154,11 @@ void free_all(Ctx& c) {
   }
   if (c.h_sc) cudaFreeHost(c.h_sc);
   c.h_sc = nullptr;
+  if (c.ev_part) cudaEventDestroy(c.ev_part);
+  if (c.ev_bins) cudaEventDestroy(c.ev_bins);
+  if (c.aux) cudaStreamDestroy(c.aux);
+  c.ev_part = c.ev_bins = nullptr;
+  c.aux = nullptr;
 }
 
 rs_status fail(Ctx& c, rs_status s, const std::string& msg) {
@@ -284,6 +289,15 @@ rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
     return RS_ERR_OOM;
   }
   std::memset(c.h_sc, 0, sizeof(DevScalars));
+  if (cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.ev_part, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.ev_bins, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = "stream or event creation failed";
+    free_all(c);
+    delete h;
+    return RS_ERR_CUDA;
+  }
   cudaMemsetAsync(c.sc, 0, sizeof(DevScalars), c.stream);
   // sparse sign embedding Omega (n x ksub, ZETA entries per row), stored by column
   {
@@ -370,13 +384,21 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   mark(1);
   k += launch_prepare_particles(c, N, min_sep, (flags & RS_VALIDATE_SEPARATION) != 0);
   mark(2);
+  // particle bins and window lists need only the particles and gamma: on the context's second
+  // stream, overlapped with the Gram and eigen stages (which leave most SMs idle)
+  cudaEventRecord(c.ev_part, s);
+  cudaStreamWaitEvent(c.aux, c.ev_part, 0);
+  c.stream = c.aux;
+  k += launch_bins(c);                     // window lists
+  c.stream = s;
+  cudaEventRecord(c.ev_bins, c.aux);
   k += launch_gram(c);                     // a3, a4: Gram matrices of the long-range side matrices
   mark(3);
   k += launch_subspace(c);                 // a4: dominant subspaces, ranks
   mark(4);
   k += launch_projection_core(c);          // a5: projection and core
   mark(5);
-  k += launch_bins(c);                     // window lists
+  cudaStreamWaitEvent(s, c.ev_bins, 0);    // window lists ready
   mark(6);
   rs_status st = check_launch(c, "solve");
   if (st != RS_OK) return st;
