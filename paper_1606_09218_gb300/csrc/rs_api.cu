@@ -156,8 +156,9 @@ void free_all(Ctx& c) {
   c.h_sc = nullptr;
   if (c.ev_part) cudaEventDestroy(c.ev_part);
   if (c.ev_bins) cudaEventDestroy(c.ev_bins);
+  if (c.ev_side) cudaEventDestroy(c.ev_side);
   if (c.aux) cudaStreamDestroy(c.aux);
-  c.ev_part = c.ev_bins = nullptr;
+  c.ev_part = c.ev_bins = c.ev_side = nullptr;
   c.aux = nullptr;
 }
 
@@ -291,7 +292,8 @@ rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
   std::memset(c.h_sc, 0, sizeof(DevScalars));
   if (cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c.ev_part, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c.ev_bins, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c.ev_bins, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.ev_side, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     g_create_err = "stream or event creation failed";
     free_all(c);
@@ -390,14 +392,18 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   cudaStreamWaitEvent(c.aux, c.ev_part, 0);
   c.stream = c.aux;
   k += launch_bins(c);                     // window lists
-  c.stream = s;
   cudaEventRecord(c.ev_bins, c.aux);
+  if (flags & RS_FORCES) k += launch_forces(c);                          // a9 (particles and bins only)
+  c.stream = s;
   k += launch_gram(c);                     // a3, a4: Gram matrices of the long-range side matrices
   mark(3);
   k += launch_subspace(c);                 // a4: dominant subspaces, ranks
   mark(4);
   k += launch_projection_core(c);          // a5: projection and core
   mark(5);
+  // (the energy stays on this stream after the assembly: beside it, its blocks delay the
+  // persistent assembly CTAs more than they save)
+  cudaEventRecord(c.ev_side, c.aux);
   cudaStreamWaitEvent(s, c.ev_bins, 0);    // window lists ready
   mark(6);
   rs_status st = check_launch(c, "solve");
@@ -407,7 +413,7 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   if (flags & RS_POTENTIAL) k += launch_windows(c, potential_out);      // a6
   mark(8);
   if (flags & RS_ENERGY) k += launch_energy(c, N);                      // a8
-  if (flags & RS_FORCES) k += launch_forces(c);                          // a9
+  cudaStreamWaitEvent(s, c.ev_side, 0);    // forces (second stream) done
   mark(9);
   st = check_launch(c, "solve");
   if (st != RS_OK) return st;

@@ -67,7 +67,7 @@ struct Ctx {
   rs_config cfg;
   cudaStream_t stream = nullptr;
   cudaStream_t aux = nullptr;    // window lists and particle bins, overlapped with the eigen stage
-  cudaEvent_t ev_part = nullptr, ev_bins = nullptr;
+  cudaEvent_t ev_part = nullptr, ev_bins = nullptr, ev_side = nullptr;
   int n = 0, R = 0, R_l = 0, R_s = 0, L = 0;   // L = 2n - 1
   int ksub = 0;        // subspace width (multiple of KB)
   int rmax = 0;        // rank bound = leading dimension of Tucker factors
