@@ -209,6 +209,7 @@ cudaError_t set_attributes_tucker(int optin);
 cudaError_t set_attributes_tc(int optin);
 cudaError_t set_attributes_core(int optin);
 int launch_core_tc(Ctx& c);
+int launch_energy_t2(Ctx& c, double* part, int blocks);
 cudaError_t set_attributes_plain(int optin);
 rs_status launch_plain(Ctx& c, int which, float* out);
 rs_status launch_pair_energy_forces(Ctx& c, int N, const double* xyz, const double* Z, double* E, double* F);

@@ -199,6 +199,85 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
   }
 }
 
+// Interaction energy on the tensor-core path (Sec. 4.2, Eq. (4.7), Lemma 3.10): the Tucker
+// value at a particle's grid point is sum_a V1[i1][a] T2[a][p], with T2[:, p] read from its tile
+// (kp FP16 hi + lo values in 16-byte chunks, scaled by 2^(S-8)) instead of the r1 r2 terms of T1,
+// which lie n apart in memory; the windows of the neighbours as on the CUDA-core path (FP64
+// factors).  One warp per charged particle; one partial sum per CTA.
+__global__ void __launch_bounds__(256)
+energy_t2_kernel(DevView c, const float* __restrict__ V1, const unsigned char* __restrict__ T2t,
+                 unsigned long long tile_bytes, int kp, double* part) {
+  __shared__ double red[8];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int mi = blockIdx.x * 8 + warp;
+  double e = 0.0;
+  if (mi < c.sc->n_nz) {
+    const int p = c.nz_idx[mi];
+    const int n = c.n, i1 = c.j[3 * p], i2 = c.j[3 * p + 1], i3 = c.j[3 * p + 2];
+    const int r1 = c.sc->rank[0];
+    const long long pt = (long long)i2 * n + i3;
+    const unsigned char* tile = T2t + (unsigned long long)(pt >> 7) * tile_bytes;
+    const int kc = kp >> 3;
+    double v = 0.0;
+    for (int ch = lane; ch < kc; ch += 32) {
+      const uint32_t off = kmajor_offset((int)(pt & 127), ch, kc);
+      const uint4 hi = *(const uint4*)(tile + off);
+      const uint4 lo = *(const uint4*)(tile + tile_bytes / 2 + off);
+      const __half2* h = reinterpret_cast<const __half2*>(&hi);
+      const __half2* l = reinterpret_cast<const __half2*>(&lo);
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 fh = __half22float2(h[q]), fl = __half22float2(l[q]);
+        const int a = 8 * ch + 2 * q;
+        if (a < r1) s = fmaf(V1[(long long)i1 * c.rmax + a], fh.x + fl.x, s);
+        if (a + 1 < r1) s = fmaf(V1[(long long)i1 * c.rmax + a + 1], fh.y + fl.y, s);
+      }
+      v += (double)s;
+    }
+    v = ldexp(v, -(operand_shift(c.sc, r1) - 8));
+    // short-range windows of the neighbours (FP64 factors)
+    const int g = c.sc->gamma, L = 2 * n - 1, nb = c.nbin;
+    const int b1a = max(0, i1 - g) / BIN, b1b = min(n - 1, i1 + g) / BIN;
+    const int b2a = max(0, i2 - g) / BIN, b2b = min(n - 1, i2 + g) / BIN;
+    const int b3a = max(0, i3 - g) / BIN, b3b = min(n - 1, i3 + g) / BIN;
+    const int nb3 = b3b - b3a + 1, nb2 = b2b - b2a + 1;
+    const int nbt = (b1b - b1a + 1) * nb2 * nb3;
+    for (int t = lane; t < nbt; t += 32) {
+      const int b3 = b3a + t % nb3, b2 = b2a + (t / nb3) % nb2, b1 = b1a + t / (nb3 * nb2);
+      const int b = (b1 * nb + b2) * nb + b3;
+      for (int it = c.bin_start[b]; it < c.bin_start[b + 1]; ++it) {
+        const int q = c.bin_items[it];
+        const int d1 = i1 - c.j[3 * q], d2 = i2 - c.j[3 * q + 1], d3 = i3 - c.j[3 * q + 2];
+        if (abs(d1) > g || abs(d2) > g || abs(d3) > g) continue;
+        double s = 0.0;
+        for (int k = c.R_l; k < c.R; ++k) {
+          const double* row = c.pk64 + (long long)k * L + n - 1;
+          s += row[d1] * row[d2] * row[d3];
+        }
+        v += c.Z[q] * s;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const double z = c.Z[p];
+    e = z * (v - z * c.sc->P_R0);
+  }
+  if (lane == 0) red[warp] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+int launch_energy_t2(Ctx& c, double* part, int blocks) {
+  const unsigned long long tile_bytes = 4ull * AS_M * (unsigned long long)c.tc_kpad;   // hi + lo FP16
+  energy_t2_kernel<<<blocks, 256, 0, c.stream>>>(make_view(c), (const float*)c.Z32, (const unsigned char*)c.T2,
+                                                 tile_bytes, c.tc_kpad, part);
+  return 1;
+}
+
 // ------------------------------------------------------------------ assembly kernel
 __global__ void __launch_bounds__(AS_THREADS, 1)
 assemble_kernel(const AsmArgs g) {

@@ -656,6 +656,7 @@ int launch_energy(Ctx& c, int N) {
   if (blocks < 1) blocks = 1;
   DevView v = make_view(c);
   if (c.fp64) energy_kernel<double><<<blocks, 256, 0, c.stream>>>(v, c.Z64, (const double*)c.T1, c.Epart);
+  else if (c.use_tc) launch_energy_t2(c, c.Epart, blocks);        // Tucker value from the T2 tiles
   else energy_kernel<float><<<blocks, 256, 0, c.stream>>>(v, c.Z32, (const float*)c.T1, c.Epart);
   energy_sum_kernel<<<1, 1024, 0, c.stream>>>(c.Epart, blocks, c.sc);
   (void)N;
