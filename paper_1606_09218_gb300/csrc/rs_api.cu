@@ -105,8 +105,11 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.om_colptr, 4 * (ks + 1));
   add(v, c.om_row, 4 * n * ZETA);
   add(v, c.om_sgn, 1 * n * ZETA);
-  add(v, c.part, 8 * (2 * 3 * NBC + 2 * 3) * (ks * KB + KB * KB));   // partials + reduced sums
+  // partials + reduced sums of the block Gram-Schmidt; before it, the rows' trace shares
+  add(v, c.part, 8 * std::max<size_t>((size_t)(2 * 3 * NBC + 2 * 3) * (ks * KB + KB * KB), 6 * (size_t)n));
   add(v, c.order, 4 * 3 * ks);
+  add(v, c.gscr.part, 8 * GEMM_SPLIT_SLOTS * 256);
+  add(v, c.gscr.count, 4 * GEMM_SPLIT_SLOTS);
   add(v, c.ev, 8 * 3 * ks);
   add(v, c.Z64, 8 * 3 * n * rm);
   add(v, c.Z32, 4 * 3 * n * rm);
@@ -281,6 +284,13 @@ rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
       return st == cudaErrorMemoryAllocation ? RS_ERR_OOM : RS_ERR_CUDA;
     }
     if (do_poison) cudaMemset(*e.first, 0xFF, e.second);
+  }
+  if (cudaMemset(c.gscr.count, 0, sizeof(unsigned) * GEMM_SPLIT_SLOTS) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = "device memset failed";
+    free_all(c);
+    delete h;
+    return RS_ERR_CUDA;
   }
   if (cudaMallocHost((void**)&c.h_sc, sizeof(DevScalars)) != cudaSuccess) {
     cudaGetLastError();

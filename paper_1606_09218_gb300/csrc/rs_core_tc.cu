@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) core_tc_kernel(CoreArgs g) {
   const float qmax = __uint_as_float(sc->qmax_bits), zmax = __uint_as_float(sc->zmax_bits);
   const int sA = (qmax > 0.f && zmax > 0.f) ? max(-100, min(100, 14 - exp2_above((double)zmax * qmax))) : 0;
   const int sB = (qmax > 0.f) ? max(-100, min(100, 14 - exp2_above((double)qmax * qmax))) : 0;
+  const int efx = beta_fx_shift(sc, g.R_l);            // fixed-point scale of the beta sums
 
   if (tid == 0) {
     for (int s = 0; s < CT_STAGES; ++s) {
@@ -322,12 +323,13 @@ __global__ void __launch_bounds__(CT_THREADS, 1) core_tc_kernel(CoreArgs g) {
       const int a = t.a0 + 32 * q + lane;
       if (a < r1) {
         // columns 32 half + j: b = b0 + 4 half + j / 8, c = c0 + j % 8
-        double* out = g.beta64 + ((long long)a * g.rmax + t.b0 + 4 * half) * g.rmax + t.c0;
+        unsigned long long* out = reinterpret_cast<unsigned long long*>(g.beta64) +
+                                  ((long long)a * g.rmax + t.b0 + 4 * half) * g.rmax + t.c0;
         const int nb = min(4, r2 - t.b0 - 4 * half), nc = min(8, r3 - t.c0);
 #pragma unroll
         for (int j = 0; j < 32; ++j)
           if ((j >> 3) < nb && (j & 7) < nc)
-            atomicAdd(out + (j >> 3) * g.rmax + (j & 7), ((double)hi[j] + (double)lo[j]) * unscale);
+            atomicAdd(out + (j >> 3) * g.rmax + (j & 7), beta_fx(((double)hi[j] + (double)lo[j]) * unscale, efx));
       }
     }
   }

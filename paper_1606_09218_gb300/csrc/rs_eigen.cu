@@ -23,19 +23,18 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 gemm_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __restrict__ A, int lda,
             long long sA, const T* __restrict__ B, int ldb, long long sB, T beta, T* C, int ldc,
-            long long sC, int splitK, const int* dynM, const int* dynN, const int* dynK) {
+            long long sC, const int* dynM, const int* dynN, const int* dynK) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
-  const int bz = blockIdx.z / splitK, kz = blockIdx.z % splitK;
+  const int bz = blockIdx.z;
   int m = M, nn = N, kk = K;
   if (dynM) m = min(m, dynM[bz]);
   if (dynN) nn = min(nn, dynN[bz]);
   if (dynK) kk = min(kk, dynK[bz]);
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
   if (row0 >= m || col0 >= nn) return;
-  const int chunk = ((kk + splitK - 1) / splitK + BK - 1) / BK * BK;
-  const int kbeg = kz * chunk, kend = min(kk, kbeg + chunk);
+  const int kbeg = 0, kend = kk;
   A += bz * sA;
   B += bz * sB;
   C += bz * sC;
@@ -87,52 +86,57 @@ gemm_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __restrict_
       int gc = col0 + tx + 16 * jj;
       if (gc >= nn) continue;
       T* p = C + (long long)gr * ldc + gc;
-      if (splitK > 1) {
-        atomicAdd(p, alpha * acc[i][jj]);
-      } else {
-        T v = alpha * acc[i][jj];
-        if (beta != T(0)) v += beta * *p;
-        *p = v;
-      }
+      T v = alpha * acc[i][jj];
+      if (beta != T(0)) v += beta * *p;
+      *p = v;
     }
   }
 }
 
-// 16x16-tile variant for small FP64 products: one output per thread, K split across CTAs so
-// that the few FP64 units of every SM take part (GB300 issues about one FP64 FMA per clock and
-// SM, so a 64x64 tile alone would take tens of microseconds).
+// 16x16-tile kernel of the FP64 products: one output per thread, K split across CTAs so that
+// the few FP64 units of every SM take part (GB300 issues about one FP64 FMA per clock and SM, so
+// a 64x64 tile alone would take tens of microseconds).  The split is deterministic: every CTA
+// stores its partial tile, and the last CTA of the tile to finish (counted with an atomic, after
+// a fence) adds the partials in the order of their K ranges and writes C, so the result does not
+// depend on the order in which the CTAs ran.  Entries of the M x N block outside the dynamic
+// sizes are written as zero.
 template <typename T>
 __global__ void __launch_bounds__(256)
 gemm_small_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __restrict__ A, int lda,
                   long long sA, const T* __restrict__ B, int ldb, long long sB, T* C, int ldc,
-                  long long sC, int splitK, const int* dynM, const int* dynN, const int* dynK) {
+                  long long sC, int splitK, const int* dynM, const int* dynN, const int* dynK,
+                  T* part, unsigned* count) {
   constexpr int BT = 16;
   __shared__ T As[BT][BT + 1];
   __shared__ T Bs[BT][BT + 1];
+  __shared__ unsigned s_last;
   const int bz = blockIdx.z / splitK, kz = blockIdx.z % splitK;
   int m = M, nn = N, kk = K;
   if (dynM) m = min(m, dynM[bz]);
   if (dynN) nn = min(nn, dynN[bz]);
   if (dynK) kk = min(kk, dynK[bz]);
   const int row0 = blockIdx.y * BT, col0 = blockIdx.x * BT;
-  if (row0 >= m || col0 >= nn) return;
+  const int tx = threadIdx.x % BT, ty = threadIdx.x / BT;
+  const int gr = row0 + ty, gc = col0 + tx;
+  C += bz * sC;
+  if (row0 >= m || col0 >= nn) {                 // the whole tile is outside the dynamic sizes
+    if (kz == 0 && gr < M && gc < N) C[(long long)gr * ldc + gc] = T(0);
+    return;
+  }
   const int chunk = ((kk + splitK - 1) / splitK + BT - 1) / BT * BT;
   const int kbeg = kz * chunk, kend = min(kk, kbeg + chunk);
-  if (kbeg >= kend) return;
   A += bz * sA;
   B += bz * sB;
-  C += bz * sC;
-  const int tx = threadIdx.x % BT, ty = threadIdx.x / BT;
   T acc = T(0);
   for (int k0 = kbeg; k0 < kend; k0 += BT) {
     {
-      int gr = row0 + ty, gk = k0 + tx;      // A element (gr, gk)
+      int ar = row0 + ty, gk = k0 + tx;      // A element (ar, gk)
       T v = T(0);
-      if (gr < m && gk < kend) v = tA ? A[(long long)gk * lda + gr] : A[(long long)gr * lda + gk];
+      if (ar < m && gk < kend) v = tA ? A[(long long)gk * lda + ar] : A[(long long)ar * lda + gk];
       As[ty][tx] = v;
-      int gk2 = k0 + ty, gc = col0 + tx;     // B element (gk2, gc)
+      int gk2 = k0 + ty, bc = col0 + tx;     // B element (gk2, bc)
       T w = T(0);
-      if (gc < nn && gk2 < kend) w = tB ? B[(long long)gc * ldb + gk2] : B[(long long)gk2 * ldb + gc];
+      if (bc < nn && gk2 < kend) w = tB ? B[(long long)bc * ldb + gk2] : B[(long long)gk2 * ldb + bc];
       Bs[ty][tx] = w;
     }
     __syncthreads();
@@ -140,58 +144,59 @@ gemm_small_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __res
     for (int k = 0; k < BT; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
     __syncthreads();
   }
-  const int gr = row0 + ty, gc = col0 + tx;
-  if (gr < m && gc < nn) atomicAdd(C + (long long)gr * ldc + gc, alpha * acc);
+  const bool inside = gr < m && gc < nn;
+  if (splitK > 1) {
+    const long long tile = ((long long)bz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    part[(tile * splitK + kz) * 256 + threadIdx.x] = acc;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&count[tile], 1u) == (unsigned)(splitK - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    acc = T(0);
+    for (int z = 0; z < splitK; ++z) acc += __ldcg(&part[(tile * splitK + z) * 256 + threadIdx.x]);
+    if (threadIdx.x == 0) count[tile] = 0u;    // ready for the next product
+  }
+  if (gr < M && gc < N) C[(long long)gr * ldc + gc] = inside ? alpha * acc : T(0);
 }
 
 template <typename T>
 void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha,
                   const T* A, int lda, long long sA, const T* B, int ldb, long long sB, T beta,
                   T* C, int ldc, long long sC, int batch, int splitK, const int* dynM,
-                  const int* dynN, const int* dynK) {
+                  const int* dynN, const int* dynK, const GemmScratch* scr) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
-  if (splitK < 1) splitK = 1;
-  // FP64 products whose 64x64 tiles would not fill half the GPU use 16x16 tiles with an
-  // automatic K split (atomics; C is cleared here).
-  if (sizeof(T) == 8 && beta == T(0) && (sC == (long long)M * ldc || batch == 1) &&
-      (long long)((N + 63) / 64) * ((M + 63) / 64) * batch < 76) {
-    long long tiles = (long long)((N + 15) / 16) * ((M + 15) / 16) * batch;
+  // FP64 products (C overwritten) use 16x16 tiles with a deterministic K split when the tiles
+  // alone would not cover the GPU twice; the split needs the context's partial-tile scratch
+  if (sizeof(T) == 8 && beta == T(0)) {
+    const long long tiles = (long long)((N + 15) / 16) * ((M + 15) / 16) * batch;
     int sk = (int)((2 * 152 + tiles - 1) / tiles);
-    int maxs = (K + 15) / 16;
+    const int maxs = (K + 15) / 16;
     if (sk > maxs) sk = maxs;
+    if (!scr || !scr->part) sk = 1;
+    else if (tiles * sk > GEMM_SPLIT_SLOTS) sk = (int)(GEMM_SPLIT_SLOTS / tiles);
     if (sk < 1) sk = 1;
-    cudaMemsetAsync(C, 0, sizeof(T) * ((long long)(batch - 1) * sC + (long long)M * ldc), s);
     dim3 grid((N + 15) / 16, (M + 15) / 16, batch * sk);
-    gemm_small_kernel<T><<<grid, 256, 0, s>>>(transA, transB, M, N, K, alpha, A, lda, sA, B, ldb,
-                                             sB, C, ldc, sC, sk, dynM, dynN, dynK);
+    gemm_small_kernel<T><<<grid, 256, 0, s>>>(transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB, C,
+                                             ldc, sC, sk, dynM, dynN, dynK,
+                                             sk > 1 ? (T*)scr->part : nullptr, sk > 1 ? scr->count : nullptr);
     return;
   }
-  // Otherwise FP64 products get an automatic K split when one is not given: enough CTAs to
-  // cover the GPU twice, chunks of at least 32 along K (C cleared here).
-  if (splitK == 1 && sizeof(T) == 8 && beta == T(0) && K >= 64) {
-    long long tiles = (long long)((N + 63) / 64) * ((M + 63) / 64) * batch;
-    int want = (int)((2 * 152 + tiles - 1) / tiles);
-    int maxs = K / 32;
-    splitK = want < maxs ? want : maxs;
-    if (splitK < 1) splitK = 1;
-    if (splitK > 1) {
-      if (sC == (long long)M * ldc || batch == 1)
-        cudaMemsetAsync(C, 0, sizeof(T) * ((long long)(batch - 1) * sC + (long long)M * ldc), s);
-      else
-        splitK = 1;
-    }
-  }
-  dim3 grid((N + 63) / 64, (M + 63) / 64, batch * splitK);
+  (void)splitK;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
   gemm_kernel<T><<<grid, 256, 0, s>>>(transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB,
-                                      beta, C, ldc, sC, splitK, dynM, dynN, dynK);
+                                      beta, C, ldc, sC, dynM, dynN, dynK);
 }
 
 template void gemm_batched<double>(cudaStream_t, bool, bool, int, int, int, double, const double*,
                                    int, long long, const double*, int, long long, double, double*,
-                                   int, long long, int, int, const int*, const int*, const int*);
+                                   int, long long, int, int, const int*, const int*, const int*,
+                                   const GemmScratch*);
 template void gemm_batched<float>(cudaStream_t, bool, bool, int, int, int, float, const float*,
                                   int, long long, const float*, int, long long, float, float*,
-                                  int, long long, int, int, const int*, const int*, const int*);
+                                  int, long long, int, int, const int*, const int*, const int*,
+                                  const GemmScratch*);
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
@@ -234,27 +239,37 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // ZETA entries +-1 in pseudo-random columns (a sparse subspace embedding; the captured energy is
 // certified later by the FP64 Rayleigh quotient).  Omega is stored by column (CSR, built once per
 // context): X[r][m] = sum over (i, s) in column m of s * G[r][i].  One thread per (r, m).
-__global__ void sparse_range_kernel(const double* __restrict__ G, const int* __restrict__ colptr,
-                                    const int* __restrict__ rowidx, const signed char* __restrict__ sgn,
-                                    int n, int ks, double* X) {
+__global__ void __launch_bounds__(KSUB_MAX)
+sparse_range_kernel(const double* __restrict__ G, const int* __restrict__ colptr,
+                    const int* __restrict__ rowidx, const signed char* __restrict__ sgn, int n, int ks,
+                    double* X, double* rowpart) {
+  // one CTA per row r of X_l (blockDim >= ks); also the row's share of trace(G_l) and ||X_l||_F^2
+  __shared__ double red[32];
   const int l = blockIdx.z, r = blockIdx.y;
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= ks) return;
+  const int m = threadIdx.x;
   const double* Gr = G + ((long long)l * n + r) * n;
   double v = 0.0;
-  for (int t = colptr[m]; t < colptr[m + 1]; ++t) v += (double)sgn[t] * Gr[rowidx[t]];
-  X[((long long)l * n + r) * ks + m] = v;
+  if (m < ks) {
+    for (int t = colptr[m]; t < colptr[m + 1]; ++t) v += (double)sgn[t] * Gr[rowidx[t]];
+    X[((long long)l * n + r) * ks + m] = v;
+  }
+  const double x2 = block_sum(v * v, red);
+  if (threadIdx.x == 0) {
+    rowpart[2 * ((long long)l * n + r)] = Gr[r];
+    rowpart[2 * ((long long)l * n + r) + 1] = x2;
+  }
 }
 
-// trace(G_l) and ||X_l||_F^2 per mode (one CTA per mode).
-__global__ void traces_kernel(const double* G, const double* X, int n, int ks, DevScalars* sc) {
+// trace(G_l) and ||X_l||_F^2 per mode from the rows' shares (one CTA per mode, fixed order)
+__global__ void traces_kernel(const double* rowpart, int n, DevScalars* sc) {
   __shared__ double red[32];
-  int l = blockIdx.x;
-  const double* g = G + (long long)l * n * n;
-  const double* x = X + (long long)l * n * ks;
+  const int l = blockIdx.x;
+  const double* rp = rowpart + 2ll * l * n;
   double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += g[(long long)i * n + i];
-  for (long long i = threadIdx.x; i < (long long)n * ks; i += blockDim.x) b += x[i] * x[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a += rp[2 * i];
+    b += rp[2 * i + 1];
+  }
   a = block_sum(a, red);
   b = block_sum(b, red);
   if (threadIdx.x == 0) {
@@ -899,9 +914,9 @@ static void congruence(Ctx& c, double* Tm, const double* Wm) {
   const long long sK = (long long)ks * ks;
   const int* ke = c.sc->k_eff;
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, Tm, ks, sK, Wm, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, 1, ke, ke, ke);
+                       c.T2k, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
   gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, Wm, ks, sK, c.T2k, ks, sK, 0.0,
-                       Tm, ks, sK, 3, 1, ke, ke, ke);
+                       Tm, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
 }
 
 // Rayleigh-Ritz refinement: two FP32 Jacobi passes on the graded T (rotations accumulated in
@@ -918,20 +933,20 @@ static int refine(Ctx& c, double*& Qa, double*& Qb) {
   jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W2, ks, c.sc, 4, 2e-7f);
   congruence(c, c.T, c.W2);
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W2, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, 1, ke, ke, ke);
+                       c.T2k, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
   // Qb = Qa (W1 W2)
   gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, c.T2k, ks, sK, 0.0, Qb,
-                       ks, sQ, 3, 1, nullptr, ke, ke);
+                       ks, sQ, 3, 1, nullptr, ke, ke, &c.gscr);
   // Newton-Schulz: E = Qb^T Qb - I ; M = I - E/2 + 3/8 E^2 ; Qa = Qb M ; T = M^T T M
   gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, Qb, ks, sQ, Qb, ks, sQ, 0.0, c.W,
-                       ks, sK, 3, 1, ke, ke, nullptr);
+                       ks, sK, 3, 1, ke, ke, nullptr, &c.gscr);
   dim3 g2((ks * ks + 255) / 256, 3);
   sub_identity_kernel<<<g2, 256, 0, c.stream>>>(c.W, ks, c.sc);
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, 1, ke, ke, ke);
+                       c.T2k, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
   ns_matrix_kernel<<<g2, 256, 0, c.stream>>>(c.W, c.T2k, c.W, ks, c.sc);
   gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qb, ks, sQ, c.W, ks, sK, 0.0, Qa,
-                       ks, sQ, 3, 1, nullptr, ke, ke);
+                       ks, sQ, 3, 1, nullptr, ke, ke, &c.gscr);
   congruence(c, c.T, c.W);
   return 2 + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1 + 1 + 2;
 }
@@ -940,9 +955,11 @@ int launch_subspace(Ctx& c) {
   const int n = c.n, ks = c.ksub;
   const long long sQ = (long long)n * ks, sK = (long long)ks * ks, sG = (long long)n * n;
   // X = G * Omega with the sparse sign embedding of this context
-  sparse_range_kernel<<<dim3((ks + 127) / 128, n, 3), 128, 0, c.stream>>>(c.G, c.om_colptr, c.om_row,
-                                                                        c.om_sgn, n, ks, c.X);
-  traces_kernel<<<3, 256, 0, c.stream>>>(c.G, c.X, n, ks, c.sc);
+  // (the row shares of the traces go to the block Gram-Schmidt's partial-sum buffer, which is
+  // free until that kernel starts)
+  sparse_range_kernel<<<dim3(1, n, 3), KSUB_MAX, 0, c.stream>>>(c.G, c.om_colptr, c.om_row, c.om_sgn, n,
+                                                               ks, c.X, c.part);
+  traces_kernel<<<3, 256, 0, c.stream>>>(c.part, n, c.sc);
   // block Gram-Schmidt (cooperative)
   {
     void* args[] = {(void*)&c.X, (void*)&c.Q, (void*)&c.part, (void*)&n, (void*)&ks, (void*)&c.sc};
@@ -957,12 +974,10 @@ int launch_subspace(Ctx& c) {
   }();
   if (dbg_steps <= 1) return 5;
   // Y = G Q ; T = Q^T Y
-  cudaMemsetAsync(c.Y, 0, sizeof(double) * 3 * sQ, c.stream);
   gemm_batched<double>(c.stream, false, false, n, ks, n, 1.0, c.G, n, sG, c.Q, ks, sQ, 0.0, c.Y,
-                       ks, sQ, 3, 4, nullptr, ke, nullptr);
-  cudaMemsetAsync(c.T, 0, sizeof(double) * 3 * sK, c.stream);
+                       ks, sQ, 3, 4, nullptr, ke, nullptr, &c.gscr);
   gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, c.Q, ks, sQ, c.Y, ks, sQ, 0.0, c.T,
-                       ks, sK, 3, 8, ke, ke, nullptr);
+                       ks, sK, 3, 8, ke, ke, nullptr, &c.gscr);
   // Rayleigh-Ritz refinement; the rotated basis goes through c.X and ends in c.Q
   double* Qa = c.Q;
   double* Qb = c.X;

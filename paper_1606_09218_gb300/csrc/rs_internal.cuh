@@ -42,6 +42,8 @@ struct DevScalars {
   unsigned flags;
   unsigned pad0;
   double P_R0, P_Rl0, delta;
+  double zabs_sum;          // sum of |z| over the particles (bound of the core sums)
+  unsigned long long w2max_bits;   // largest |z|^{2/3} (double bits; scale of the weight sums)
   double trG[3], trT[3], xnorm2[3], tail_rel[3];
   int gamma;
   int n_nz;                 // particles with nonzero charge
@@ -63,10 +65,20 @@ struct DevScalars {
   alignas(128) unsigned bar_gen[3 * 32];
 };
 
+// scratch of the deterministic K split of the FP64 products: GEMM_SPLIT_SLOTS partial 16x16
+// tiles and as many arrival counters (a split product has fewer than 2 x 152 tiles and at most
+// ceil(2 x 152 / tiles) parts per tile, so fewer than 608 partials)
+constexpr long long GEMM_SPLIT_SLOTS = 608;
+struct GemmScratch {
+  double* part = nullptr;
+  unsigned* count = nullptr;
+};
+
 struct Ctx {
   rs_config cfg;
   cudaStream_t stream = nullptr;
   cudaStream_t aux = nullptr;    // window lists and particle bins, overlapped with the eigen stage
+  GemmScratch gscr;              // deterministic K split of the FP64 products
   cudaEvent_t ev_part = nullptr, ev_bins = nullptr, ev_side = nullptr;
   int n = 0, R = 0, R_l = 0, R_s = 0, L = 0;   // L = 2n - 1
   int ksub = 0;        // subspace width (multiple of KB)
@@ -218,12 +230,31 @@ int launch_eval_points(Ctx& c, int M, const int* idx, double* out);
 // generic batched GEMM on row-major matrices:
 //   C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b]
 // op(A) is M x K (A stored M x K with lda, or K x M when transA), op(B) is K x N.
+// Fixed-point accumulation of the Tucker core.  Every partial sum of beta[a][b][c] (any subset
+// of its terms z_K q1[K][a] q2[K][b] q3[K][c]) is bounded by B = R_l sum|z| qmax^3 (qmax the
+// largest projection, recorded as a rounded float: factor 2 of margin), so with the scale 2^e,
+// B 2^e < 2^61, the partial sums are 64-bit integers that add exactly: beta does not depend on
+// the order of the atomic additions (2^-e is about 2^-61 B, far below FP64 rounding of beta).
+__device__ __forceinline__ int beta_fx_shift(const DevScalars* sc, int R_l) {
+  const double q = (double)__uint_as_float(sc->qmax_bits);
+  const double B = 2.0 * R_l * sc->zabs_sum * q * q * q;
+  if (!(B > 0.0) || !isfinite(B)) return 0;
+  int E = 0;
+  frexp(B, &E);                       // B < 2^E
+  return max(-1000, min(1000, 61 - E));
+}
+__device__ __forceinline__ unsigned long long beta_fx(double v, int e) {
+  return (unsigned long long)__double2ll_rn(ldexp(v, e));
+}
+
+// FP64 products with beta = 0 split K across CTAs deterministically through scr (partial tiles
+// and per-tile arrival counters, zero between products); without scr they do not split.
 template <typename T>
 void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K,
                   T alpha, const T* A, int lda, long long sA,
                   const T* B, int ldb, long long sB, T beta, T* C, int ldc, long long sC,
                   int batch, int splitK, const int* dynM = nullptr, const int* dynN = nullptr,
-                  const int* dynK = nullptr);
+                  const int* dynK = nullptr, const GemmScratch* scr = nullptr);
 
 }  // namespace rs
 

@@ -82,31 +82,67 @@ int launch_factors(Ctx& c) {
 
 // ------------------------------------------------------------------ particles
 // Snap each centre to its nearest grid point (ties away from zero; Sec. 3.2 places the
-// centres on grid points), flag centres outside the box, and aggregate the squared column
-// weights w^2 = |z|^{2/3} per grid coordinate (columns at equal shifts add in U U^T).
-__global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n, double b,
-                               double h, int* j, double* C, DevScalars* sc) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
-  double z = Z[p];
+// centres on grid points), flag centres outside the box, and record the largest squared column
+// weight w^2 = |z|^{2/3} (the scale of the aggregation below).
+__device__ __forceinline__ bool snap_particle(const double* xyz, double z, int p, int n, double b, double h,
+                                              int jj[3]) {
   bool bad = !isfinite(z);
-  int jj[3];
   for (int l = 0; l < 3; ++l) {
     double x = xyz[3 * p + l];
     if (!isfinite(x) || fabs(x) > b * (1.0 + 1e-12)) bad = true;
     double s = (x + b) / h;
     int q = isfinite(s) ? (int)floor(s + 0.5) : 0;
     jj[l] = min(max(q, 0), n - 1);
-    j[3 * p + l] = jj[l];
   }
-  if (bad) {
+  return !bad;
+}
+
+__global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n, double b,
+                               double h, int* j, DevScalars* sc) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const double z = Z[p];
+  int jj[3];
+  const bool ok = snap_particle(xyz, z, p, n, b, h, jj);
+  for (int l = 0; l < 3; ++l) j[3 * p + l] = jj[l];
+  if (!ok) {
     atomicOr(&sc->flags, (unsigned)FLAG_OUTSIDE);
     return;
   }
-  if (z != 0.0) {
-    double w2 = pow(fabs(z), 2.0 / 3.0);
-    for (int l = 0; l < 3; ++l) atomicAdd(&C[l * n + jj[l]], w2);
-  }
+  if (z != 0.0) atomicMax(&sc->w2max_bits, (unsigned long long)__double_as_longlong(pow(fabs(z), 2.0 / 3.0)));
+}
+
+// The weights C_l[j] = sum_{nu at j} w_nu^2 per grid coordinate (columns at equal shifts add in
+// U U^T) as 64-bit fixed-point sums with the scale 2^e, N max w^2 2^e < 2^61: integer additions
+// are exact, so C does not depend on the order of the atomics (a nonzero weight adds at least
+// one unit, so no charged coordinate drops out).  C holds the integers until c_fixed_to_double.
+__device__ __forceinline__ int c_fx_shift(const DevScalars* sc, int N) {
+  const double wmax = __longlong_as_double((long long)sc->w2max_bits);
+  const double B = (double)N * wmax;
+  if (!(B > 0.0) || !isfinite(B)) return 0;
+  int E = 0;
+  frexp(B, &E);
+  return max(-1000, min(1000, 61 - E));
+}
+
+__global__ void aggregate_kernel(const double* xyz, const double* Z, int N, int n, double b, double h,
+                                 double* C, const DevScalars* sc) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const double z = Z[p];
+  int jj[3];
+  if (!snap_particle(xyz, z, p, n, b, h, jj) || z == 0.0) return;
+  const int e = c_fx_shift(sc, N);
+  const long long v = __double2ll_rn(ldexp(pow(fabs(z), 2.0 / 3.0), e));
+  unsigned long long* Cfx = reinterpret_cast<unsigned long long*>(C);
+  for (int l = 0; l < 3; ++l) atomicAdd(&Cfx[l * n + jj[l]], (unsigned long long)(v > 0 ? v : 1));
+}
+
+__global__ void c_fixed_to_double(double* C, int n, int N, const DevScalars* sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n) return;
+  const int e = c_fx_shift(sc, N);
+  C[i] = ldexp((double)reinterpret_cast<const long long*>(C)[i], -e);
 }
 
 // Deterministic compaction of the particles with nonzero charge (one CTA, chunked scan).
@@ -115,10 +151,24 @@ __global__ void compact_nz_kernel(const double* Z, int N, int* nz_idx, DevScalar
   const int T = blockDim.x, t = threadIdx.x;
   const int per = (N + T - 1) / T;
   const int b0 = min(N, t * per), b1 = min(N, b0 + per);
+  __shared__ double zred[32];
   int cnt = 0;
-  for (int p = b0; p < b1; ++p) cnt += (Z[p] != 0.0 && isfinite(Z[p])) ? 1 : 0;
+  double za = 0.0;
+  for (int p = b0; p < b1; ++p) {
+    const bool nz = Z[p] != 0.0 && isfinite(Z[p]);
+    cnt += nz ? 1 : 0;
+    za += nz ? fabs(Z[p]) : 0.0;
+  }
+  // sum |z| in a fixed order (bound of the core sums)
+  for (int o = 16; o > 0; o >>= 1) za += __shfl_down_sync(0xffffffffu, za, o);
+  if ((t & 31) == 0) zred[t >> 5] = za;
   scan[t] = cnt;
   __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (T + 31) / 32; ++w) s += zred[w];
+    sc->zabs_sum = s;
+  }
   for (int o = 1; o < T; o <<= 1) {
     int v = (t >= o) ? scan[t - o] : 0;
     __syncthreads();
@@ -172,9 +222,10 @@ int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep) {
   int k = 2;
   cudaMemsetAsync(c.C, 0, sizeof(double) * 3 * c.n, c.stream);
   if (N > 0) {
-    prepare_kernel<<<(N + 255) / 256, 256, 0, c.stream>>>(c.xyz, c.Z, N, c.n, c.cfg.b, c.h, c.j,
-                                                          c.C, c.sc);
-    ++k;
+    prepare_kernel<<<(N + 255) / 256, 256, 0, c.stream>>>(c.xyz, c.Z, N, c.n, c.cfg.b, c.h, c.j, c.sc);
+    aggregate_kernel<<<(N + 255) / 256, 256, 0, c.stream>>>(c.xyz, c.Z, N, c.n, c.cfg.b, c.h, c.C, c.sc);
+    c_fixed_to_double<<<(3 * c.n + 255) / 256, 256, 0, c.stream>>>(c.C, c.n, N, c.sc);
+    k += 3;
   }
   compact_nz_kernel<<<1, 1024, 0, c.stream>>>(c.Z, N, c.nz_idx, c.sc);
   compact_nzj_kernel<<<3, 1024, 0, c.stream>>>(c.C, c.n, c.nzj, c.sc);
@@ -186,19 +237,26 @@ int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep) {
 }
 
 // ------------------------------------------------------------------ F and Gram (a3, a4)
-// F[a][b] = sum_{k long} p_k[a] p_k[b] over the doubled index range (L x L, FP64).
-__global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F) {
+// F[a][b] = sum_{k long} p_k[a] p_k[b] over the doubled index range (L x L, FP64), or, for the
+// double-float Gram, the same values as FP32 pairs (hi, lo) with hi + lo = F to 2^-48.
+__global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F, float2* F2) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   int a = blockIdx.y;
   if (b >= L) return;
   double v = 0.0;
   for (int k = 0; k < R_l; ++k) v += pk64[k * L + a] * pk64[k * L + b];
-  F[(long long)a * L + b] = v;
+  if (F2) {
+    const float hi = (float)v;
+    F2[(long long)a * L + b] = make_float2(hi, (float)(v - (double)hi));
+  } else {
+    F[(long long)a * L + b] = v;
+  }
 }
 
-static void launch_fmatrix(Ctx& c) {
+static void launch_fmatrix(Ctx& c, bool split) {
   dim3 grid((c.L + 255) / 256, c.L);
-  fmatrix_kernel<<<grid, 256, 0, c.stream>>>(c.pk64, c.R_l, c.L, c.F);
+  fmatrix_kernel<<<grid, 256, 0, c.stream>>>(c.pk64, c.R_l, c.L, split ? nullptr : c.F,
+                                             split ? (float2*)c.F : nullptr);
 }
 
 // G_l[i][i'] = sum_j C_l[j] F[i - j + n - 1][i' - j + n - 1]  (= U^(l) U^(l)^T with the columns
@@ -263,12 +321,102 @@ gram_kernel(const double* __restrict__ F, const double* __restrict__ C, const in
   }
 }
 
+// The FP32 bulk path forms G with the same sums in double-float arithmetic: w = C_l[j] and
+// F as FP32 pairs (hi, lo), each product w F as hi*hi plus its exact rounding error (FMA) plus
+// the two cross terms, added into an FP32 pair (s, t) by an error-free two-sum and renormalised
+// every 16 terms.  All terms are positive, so every entry carries a relative error of order
+// 2^-48 sqrt(terms) (about 1e-13; FP64 gives 1e-15), while the rank cut-off resolves eigenvalues
+// down to eps^2/3 of the trace.  One FP64 FMA issues at 1/64 of the FP32 rate on this GPU, so the
+// twelve FP32 operations of a term take a fifth of the time.  The exact roundings are
+// intrinsics, so no product is contracted into an addition.
+__global__ void __launch_bounds__(256)
+gram_df_kernel(const float2* __restrict__ F2, const double* __restrict__ C, const int* __restrict__ nzj,
+               const DevScalars* sc, int n, double* G) {
+  const int l = blockIdx.y;
+  const int nt = (n + 31) / 32;
+  int t = blockIdx.x, ti = 0;
+  while (t >= nt - ti) { t -= nt - ti; ++ti; }
+  const int tj = ti + t;
+  const int I0 = ti * 32, J0 = tj * 32;
+  const int L = 2 * n - 1;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  __shared__ float2 sw[256];
+  __shared__ int sj[256];
+  float hs[4] = {0.f, 0.f, 0.f, 0.f}, ls[4] = {0.f, 0.f, 0.f, 0.f};
+  const int cnt_all = sc->nzj_count[l];
+  const int split = gridDim.z;
+  const int mh = (cnt_all + split - 1) / split;
+  const int mbeg = min(cnt_all, (int)blockIdx.z * mh), cnt = min(cnt_all, mbeg + mh);
+  const double* Cl = C + l * n;
+  const int* nl = nzj + l * n;
+  const int ip = J0 + tx;
+  bool live[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) live[r] = (I0 + ty + 8 * r < n) && ip < n;
+  for (int m0 = mbeg; m0 < cnt; m0 += 256) {
+    int m = m0 + threadIdx.x;
+    if (m < cnt) {
+      const int jv = nl[m];
+      const double w = Cl[jv];
+      const float wh = (float)w;
+      sj[threadIdx.x] = jv;
+      sw[threadIdx.x] = make_float2(wh, (float)(w - (double)wh));
+    }
+    __syncthreads();
+    int mm = min(256, cnt - m0);
+    for (int q = 0; q < mm; ++q) {
+      const int jv = sj[q];
+      const float2 w = sw[q];
+      const float2* Fr = F2 + (long long)(I0 + ty - jv + n - 1) * L + (ip - jv + n - 1);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (!live[r]) continue;
+        const float2 f = Fr[(long long)(8 * r) * L];
+        const float p = __fmul_rn(w.x, f.x);
+        float e = fmaf(w.x, f.x, -p);                 // exact error of the rounded product
+        e = fmaf(w.x, f.y, e);
+        e = fmaf(w.y, f.x, e);
+        const float s = __fadd_rn(hs[r], p);          // two-sum: s + err = hs + p exactly
+        const float z = __fsub_rn(s, hs[r]);
+        const float err = __fadd_rn(__fsub_rn(hs[r], __fsub_rn(s, z)), __fsub_rn(p, z));
+        ls[r] = __fadd_rn(ls[r], __fadd_rn(err, e));
+        hs[r] = s;
+      }
+      if ((q & 15) == 15) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {                // fast two-sum, |hs| >= |ls|
+          const float s = __fadd_rn(hs[r], ls[r]);
+          ls[r] = __fsub_rn(ls[r], __fsub_rn(s, hs[r]));
+          hs[r] = s;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  double* Gl = G + (long long)l * n * n;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int i = I0 + ty + 8 * r;
+    if (!live[r]) continue;
+    const double v = (double)hs[r] + (double)ls[r];
+    if (split == 1) {
+      Gl[(long long)i * n + ip] = v;
+      if (ti != tj) Gl[(long long)ip * n + i] = v;
+    } else {
+      atomicAdd(&Gl[(long long)i * n + ip], v);
+      if (ti != tj) atomicAdd(&Gl[(long long)ip * n + i], v);
+    }
+  }
+}
+
 int launch_gram(Ctx& c) {
-  launch_fmatrix(c);
+  const bool df = !c.fp64;                   // double-float sums on the FP32 bulk path
+  launch_fmatrix(c, df);
   int nt = (c.n + 31) / 32;
   dim3 grid(nt * (nt + 1) / 2, 3, 2);
   cudaMemsetAsync(c.G, 0, sizeof(double) * 3 * (size_t)c.n * c.n, c.stream);
-  gram_kernel<<<grid, 256, 0, c.stream>>>(c.F, c.C, c.nzj, c.sc, c.n, c.G);
+  if (df) gram_df_kernel<<<grid, 256, 0, c.stream>>>((const float2*)c.F, c.C, c.nzj, c.sc, c.n, c.G);
+  else gram_kernel<<<grid, 256, 0, c.stream>>>(c.F, c.C, c.nzj, c.sc, c.n, c.G);
   return 2;
 }
 

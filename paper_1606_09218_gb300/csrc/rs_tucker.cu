@@ -220,6 +220,8 @@ core_kernel(const T* __restrict__ Qp, const int* __restrict__ jidx, const int* _
   }
   const int bb = b0 + tb;
   if (bb >= r2) return;
+  const int efx = beta_fx_shift(sc, R_l);
+  unsigned long long* bfx = reinterpret_cast<unsigned long long*>(beta64);
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
     const int aa = a0 + 4 * ta + x;
@@ -227,21 +229,26 @@ core_kernel(const T* __restrict__ Qp, const int* __restrict__ jidx, const int* _
 #pragma unroll
     for (int y = 0; y < 8; ++y) {
       const int cc = c0 + 8 * tc + y;
-      if (cc < r3) atomicAdd(&beta64[((long long)aa * rmax + bb) * rmax + cc], (double)hi[x][y] + (double)lo[x][y]);
+      if (cc < r3)
+        atomicAdd(&bfx[((long long)aa * rmax + bb) * rmax + cc], beta_fx((double)hi[x][y] + (double)lo[x][y], efx));
     }
   }
 }
 
-// beta in the bulk type, and ||beta[a, :, :]||^2 per slice a (one CTA per slice)
+// beta from its fixed-point sums (in place as FP64, and in the bulk type), and ||beta[a, :, :]||^2
+// per slice a (one CTA per slice)
 template <typename T>
 __global__ void __launch_bounds__(256)
-convert_beta_kernel(const double* beta64, T* beta, int rmax, DevScalars* sc) {
+convert_beta_kernel(double* beta64, T* beta, int rmax, int R_l, DevScalars* sc) {
   __shared__ double red[8];
   const int a = blockIdx.x;
   const long long base = (long long)a * rmax * rmax;
+  const int efx = beta_fx_shift(sc, R_l);
+  long long* bfx = reinterpret_cast<long long*>(beta64);
   double s = 0.0;
   for (int e = threadIdx.x; e < rmax * rmax; e += blockDim.x) {
-    const double v = beta64[base + e];
+    const double v = ldexp((double)bfx[base + e], -efx);
+    beta64[base + e] = v;
     beta[base + e] = (T)v;
     s += v * v;
   }
@@ -289,18 +296,18 @@ static int projection_core_t(Ctx& c) {
   else
     core_kernel<T><<<g2, 256, core_smem_bytes<T>(), c.stream>>>(Qp, c.j, c.nz_idx, c.Z, n, rmax, c.R_l, c.sc,
                                                                  c.beta64);
-  convert_beta_kernel<T><<<rmax, 256, 0, c.stream>>>(c.beta64, (T*)c.beta, rmax, c.sc);
+  convert_beta_kernel<T><<<rmax, 256, 0, c.stream>>>(c.beta64, (T*)c.beta, rmax, c.R_l, c.sc);
   // T1[a][b][i3] = sum_c beta[a][b][c] V3[i3][c]      (rows (a,b), K = r3)
   const T* Zb = Bulk<T>::Z(c);
   const long long sZ = (long long)n * rmax;
   gemm_batched<T>(c.stream, false, true, rmax * rmax, n, rmax, T(1), (const T*)c.beta, rmax, 0,
-                  Zb + 2 * sZ, rmax, 0, T(0), (T*)c.T1, n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 2);
+                  Zb + 2 * sZ, rmax, 0, T(0), (T*)c.T1, n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 2, &c.gscr);
   // T2[a][i2][i3] = sum_b V2[i2][b] T1[a][b][i3]        (batch a < r1, K = r2)
   if (c.use_tc && !c.fp64) return 3 + kcore + launch_t2_tiles(c);   // tiled FP16 operands
   batch_dims_kernel<<<(rmax + 127) / 128, 128, 0, c.stream>>>(c.adims, c.kdims, rmax, n, c.sc);
   gemm_batched<T>(c.stream, false, false, n, n, rmax, T(1), Zb + sZ, rmax, 0, (const T*)c.T1, n,
                   (long long)rmax * n, T(0), (T*)c.T2, c.t2_ld, (long long)n * c.t2_ld, rmax, 1,
-                  c.adims, nullptr, c.kdims);
+                  c.adims, nullptr, c.kdims, &c.gscr);
   return 5 + kcore;
 }
 
@@ -528,13 +535,13 @@ static int recon_gemm_t(Ctx& c, T* out) {
   if (c.t2_ld == n) {
     // P[i1][(i2,i3)] = sum_a V1[i1][a] T2[a][(i2,i3)]
     gemm_batched<T>(c.stream, false, false, n, n * n, rmax, T(1), Zb, rmax, 0, (const T*)c.T2,
-                    n * n, 0, T(0), out, n * n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 0);
+                    n * n, 0, T(0), out, n * n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 0, &c.gscr);
   } else {
     // padded T2 rows: one batch per i2, P[i1][i2][i3] = sum_a V1[i1][a] T2[a][i2][i3]
     const long long ldb = (long long)n * c.t2_ld;
     gemm_batched<T>(c.stream, false, false, n, n, rmax, T(1), Zb, rmax, 0, (const T*)c.T2,
                     (int)ldb, c.t2_ld, T(0), out, n * n, n, n, 1, nullptr, nullptr,
-                    c.sc->rank + 0);
+                    c.sc->rank + 0, &c.gscr);
   }
   return 1;
 }

@@ -17,7 +17,7 @@ from workloads import load_config, make_particles  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-REL_TOL = 1e-12   # FP64 Gram matrices; only the order of the FP64 atomic weight sums differs
+REL_TOL = 1e-12   # FP64 Gram matrices (the FP32 bulk path forms G in double-float arithmetic, ~1e-14)
 
 
 def _gram_noalloc(lib, ccfg, xyz, Z, n):
