@@ -717,14 +717,21 @@ jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* s
   }
   __syncthreads();
   const int half = ke / 2;
+  // round-robin pairing (position 0 fixed, the others rotate): pair m of round r is
+  // (a, b) = (m ? 1 + (m - 1 + r) mod (ke - 1) : 0, 1 + (ke - 2 - m + r) mod (ke - 1)); thread m
+  // keeps its pair in registers and advances it by one position per round (the integer
+  // divisions of the closed form had been the larger part of the parameter phase)
+  int ra = 0, rb = 0;
+  if (tid < half) {
+    ra = tid;
+    rb = (tid == 0) ? ke - 1 : ke - 1 - tid;
+  }
   for (int sweep = 0; sweep < max_sweeps && ke > 1; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int round = 0; round < ke - 1; ++round) {
-      // round-robin pairing: position 0 fixed, the others rotate
-      for (int m = tid; m < half; m += nt) {
-        int a = (m == 0) ? 0 : 1 + (m - 1 + round) % (ke - 1);
-        int b = 1 + (ke - 2 - m + round) % (ke - 1);
+      for (int m = tid; m < half; m += nt) {        // half <= KSUB_MAX / 2 < nt: one pair per thread
+        const int a = ra, b = rb;
         int p = min(a, b), q = max(a, b);
         pp[m] = p;
         qq[m] = q;
@@ -746,6 +753,10 @@ jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* s
         sn[m] = s;
         dpp[m] = app - t * apq;     // graded-accurate diagonal of the rotated pair
         dqq[m] = aqq + t * apq;
+      }
+      if (tid < half) {                             // the pairs of the next round
+        if (tid != 0) ra = (ra == ke - 1) ? 1 : ra + 1;
+        rb = (rb == ke - 1) ? 1 : rb + 1;
       }
       __syncthreads();
       // rows: A[p,:], A[q,:] -- warp w takes pairs w, w + 8, ..., lanes take columns

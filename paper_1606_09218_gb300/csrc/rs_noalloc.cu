@@ -24,8 +24,7 @@ __global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n,
                                double h, int* j, DevScalars* sc);
 __global__ void aggregate_kernel(const double* xyz, const double* Z, int N, int n, double b, double h,
                                  double* C, const DevScalars* sc);
-__global__ void c_fixed_to_double(double* C, int n, int N, const DevScalars* sc);
-__global__ void compact_nzj_kernel(const double* C, int n, int* nzj, DevScalars* sc);
+__global__ void compact_nzj_kernel(double* C, int n, int N, int* nzj, DevScalars* sc);
 __global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F, float2* F2);
 __global__ void gram_kernel(const double* F, const double* C, const int* nzj,
                             const DevScalars* sc, int n, double* G);
@@ -120,9 +119,8 @@ extern "C" rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* 
   if (N > 0) {
     prepare_kernel<<<(N + 255) / 256, 256, 0, s>>>(xyz, Z, N, n, cfg->b, h, j, sc);
     aggregate_kernel<<<(N + 255) / 256, 256, 0, s>>>(xyz, Z, N, n, cfg->b, h, C, sc);
-    c_fixed_to_double<<<(3 * n + 255) / 256, 256, 0, s>>>(C, n, N, sc);
   }
-  compact_nzj_kernel<<<3, 1024, 0, s>>>(C, n, nzj, sc);
+  compact_nzj_kernel<<<3, 1024, 0, s>>>(C, n, N, nzj, sc);
   fmatrix_kernel<<<dim3((L + 255) / 256, L), 256, 0, s>>>(pk64, R_l, L, F, nullptr);
   const int nt = (n + 31) / 32;
   gram_kernel<<<dim3(nt * (nt + 1) / 2, 3), 256, 0, s>>>(F, C, nzj, sc, n, G);

@@ -115,7 +115,7 @@ __global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n,
 // The weights C_l[j] = sum_{nu at j} w_nu^2 per grid coordinate (columns at equal shifts add in
 // U U^T) as 64-bit fixed-point sums with the scale 2^e, N max w^2 2^e < 2^61: integer additions
 // are exact, so C does not depend on the order of the atomics (a nonzero weight adds at least
-// one unit, so no charged coordinate drops out).  C holds the integers until c_fixed_to_double.
+// one unit, so no charged coordinate drops out).  C holds the integers until compact_nzj_kernel.
 __device__ __forceinline__ int c_fx_shift(const DevScalars* sc, int N) {
   const double wmax = __longlong_as_double((long long)sc->w2max_bits);
   const double B = (double)N * wmax;
@@ -136,13 +136,6 @@ __global__ void aggregate_kernel(const double* xyz, const double* Z, int N, int 
   const long long v = __double2ll_rn(ldexp(pow(fabs(z), 2.0 / 3.0), e));
   unsigned long long* Cfx = reinterpret_cast<unsigned long long*>(C);
   for (int l = 0; l < 3; ++l) atomicAdd(&Cfx[l * n + jj[l]], (unsigned long long)(v > 0 ? v : 1));
-}
-
-__global__ void c_fixed_to_double(double* C, int n, int N, const DevScalars* sc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 3 * n) return;
-  const int e = c_fx_shift(sc, N);
-  C[i] = ldexp((double)reinterpret_cast<const long long*>(C)[i], -e);
 }
 
 // Deterministic compaction of the particles with nonzero charge (one CTA, chunked scan).
@@ -182,14 +175,20 @@ __global__ void compact_nz_kernel(const double* Z, int N, int* nz_idx, DevScalar
 }
 
 // Distinct coordinates with nonzero aggregated weight, per mode (one CTA per mode).
-__global__ void compact_nzj_kernel(const double* C, int n, int* nzj, DevScalars* sc) {
+// The weights arrive as fixed-point integers (aggregate_kernel) and leave as FP64.
+__global__ void compact_nzj_kernel(double* C, int n, int N, int* nzj, DevScalars* sc) {
   __shared__ int scan[1024];
   const int l = blockIdx.x, T = blockDim.x, t = threadIdx.x;
-  const double* Cl = C + l * n;
+  double* Cl = C + l * n;
   const int per = (n + T - 1) / T;
   const int b0 = min(n, t * per), b1 = min(n, b0 + per);
+  const int e = c_fx_shift(sc, N);
   int cnt = 0;
-  for (int i = b0; i < b1; ++i) cnt += (Cl[i] > 0.0) ? 1 : 0;
+  for (int i = b0; i < b1; ++i) {
+    const double v = ldexp((double)reinterpret_cast<const long long*>(Cl)[i], -e);
+    Cl[i] = v;
+    cnt += (v > 0.0) ? 1 : 0;
+  }
   scan[t] = cnt;
   __syncthreads();
   for (int o = 1; o < T; o <<= 1) {
@@ -224,11 +223,10 @@ int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep) {
   if (N > 0) {
     prepare_kernel<<<(N + 255) / 256, 256, 0, c.stream>>>(c.xyz, c.Z, N, c.n, c.cfg.b, c.h, c.j, c.sc);
     aggregate_kernel<<<(N + 255) / 256, 256, 0, c.stream>>>(c.xyz, c.Z, N, c.n, c.cfg.b, c.h, c.C, c.sc);
-    c_fixed_to_double<<<(3 * c.n + 255) / 256, 256, 0, c.stream>>>(c.C, c.n, N, c.sc);
-    k += 3;
+    k += 2;
   }
   compact_nz_kernel<<<1, 1024, 0, c.stream>>>(c.Z, N, c.nz_idx, c.sc);
-  compact_nzj_kernel<<<3, 1024, 0, c.stream>>>(c.C, c.n, c.nzj, c.sc);
+  compact_nzj_kernel<<<3, 1024, 0, c.stream>>>(c.C, c.n, N, c.nzj, c.sc);
   if (check_sep && N > 1) {
     separation_kernel<<<(N + 127) / 128, 128, 0, c.stream>>>(c.xyz, N, min_sep * min_sep, c.sc);
     ++k;
