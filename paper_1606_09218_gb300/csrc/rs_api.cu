@@ -85,6 +85,7 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   const size_t nbins = (size_t)c.nbin * c.nbin * c.nbin;
   add(v, c.pk64, 8 * R * L);
   add(v, c.pk32, 4 * R * L);
+  add(v, c.pk32lo, 4 * R * L);
   add(v, c.dpk64, 8 * R * L);
   add(v, c.dpk32, 4 * R * L);
   add(v, c.xyz, 8 * 3 * N);

@@ -15,6 +15,7 @@
 
 #include <cstdio>
 #include <cstdlib>
+#include <utility>
 
 namespace rs {
 
@@ -931,7 +932,10 @@ static void congruence(Ctx& c, double* Tm, const double* Wm) {
 }
 
 // Rayleigh-Ritz refinement: two FP32 Jacobi passes on the graded T (rotations accumulated in
-// FP64), one rotation of the basis, one Newton-Schulz re-orthonormalisation.
+// FP64), one Newton-Schulz re-orthonormalisation of the accumulated rotation, one rotation of
+// the basis.  The basis Qa from the block Gram-Schmidt is orthonormal to working precision, so
+// the loss of orthogonality of Qa W1 W2 is that of W = W1 W2 (FP32 rotations): E = W^T W - I,
+// M = I - E/2 + 3/8 E^2, and the final basis is Qa (W M) — k x k products, one n x k product.
 static int refine(Ctx& c, double*& Qa, double*& Qb) {
   const int n = c.n, ks = c.ksub;
   const long long sQ = (long long)n * ks, sK = (long long)ks * ks;
@@ -940,25 +944,26 @@ static int refine(Ctx& c, double*& Qa, double*& Qb) {
   // pass 1: T -> W1^T T W1
   jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, 12, 1e-4f);
   congruence(c, c.T, c.W);
-  // pass 2: T -> W2^T T W2, W <- W1 W2
+  // pass 2: T -> W2^T T W2
   jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W2, ks, c.sc, 4, 2e-7f);
   congruence(c, c.T, c.W2);
+  // T2k = W = W1 W2 ; W2 = E = W^T W - I ; c.W = E^2 ; W2 = M
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W2, ks, sK, 0.0,
                        c.T2k, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
-  // Qb = Qa (W1 W2)
-  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, c.T2k, ks, sK, 0.0, Qb,
-                       ks, sQ, 3, 1, nullptr, ke, ke, &c.gscr);
-  // Newton-Schulz: E = Qb^T Qb - I ; M = I - E/2 + 3/8 E^2 ; Qa = Qb M ; T = M^T T M
-  gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, Qb, ks, sQ, Qb, ks, sQ, 0.0, c.W,
-                       ks, sK, 3, 1, ke, ke, nullptr, &c.gscr);
+  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.T2k, ks, sK, c.T2k, ks, sK, 0.0,
+                       c.W2, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
   dim3 g2((ks * ks + 255) / 256, 3);
-  sub_identity_kernel<<<g2, 256, 0, c.stream>>>(c.W, ks, c.sc);
-  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
-  ns_matrix_kernel<<<g2, 256, 0, c.stream>>>(c.W, c.T2k, c.W, ks, c.sc);
-  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qb, ks, sQ, c.W, ks, sK, 0.0, Qa,
+  sub_identity_kernel<<<g2, 256, 0, c.stream>>>(c.W2, ks, c.sc);
+  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W2, ks, sK, c.W2, ks, sK, 0.0,
+                       c.W, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
+  ns_matrix_kernel<<<g2, 256, 0, c.stream>>>(c.W2, c.W, c.W2, ks, c.sc);
+  // c.W = W M ; Qb = Qa (W M) ; T = M^T T M
+  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.T2k, ks, sK, c.W2, ks, sK, 0.0,
+                       c.W, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
+  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, c.W, ks, sK, 0.0, Qb,
                        ks, sQ, 3, 1, nullptr, ke, ke, &c.gscr);
-  congruence(c, c.T, c.W);
+  congruence(c, c.T, c.W2);
+  std::swap(Qa, Qb);
   return 2 + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1 + 1 + 2;
 }
 
@@ -989,13 +994,13 @@ int launch_subspace(Ctx& c) {
                        ks, sQ, 3, 4, nullptr, ke, nullptr, &c.gscr);
   gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, c.Q, ks, sQ, c.Y, ks, sQ, 0.0, c.T,
                        ks, sK, 3, 8, ke, ke, nullptr, &c.gscr);
-  // Rayleigh-Ritz refinement; the rotated basis goes through c.X and ends in c.Q
+  // Rayleigh-Ritz refinement; the rotated basis ends in c.X
   double* Qa = c.Q;
   double* Qb = c.X;
   int k = 6;
   if (dbg_steps <= 2) return k;
   k += refine(c, Qa, Qb);
-  // Qa holds the final basis (c.Q)
+  // Qa holds the final basis
   rank_select_kernel<<<3, 128, 0, c.stream>>>(c.T, ks, c.cfg.eps, c.cfg.rank_cap, c.rmax, c.order,
                                               c.ev, c.sc);
   long long totZ = 3ll * n * c.rmax;

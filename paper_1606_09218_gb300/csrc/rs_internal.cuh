@@ -95,6 +95,7 @@ struct Ctx {
   // device buffers
   double* pk64 = nullptr;   // R x L
   float*  pk32 = nullptr;   // R x L
+  float*  pk32lo = nullptr; // R x L: p_k - pk32 (FP32 pairs of the factors)
   double* dpk64 = nullptr;  // R x L: derivatives of the factors in the centre offset
   float*  dpk32 = nullptr;  // R x L
   double* xyz = nullptr;    // maxN x 3 (copy of host input)

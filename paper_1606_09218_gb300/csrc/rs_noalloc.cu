@@ -16,8 +16,8 @@
 
 namespace rs {
 // kernels of the setup stage (rs_setup.cu), launched here on scratch inside the static array
-__global__ void factors_kernel(double* pk64, float* pk32, double* dpk64, float* dpk32, int R, int n,
-                               double h, double hq, double u0);
+__global__ void factors_kernel(double* pk64, float* pk32, float* pk32lo, double* dpk64, float* dpk32, int R,
+                               int n, double h, double hq, double u0);
 __global__ void scalars_kernel(const double* pk64, int R, int R_l, int n, double delta_rel,
                                DevScalars* sc);
 __global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n, double b,
@@ -25,7 +25,7 @@ __global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n,
 __global__ void aggregate_kernel(const double* xyz, const double* Z, int N, int n, double b, double h,
                                  double* C, const DevScalars* sc);
 __global__ void compact_nzj_kernel(double* C, int n, int N, int* nzj, DevScalars* sc);
-__global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F, float2* F2);
+__global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F);
 __global__ void gram_kernel(const double* F, const double* C, const int* nzj,
                             const DevScalars* sc, int n, double* G);
 void set_host_error(const std::string& msg);
@@ -114,14 +114,14 @@ extern "C" rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* 
   cudaMemsetAsync(sc, 0, sizeof(DevScalars), s);
   cudaMemsetAsync(C, 0, sizeof(double) * 3 * (size_t)n, s);
   const int tot = R * L;
-  factors_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pk64, pk32, dpk64, dpk32, R, n, h, cfg->h_q, cfg->u0);
+  factors_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pk64, pk32, nullptr, dpk64, dpk32, R, n, h, cfg->h_q, cfg->u0);
   scalars_kernel<<<1, 256, 0, s>>>(pk64, R, R_l, n, cfg->delta_rel, sc);
   if (N > 0) {
     prepare_kernel<<<(N + 255) / 256, 256, 0, s>>>(xyz, Z, N, n, cfg->b, h, j, sc);
     aggregate_kernel<<<(N + 255) / 256, 256, 0, s>>>(xyz, Z, N, n, cfg->b, h, C, sc);
   }
   compact_nzj_kernel<<<3, 1024, 0, s>>>(C, n, N, nzj, sc);
-  fmatrix_kernel<<<dim3((L + 255) / 256, L), 256, 0, s>>>(pk64, R_l, L, F, nullptr);
+  fmatrix_kernel<<<dim3((L + 255) / 256, L), 256, 0, s>>>(pk64, R_l, L, F);
   const int nt = (n + 31) / 32;
   gram_kernel<<<dim3(nt * (nt + 1) / 2, 3), 256, 0, s>>>(F, C, nzj, sc, n, G);
   cudaError_t e = cudaGetLastError();

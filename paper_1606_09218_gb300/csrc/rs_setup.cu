@@ -11,8 +11,8 @@ namespace rs {
 // Laplace-Gauss transform of 1/z, Eqs. (2.6)-(2.8); Galerkin cell averages, Eq. (2.5)).
 // dp_k[d] = d/dc of p_k at the centre offset c = d*h: a_k^{1/3} (exp(-t_k^2 (c+h/2)^2) -
 // exp(-t_k^2 (c-h/2)^2)) / h (the cell average differentiated in its centre; adjoint forces).
-__global__ void factors_kernel(double* pk64, float* pk32, double* dpk64, float* dpk32, int R, int n,
-                               double h, double hq, double u0) {
+__global__ void factors_kernel(double* pk64, float* pk32, float* pk32lo, double* dpk64, float* dpk32, int R,
+                               int n, double h, double hq, double u0) {
   const int L = 2 * n - 1;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= R * L) return;
@@ -27,6 +27,7 @@ __global__ void factors_kernel(double* pk64, float* pk32, double* dpk64, float* 
   double v = ca * (0.88622692545275801 / (t * h)) * diff;   // sqrt(pi)/2
   pk64[e] = v;
   pk32[e] = (float)v;
+  if (pk32lo) pk32lo[e] = (float)(v - (double)(float)v);    // pk32 + pk32lo = p_k to 2^-48
   const double up = t * (cs + 0.5 * h), dn = t * (cs - 0.5 * h);
   const double dv = ca * (exp(-up * up) - exp(-dn * dn)) / h;
   dpk64[e] = dv;
@@ -74,8 +75,8 @@ __global__ void scalars_kernel(const double* pk64, int R, int R_l, int n, double
 
 int launch_factors(Ctx& c) {
   int tot = c.R * c.L;
-  factors_kernel<<<(tot + 255) / 256, 256, 0, c.stream>>>(c.pk64, c.pk32, c.dpk64, c.dpk32, c.R, c.n,
-                                                          c.h, c.cfg.h_q, c.cfg.u0);
+  factors_kernel<<<(tot + 255) / 256, 256, 0, c.stream>>>(c.pk64, c.pk32, c.pk32lo, c.dpk64, c.dpk32, c.R,
+                                                          c.n, c.h, c.cfg.h_q, c.cfg.u0);
   scalars_kernel<<<1, 256, 0, c.stream>>>(c.pk64, c.R, c.R_l, c.n, c.cfg.delta_rel, c.sc);
   return 2;
 }
@@ -235,26 +236,44 @@ int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep) {
 }
 
 // ------------------------------------------------------------------ F and Gram (a3, a4)
-// F[a][b] = sum_{k long} p_k[a] p_k[b] over the doubled index range (L x L, FP64), or, for the
-// double-float Gram, the same values as FP32 pairs (hi, lo) with hi + lo = F to 2^-48.
-__global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F, float2* F2) {
+// F[a][b] = sum_{k long} p_k[a] p_k[b] over the doubled index range (L x L, FP64).
+__global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   int a = blockIdx.y;
   if (b >= L) return;
   double v = 0.0;
   for (int k = 0; k < R_l; ++k) v += pk64[k * L + a] * pk64[k * L + b];
-  if (F2) {
-    const float hi = (float)v;
-    F2[(long long)a * L + b] = make_float2(hi, (float)(v - (double)hi));
-  } else {
-    F[(long long)a * L + b] = v;
+  F[(long long)a * L + b] = v;
+}
+
+// The same F for the double-float Gram, as FP32 pairs (hi, lo), from the factors as FP32 pairs:
+// each product p_k[a] p_k[b] as hi*hi plus its exact rounding error plus the two cross terms,
+// the R_l positive terms added by two-sums (relative error about 2^-46), no FP64 arithmetic.
+__global__ void fmatrix_df_kernel(const float* __restrict__ ph, const float* __restrict__ pl, int R_l, int L,
+                                  float2* F2) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  int a = blockIdx.y;
+  if (b >= L) return;
+  float s = 0.f, t = 0.f;
+  for (int k = 0; k < R_l; ++k) {
+    const float xa = ph[k * L + a], ya = pl[k * L + a], xb = ph[k * L + b], yb = pl[k * L + b];
+    const float p = __fmul_rn(xa, xb);
+    float e = fmaf(xa, xb, -p);
+    e = fmaf(xa, yb, e);
+    e = fmaf(ya, xb, e);
+    const float u = __fadd_rn(s, p);
+    const float z = __fsub_rn(u, s);
+    t = __fadd_rn(t, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(u, z)), __fsub_rn(p, z)), e));
+    s = u;
   }
+  const float hi = __fadd_rn(s, t);
+  F2[(long long)a * L + b] = make_float2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
 }
 
 static void launch_fmatrix(Ctx& c, bool split) {
   dim3 grid((c.L + 255) / 256, c.L);
-  fmatrix_kernel<<<grid, 256, 0, c.stream>>>(c.pk64, c.R_l, c.L, split ? nullptr : c.F,
-                                             split ? (float2*)c.F : nullptr);
+  if (split) fmatrix_df_kernel<<<grid, 256, 0, c.stream>>>(c.pk32, c.pk32lo, c.R_l, c.L, (float2*)c.F);
+  else fmatrix_kernel<<<grid, 256, 0, c.stream>>>(c.pk64, c.R_l, c.L, c.F);
 }
 
 // G_l[i][i'] = sum_j C_l[j] F[i - j + n - 1][i' - j + n - 1]  (= U^(l) U^(l)^T with the columns
