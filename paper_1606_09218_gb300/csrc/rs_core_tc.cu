@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) core_tc_kernel(CoreArgs g) {
   const float qmax = __uint_as_float(sc->qmax_bits), zmax = __uint_as_float(sc->zmax_bits);
   const int sA = (qmax > 0.f && zmax > 0.f) ? max(-100, min(100, 14 - exp2_above((double)zmax * qmax))) : 0;
   const int sB = (qmax > 0.f) ? max(-100, min(100, 14 - exp2_above((double)qmax * qmax))) : 0;
-  const int efx = beta_fx_shift(sc, g.R_l);            // fixed-point scale of the beta sums
+  const double pfx = ldexp(1.0, beta_fx_shift(sc, g.R_l));   // fixed-point scale of the beta sums
 
   if (tid == 0) {
     for (int s = 0; s < CT_STAGES; ++s) {
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) core_tc_kernel(CoreArgs g) {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
           if ((j >> 3) < nb && (j & 7) < nc)
-            atomicAdd(out + (j >> 3) * g.rmax + (j & 7), beta_fx(((double)hi[j] + (double)lo[j]) * unscale, efx));
+            atomicAdd(out + (j >> 3) * g.rmax + (j & 7), beta_fx(((double)hi[j] + (double)lo[j]) * unscale, pfx));
       }
     }
   }

@@ -244,8 +244,9 @@ __device__ __forceinline__ int beta_fx_shift(const DevScalars* sc, int R_l) {
   frexp(B, &E);                       // B < 2^E
   return max(-1000, min(1000, 61 - E));
 }
-__device__ __forceinline__ unsigned long long beta_fx(double v, int e) {
-  return (unsigned long long)__double2ll_rn(ldexp(v, e));
+// v 2^e as a 64-bit integer (pow2 = 2^e: the product is exact)
+__device__ __forceinline__ unsigned long long beta_fx(double v, double pow2) {
+  return (unsigned long long)__double2ll_rn(v * pow2);
 }
 
 // FP64 products with beta = 0 split K across CTAs deterministically through scr (partial tiles

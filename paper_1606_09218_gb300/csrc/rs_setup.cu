@@ -133,8 +133,7 @@ __global__ void aggregate_kernel(const double* xyz, const double* Z, int N, int 
   const double z = Z[p];
   int jj[3];
   if (!snap_particle(xyz, z, p, n, b, h, jj) || z == 0.0) return;
-  const int e = c_fx_shift(sc, N);
-  const long long v = __double2ll_rn(ldexp(pow(fabs(z), 2.0 / 3.0), e));
+  const long long v = __double2ll_rn(pow(fabs(z), 2.0 / 3.0) * ldexp(1.0, c_fx_shift(sc, N)));
   unsigned long long* Cfx = reinterpret_cast<unsigned long long*>(C);
   for (int l = 0; l < 3; ++l) atomicAdd(&Cfx[l * n + jj[l]], (unsigned long long)(v > 0 ? v : 1));
 }
@@ -183,10 +182,10 @@ __global__ void compact_nzj_kernel(double* C, int n, int N, int* nzj, DevScalars
   double* Cl = C + l * n;
   const int per = (n + T - 1) / T;
   const int b0 = min(n, t * per), b1 = min(n, b0 + per);
-  const int e = c_fx_shift(sc, N);
+  const double pinv = ldexp(1.0, -c_fx_shift(sc, N));
   int cnt = 0;
   for (int i = b0; i < b1; ++i) {
-    const double v = ldexp((double)reinterpret_cast<const long long*>(Cl)[i], -e);
+    const double v = (double)reinterpret_cast<const long long*>(Cl)[i] * pinv;
     Cl[i] = v;
     cnt += (v > 0.0) ? 1 : 0;
   }

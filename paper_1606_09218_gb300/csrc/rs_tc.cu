@@ -111,10 +111,19 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
   extern __shared__ __align__(16) float tsm[];
   float* T1s = tsm;                          // [8][rmax][32]
   float* V2s = tsm + 8 * rmax * 32;          // [32][rmax]
+  __shared__ float s_scale;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int t3 = blockIdx.x, i2b = blockIdx.y * TT_ROWS, i3 = t3 * AS_T3 + lane;
   const int r1 = sc->rank[0], r2 = sc->rank[1];
-  const float scale = ldexpf(1.0f, operand_shift(sc, r1) - 8);
+  if (warp == 0) {
+    // operand_shift(sc, r1), its maximum taken by one warp (the same exact maximum)
+    double m = 0.0;
+    for (int a = lane; a < r1; a += 32) m = fmax(m, sc->beta_a2[a]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_scale = ldexpf(1.0f, (m > 0.0 ? max(-100, min(100, 22 - exp2_above(sqrt(m)))) : 0) - 8);
+  }
+  __syncthreads();
+  const float scale = s_scale;
   const unsigned long long half_bytes = tile_bytes / 2;
   const long long np = (long long)n * n;
   if (blockIdx.x == 0 && blockIdx.y == 0) {
@@ -130,9 +139,9 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
       }
     }
   }
-  for (int e = tid; e < TT_ROWS * rmax; e += 256) {
-    const int r = e / rmax, b = e % rmax, i2 = i2b + r;
-    V2s[e] = (i2 < n && b < r2) ? V2[(long long)i2 * rmax + b] : 0.f;
+  for (int r = warp; r < TT_ROWS; r += 8) {
+    const int i2 = i2b + r;
+    for (int b = lane; b < rmax; b += 32) V2s[r * rmax + b] = (i2 < n && b < r2) ? V2[(long long)i2 * rmax + b] : 0.f;
   }
   for (int a0 = 0; a0 < kp; a0 += 8) {
     if (a0 >= r1) {
@@ -150,16 +159,18 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
       continue;
     }
     __syncthreads();
-    // asynchronous 4-byte copies (all in flight at once); zero fill outside the ranks / grid
-    for (int e = tid; e < 8 * r2 * AS_T3; e += 256) {
-      const int x = e / (r2 * AS_T3), rem = e % (r2 * AS_T3), b = rem / AS_T3, i3o = rem % AS_T3;
-      const int a = a0 + x, ii = t3 * AS_T3 + i3o;
-      const bool in = a < r1 && ii < n;
-      const float* src = in ? T1 + ((long long)a * rmax + b) * n + ii : T1;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
-                       smem_addr(&T1s[(x * rmax + b) * AS_T3 + i3o])),
-                   "l"(src), "r"(in ? 4 : 0)
-                   : "memory");
+    // asynchronous 4-byte copies (all in flight at once; warps over (rank, b) rows, lanes over
+    // i3); zero fill outside the ranks / grid
+    for (int x = 0; x < 8; ++x) {
+      const int a = a0 + x;
+      const bool in = a < r1 && i3 < n;
+      for (int b = warp; b < r2; b += 8) {
+        const float* src = in ? T1 + ((long long)a * rmax + b) * n + i3 : T1;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                         smem_addr(&T1s[(x * rmax + b) * AS_T3 + lane])),
+                     "l"(src), "r"(in ? 4 : 0)
+                     : "memory");
+      }
     }
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     __syncthreads();

@@ -220,7 +220,7 @@ core_kernel(const T* __restrict__ Qp, const int* __restrict__ jidx, const int* _
   }
   const int bb = b0 + tb;
   if (bb >= r2) return;
-  const int efx = beta_fx_shift(sc, R_l);
+  const double pfx = ldexp(1.0, beta_fx_shift(sc, R_l));
   unsigned long long* bfx = reinterpret_cast<unsigned long long*>(beta64);
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
@@ -230,7 +230,7 @@ core_kernel(const T* __restrict__ Qp, const int* __restrict__ jidx, const int* _
     for (int y = 0; y < 8; ++y) {
       const int cc = c0 + 8 * tc + y;
       if (cc < r3)
-        atomicAdd(&bfx[((long long)aa * rmax + bb) * rmax + cc], beta_fx((double)hi[x][y] + (double)lo[x][y], efx));
+        atomicAdd(&bfx[((long long)aa * rmax + bb) * rmax + cc], beta_fx((double)hi[x][y] + (double)lo[x][y], pfx));
     }
   }
 }
@@ -243,11 +243,11 @@ convert_beta_kernel(double* beta64, T* beta, int rmax, int R_l, DevScalars* sc) 
   __shared__ double red[8];
   const int a = blockIdx.x;
   const long long base = (long long)a * rmax * rmax;
-  const int efx = beta_fx_shift(sc, R_l);
+  const double pinv = ldexp(1.0, -beta_fx_shift(sc, R_l));
   long long* bfx = reinterpret_cast<long long*>(beta64);
   double s = 0.0;
   for (int e = threadIdx.x; e < rmax * rmax; e += blockDim.x) {
-    const double v = ldexp((double)bfx[base + e], -efx);
+    const double v = (double)bfx[base + e] * pinv;
     beta64[base + e] = v;
     beta[base + e] = (T)v;
     s += v * v;
