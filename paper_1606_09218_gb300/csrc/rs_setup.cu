@@ -379,33 +379,57 @@ gram_df_kernel(const float2* __restrict__ F2, const double* __restrict__ C, cons
       sw[threadIdx.x] = make_float2(wh, (float)(w - (double)wh));
     }
     __syncthreads();
-    int mm = min(256, cnt - m0);
-    for (int q = 0; q < mm; ++q) {
-      const int jv = sj[q];
-      const float2 w = sw[q];
-      const float2* Fr = F2 + (long long)(I0 + ty - jv + n - 1) * L + (ip - jv + n - 1);
+    const int mm = min(256, cnt - m0);
+    // one term w F into the pair (hs[r], ls[r])
+    auto add_term = [&](int r, float2 w, float2 f) {
+      const float p = __fmul_rn(w.x, f.x);
+      float e = fmaf(w.x, f.x, -p);                   // exact error of the rounded product
+      e = fmaf(w.x, f.y, e);
+      e = fmaf(w.y, f.x, e);
+      const float s = __fadd_rn(hs[r], p);            // two-sum: s + err = hs + p exactly
+      const float z = __fsub_rn(s, hs[r]);
+      const float err = __fadd_rn(__fsub_rn(hs[r], __fsub_rn(s, z)), __fsub_rn(p, z));
+      ls[r] = __fadd_rn(ls[r], __fadd_rn(err, e));
+      hs[r] = s;
+    };
+    auto renorm = [&]() {                             // fast two-sum, |hs| >= |ls|
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        if (!live[r]) continue;
-        const float2 f = Fr[(long long)(8 * r) * L];
-        const float p = __fmul_rn(w.x, f.x);
-        float e = fmaf(w.x, f.x, -p);                 // exact error of the rounded product
-        e = fmaf(w.x, f.y, e);
-        e = fmaf(w.y, f.x, e);
-        const float s = __fadd_rn(hs[r], p);          // two-sum: s + err = hs + p exactly
-        const float z = __fsub_rn(s, hs[r]);
-        const float err = __fadd_rn(__fsub_rn(hs[r], __fsub_rn(s, z)), __fsub_rn(p, z));
-        ls[r] = __fadd_rn(ls[r], __fadd_rn(err, e));
+        const float s = __fadd_rn(hs[r], ls[r]);
+        ls[r] = __fsub_rn(ls[r], __fsub_rn(s, hs[r]));
         hs[r] = s;
       }
-      if ((q & 15) == 15) {
+    };
+    auto row_ptr = [&](int jv) {
+      return F2 + (long long)(I0 + ty - jv + n - 1) * L + (ip - jv + n - 1);
+    };
+    // four coordinates at a time: their 16 loads are issued before the sums (the order of the
+    // additions, and the renormalisation every 16 terms, are those of one term at a time)
+    int q = 0;
+    for (; q + 4 <= mm; q += 4) {
+      float2 f[4][4], w4[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {                // fast two-sum, |hs| >= |ls|
-          const float s = __fadd_rn(hs[r], ls[r]);
-          ls[r] = __fsub_rn(ls[r], __fsub_rn(s, hs[r]));
-          hs[r] = s;
-        }
+      for (int u = 0; u < 4; ++u) {
+        w4[u] = sw[q + u];
+        const float2* Fr = row_ptr(sj[q + u]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) f[u][r] = live[r] ? Fr[(long long)(8 * r) * L] : make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (live[r]) add_term(r, w4[u], f[u][r]);
+        if (((q + u) & 15) == 15) renorm();
+      }
+    }
+    for (; q < mm; ++q) {
+      const float2 w = sw[q];
+      const float2* Fr = row_ptr(sj[q]);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (live[r]) add_term(r, w, Fr[(long long)(8 * r) * L]);
+      if ((q & 15) == 15) renorm();
     }
     __syncthreads();
   }
