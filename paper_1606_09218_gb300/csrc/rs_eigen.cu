@@ -588,25 +588,41 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
         sq(ii, kq + jc) = Xl[(long long)(r0 + ii) * ks + s + jc];
       }
     __syncthreads();   // the partial products below read rows written by other threads
-    // (A) first projection against the accepted columns, (B) the second
-    for (int pass = 0; pass < 2; ++pass) {
-      if (kq > 0) {
-        partial_h(pbuf(phase, l, c));
-        mode_barrier(sc, l, bar_gen, poisoned);
-        reduce_slice(phase, 0, kq * KB);
-        mode_barrier(sc, l, bar_gen, poisoned);
-        fetch(phase, 0, kq * KB, h);
-        __syncthreads();
-        subtract_Qh();
-      }
-      ++phase;
+    // (A) first projection against the accepted columns
+    if (kq > 0) {
+      partial_h(pbuf(phase, l, c));
+      mode_barrier(sc, l, bar_gen, poisoned);
+      reduce_slice(phase, 0, kq * KB);
+      mode_barrier(sc, l, bar_gen, poisoned);
+      fetch(phase, 0, kq * KB, h);
+      __syncthreads();
+      subtract_Qh();
+    }
+    ++phase;
+    // (B) second projection and (C) the Gram of the block from one reduction, as in (D):
+    //     h = Q^T B, S = B^T B, B <- B - Q h, S <- S - h^T h (after (A) h is small, so the
+    //     difference loses nothing); then the norm test and the first Cholesky QR.  Without
+    //     accepted columns S alone, summed by every CTA after one barrier.
+    if (kq > 0) {
+      double* P = pbuf(phase, l, c);
+      partial_h(P);
+      partial_S(P + (long long)ks * KB);
+      mode_barrier(sc, l, bar_gen, poisoned);
+      reduce_slice(phase, 0, kq * KB);
+      reduce_slice(phase, (long long)ks * KB, KB * KB);
+      mode_barrier(sc, l, bar_gen, poisoned);
+      fetch(phase, 0, kq * KB, h);
+      fetch(phase, (long long)ks * KB, KB * KB, S);
+      __syncthreads();
+      subtract_hth();
+      subtract_Qh();
+    } else {
+      partial_S(pbuf(phase, l, c));
+      mode_barrier(sc, l, bar_gen, poisoned);
+      reduce_S(phase, 0);
     }
     block_to_global();                       // CTA 0 reads every row if the block falls back
-    // (C) Gram of the block: norm test and first Cholesky QR
-    partial_S(pbuf(phase, l, c));
-    mode_barrier(sc, l, bar_gen, poisoned);
     {
-      reduce_S(phase, 0);
       __syncthreads();
       if (tid < 32) {
         double tr = 0.0;
@@ -619,6 +635,9 @@ bcgs2_kernel(const double* __restrict__ X, double* Q, double* part, int n, int k
       if (s_stop == 1) mark_stop(0u);
       else if (s_stop == 3) {
         fallback = true;
+        // the same decision in every CTA of the mode: one more barrier, so that CTA 0 sees every
+        // CTA's rows of the block in global memory
+        mode_barrier(sc, l, bar_gen, poisoned);
         if (c == 0) {
           if (tid == 0) atomicAdd(&sc->fallbacks, 1);
           fallback_block();
