@@ -350,7 +350,7 @@ def run_ours(args, rank, world, local_rank):
     ach = bytes_alg / (per_launch_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": ach / pk["hbm_gbs"],
-            "kernel": "assemble_kernel (tcgen05: FP16-split Tucker product + TF32-split windows, one pass)",
+            "kernel": "assemble_kernel (tcgen05 kind::f16: FP16-split Tucker product and windows, one pass)",
             "traffic": NCU_TRAFFIC.get(kernel_hash()) if args.workload == DEFAULT_WORKLOAD else None,
             "traffic_unit": "bytes per launch (ncu dram read + write)",
             "peak_source": pk["source"] + " hbm_gbs (copy, burst)",
