@@ -350,6 +350,50 @@ def rs_tucker_full(beta, Vs, j, z, pk, kshort, gamma, n):
 
 
 # ----------------------------------------------------------------------------
+# Tucker-to-canonical transform: the RS-canonical format  (Def. 3.7, Lemma 3.8)
+# ----------------------------------------------------------------------------
+def tucker_to_canonical(beta, Vs, eps: float):
+    """Canonical form of the Tucker tensor beta x_1 V^(1) x_2 V^(2) x_3 V^(3), the long-range
+    part of an RS-canonical tensor (Def. 3.7).  Sec. 3 reports RS-canonical ranks after a
+    Tucker-to-canonical step at a given accuracy but does not state the algorithm.  Reading:
+    the singular value decomposition of every mode-1 slice of the core,
+    beta[a, :, :] = sum_m s_{a,m} x_{a,m} y_{a,m}^T; all (a, m) terms are ordered by s^2 and
+    the smallest are discarded while their squared sum stays <= eps^2 ||beta||_F^2; every kept
+    term is the rank-1 tensor s (V^(1) e_a) x (V^(2) x_{a,m}) x (V^(3) y_{a,m}).  With
+    orthonormal V^(l) the Frobenius error is exactly sqrt(discarded) <= eps ||beta||_F.
+    Returns (xi (R*), [U1, U2, U3] (n x R*), kept (a, m) pairs, discarded squared sum)."""
+    beta = np.asarray(beta, dtype=np.float64)
+    r1 = beta.shape[0]
+    svd = [np.linalg.svd(beta[a], full_matrices=False) for a in range(r1)]
+    terms = [(a, m, float(svd[a][1][m])) for a in range(r1) for m in range(len(svd[a][1]))]
+    s2 = np.array([t[2] ** 2 for t in terms])
+    budget = eps * eps * float(np.sum(beta * beta))
+    order = np.argsort(s2, kind="stable")
+    csum = np.cumsum(s2[order])
+    ndisc = int(np.searchsorted(csum, budget, side="right"))
+    drop = np.zeros(len(terms), dtype=bool)
+    drop[order[:ndisc]] = True
+    kept = [(a, m) for (a, m, _), d in zip(terms, drop) if not d]
+    xi = np.array([svd[a][1][m] for a, m in kept])
+    U1 = np.stack([Vs[0][:, a] for a, m in kept], axis=1) if kept else np.zeros((Vs[0].shape[0], 0))
+    U2 = np.stack([Vs[1] @ svd[a][0][:, m] for a, m in kept], axis=1) if kept else np.zeros((Vs[1].shape[0], 0))
+    U3 = np.stack([Vs[2] @ svd[a][2][m, :] for a, m in kept], axis=1) if kept else np.zeros((Vs[2].shape[0], 0))
+    return xi, [U1, U2, U3], kept, float(csum[ndisc - 1]) if ndisc else 0.0
+
+
+def canonical_full(xi, Us):
+    """sum_k xi_k u_k^(1) x u_k^(2) x u_k^(3) on the full grid (first term of Eq. (3.10))."""
+    return np.einsum("k,ik,jk,lk->ijl", xi, Us[0], Us[1], Us[2], optimize=True)
+
+
+def canonical_points(xi, Us, idx_pts):
+    """Entries of the canonical tensor at grid multi-indices: the Hadamard product of the rows
+    of the three side matrices times xi (Lemma 3.8, first term)."""
+    idx_pts = np.asarray(idx_pts, dtype=np.int64)
+    return (Us[0][idx_pts[:, 0]] * Us[1][idx_pts[:, 1]] * Us[2][idx_pts[:, 2]]) @ xi
+
+
+# ----------------------------------------------------------------------------
 # Energy and forces  (Sec. 4.2, Sec. 4.3)
 # ----------------------------------------------------------------------------
 def energy_direct(xyz, z):

@@ -509,3 +509,66 @@ def test_direct_long_forces_equal_galerkin_up_to_window_cut():
     F = pr.forces_galerkin()
     Fd = pr.forces_direct_long()
     assert np.linalg.norm(Fd - F) / np.linalg.norm(F) <= 1e-7
+
+
+# ---------------------------------------------------------------- Def. 3.7, Lemma 3.8: Tucker-to-canonical
+def _random_tucker(rng, n, ranks):
+    Vs = [np.linalg.qr(rng.standard_normal((n, r)))[0] for r in ranks]
+    # a graded core (decaying slices and singular values), like an RHOSVD core
+    beta = rng.standard_normal(ranks) * np.exp(-0.7 * np.add.outer(np.add.outer(
+        np.arange(ranks[0]), np.arange(ranks[1])), np.arange(ranks[2])))
+    return beta, Vs
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-6, 1e-3, 0.1])
+def test_tucker_to_canonical_error_is_the_discarded_energy(eps):
+    """Brute force on a 13^3 grid: ||T - C||_F^2 equals the discarded squared singular values,
+    which stay within eps^2 ||T||_F^2, and discarding the smallest kept term would exceed it
+    (the budget is used up); eps = 0 reproduces T exactly."""
+    rng = np.random.default_rng(11)
+    beta, Vs = _random_tucker(rng, 13, (5, 6, 4))
+    xi, Us, kept, disc = O.tucker_to_canonical(beta, Vs, eps)
+    T = np.einsum("abc,ia,jb,kc->ijk", beta, *Vs)          # full tensors, written out here
+    C = sum(xi[k] * np.einsum("i,j,l->ijl", Us[0][:, k], Us[1][:, k], Us[2][:, k]) for k in range(len(xi)))
+    C = np.asarray(C) if len(xi) else np.zeros_like(T)
+    err2 = float(np.sum((T - C) ** 2))
+    nT2 = float(np.sum(T * T))
+    assert abs(err2 - disc) <= 1e-12 * nT2
+    assert err2 <= eps * eps * nT2 * (1 + 1e-12) + 1e-28
+    if eps == 0.0:
+        assert np.abs(T - C).max() <= 1e-13 * np.abs(T).max()
+        assert len(kept) == 5 * 4
+    elif len(xi):
+        assert disc + float(np.min(xi)) ** 2 > eps * eps * nT2
+
+
+def test_tucker_to_canonical_known_rank():
+    """A core that is a sum of three rank-1 terms in distinct mode-1 slices has RS-canonical
+    rank 3 at any small eps, and its terms are recovered up to sign."""
+    rng = np.random.default_rng(12)
+    n = 9
+    Vs = [np.linalg.qr(rng.standard_normal((n, r)))[0] for r in (4, 5, 5)]
+    beta = np.zeros((4, 5, 5))
+    lam = [3.0, -1.5, 0.25]
+    for a, l in zip([0, 2, 3], lam):
+        x, y = rng.standard_normal(5), rng.standard_normal(5)
+        beta[a] += l * np.outer(x / np.linalg.norm(x), y / np.linalg.norm(y))
+    xi, Us, kept, disc = O.tucker_to_canonical(beta, Vs, 1e-8)
+    assert len(xi) == 3 and sorted(a for a, _ in kept) == [0, 2, 3]
+    assert np.allclose(sorted(xi), sorted(abs(l) for l in lam))
+    assert disc <= 1e-20
+
+
+def test_canonical_points_match_full_tensor():
+    """Lemma 3.8 (first term): the entry at i is the Hadamard product of the side-matrix rows
+    times xi — against the full canonical tensor and against the Tucker tensor within the
+    discarded energy."""
+    rng = np.random.default_rng(13)
+    beta, Vs = _random_tucker(rng, 11, (4, 4, 5))
+    xi, Us, kept, disc = O.tucker_to_canonical(beta, Vs, 1e-4)
+    C = O.canonical_full(xi, Us)
+    idx = rng.integers(0, 11, (200, 3))
+    v = O.canonical_points(xi, Us, idx)
+    assert np.allclose(v, C[idx[:, 0], idx[:, 1], idx[:, 2]], rtol=0, atol=1e-14 * np.abs(C).max())
+    T = O.tucker_points(beta, Vs, idx)
+    assert np.abs(v - T).max() <= math.sqrt(disc) + 1e-14
