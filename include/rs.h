@@ -152,6 +152,31 @@ rs_status rs_get_tucker(rs_ctx* ctx, int ranks[3], int* ld_V, int* ld_b,
  * idx: device int32 array (M x 3), out: device double array (M).  Asynchronous. */
 rs_status rs_eval_points(rs_ctx* ctx, int M, const int* idx, double* out);
 
+/* RS-canonical form (Def. 3.7) of the last solve: its long-range Tucker part converted to a
+ * canonical tensor sum_k xi_k u1_k (x) u2_k (x) u3_k by the singular value decomposition of every
+ * mode-1 slice of the core, beta[a,:,:] = sum_m s x y^T (FP64 one-sided Jacobi, one CTA per
+ * slice), with the smallest s^2 discarded while their sum stays <= eps^2 ||beta||_F^2 and
+ * u1 = V1[:, a], u2 = V2 x, u3 = V3 y, xi = s for the rest (the Frobenius error of the long part
+ * is then at most eps ||beta||_F = eps ||P_l^T||_F).  Sec. 3 reports RS-canonical ranks after
+ * such a Tucker-to-canonical step; the slice SVD is this library's reading of its algorithm.
+ * eps >= 0; *rank receives R*.  The first call allocates the form's device memory
+ * (3 n r1 r3 + O(rmax^3) doubles), kept until rs_destroy.  Ranks above RS_CANONICAL_RMAX or
+ * r1 r3 above RS_CANONICAL_TERMS give RS_ERR_CAPACITY; before a solve RS_ERR_NOT_READY.
+ * Synchronises.  The form is valid until the next rs_solve. */
+#define RS_CANONICAL_RMAX 112
+#define RS_CANONICAL_TERMS 16384
+rs_status rs_canonical(rs_ctx* ctx, double eps, int* rank);
+
+/* Point values of the RS-canonical tensor (Lemma 3.8): the canonical long part at M grid
+ * multi-indices (3 R* products each) plus the windows of the neighbours.  idx: device int32
+ * (M x 3, clamped to the grid), out: device double (M).  Needs rs_canonical after the last
+ * solve (else RS_ERR_NOT_READY).  Asynchronous. */
+rs_status rs_canonical_eval_points(rs_ctx* ctx, int M, const int* idx, double* out);
+
+/* Device pointers to the RS-canonical form (valid until the next rs_solve or rs_canonical):
+ * xi (R*), U: three side matrices, U[(l*n + i)*ld + k] for mode l, grid index i, term k < R*. */
+rs_status rs_get_canonical(rs_ctx* ctx, int* rank, const double** xi, const double** U, int* ld);
+
 /* Stage timing (tracing): with enable != 0, each rs_solve records one CUDA event per stage
  * boundary on the context stream (ring of 512 solves).  Errors: RS_ERR_CUDA. */
 rs_status rs_profile_enable(rs_ctx* ctx, int enable);

@@ -226,6 +226,32 @@ class RSContext:
         raw = torch.as_tensor(_DevArray(ptr.value, (nb.value,), "|u1"), device="cuda")
         return raw if dtype is None else raw.view(dtype)
 
+    def canonical(self, eps: float) -> int:
+        """RS-canonical form of the last solve (Def. 3.7): Tucker-to-canonical transform of the
+        long part at accuracy ``eps`` (slice SVD of the core); returns the canonical rank R*."""
+        r = C.c_int()
+        _lib.check(self.lib.rs_canonical(self.h, float(eps), C.byref(r)), self.h)
+        return int(r.value)
+
+    def canonical_eval_points(self, idx):
+        """RS-canonical entries (Lemma 3.8) at grid multi-indices idx (M,3) int32 CUDA tensor."""
+        torch = self._torch
+        idx = idx.to(device="cuda", dtype=torch.int32).contiguous()
+        out = torch.empty(idx.shape[0], dtype=torch.float64, device="cuda")
+        _lib.check(self.lib.rs_canonical_eval_points(self.h, int(idx.shape[0]), C.c_void_p(idx.data_ptr()),
+                                                     C.c_void_p(out.data_ptr())), self.h)
+        return out
+
+    def get_canonical(self):
+        """(xi (R*,), [U1, U2, U3] (n, R*)) float64 CUDA views of the RS-canonical form."""
+        torch = self._torch
+        r, xi, U, ld = C.c_int(), C.c_void_p(), C.c_void_p(), C.c_int()
+        _lib.check(self.lib.rs_get_canonical(self.h, C.byref(r), C.byref(xi), C.byref(U), C.byref(ld)), self.h)
+        R, n, L = int(r.value), self.n, int(ld.value)
+        xi_t = torch.as_tensor(_DevArray(xi.value, (max(R, 1),), "<f8"), device="cuda")[:R]
+        Uall = torch.as_tensor(_DevArray(U.value, (3 * n * L,), "<f8"), device="cuda").view(3, n, L)[:, :, :R]
+        return xi_t, [Uall[0], Uall[1], Uall[2]]
+
     def eval_points(self, idx):
         """RS-Tucker entries (Lemma 3.10) at grid multi-indices idx (M,3) int32 CUDA tensor."""
         torch = self._torch

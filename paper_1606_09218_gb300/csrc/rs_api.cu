@@ -149,6 +149,16 @@ void free_profile(Ctx& c) {
   c.prof_count = 0;
 }
 
+void free_canonical(Ctx& c) {
+  for (void* p : {(void*)c.cn_sig, (void*)c.cn_X, (void*)c.cn_Y, (void*)c.cn_kept, (void*)c.cn_count, (void*)c.cn_U,
+                  (void*)c.cn_xi})
+    if (p) cudaFree(p);
+  c.cn_sig = c.cn_X = c.cn_Y = c.cn_U = c.cn_xi = nullptr;
+  c.cn_kept = c.cn_count = nullptr;
+  c.cn_cap = 0;
+  c.cn_rank = -1;
+}
+
 void free_all(Ctx& c) {
   free_profile(c);
   auto v = buffer_list(c);
@@ -158,6 +168,7 @@ void free_all(Ctx& c) {
   }
   if (c.h_sc) cudaFreeHost(c.h_sc);
   c.h_sc = nullptr;
+  free_canonical(c);
   if (c.ev_part) cudaEventDestroy(c.ev_part);
   if (c.ev_bins) cudaEventDestroy(c.ev_bins);
   if (c.ev_side) cudaEventDestroy(c.ev_side);
@@ -242,6 +253,7 @@ bool ensure_kernel_attributes(std::string& err) {
   if (e == cudaSuccess) e = set_attributes_tc(optin);
   if (e == cudaSuccess) e = set_attributes_core(optin);
   if (e == cudaSuccess) e = set_attributes_plain(optin);
+  if (e == cudaSuccess) e = set_attributes_canonical(optin);
   if (e != cudaSuccess) {
     err = std::string("kernel attributes: ") + cudaGetErrorString(e);
     cudaGetLastError();
@@ -364,6 +376,7 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   if (!h) return RS_ERR_INVALID_ARG;
   Ctx& c = h->c;
   c.solved = false;
+  c.cn_rank = -1;
   if (N < 0) return fail(c, RS_ERR_INVALID_ARG, "N must be >= 0");
   if (N > c.maxN) return fail(c, RS_ERR_CAPACITY, "N above max_particles of this context");
   if (N > 0 && (!xyz || !Z)) return fail(c, RS_ERR_INVALID_ARG, "null particle arrays");
@@ -523,6 +536,82 @@ rs_status rs_eval_points(rs_ctx* h, int M, const int* idx, double* out) {
   if (M < 0 || (M > 0 && (!idx || !out))) return fail(c, RS_ERR_INVALID_ARG, "bad point list");
   launch_eval_points(c, M, idx, out);
   return check_launch(c, "eval_points");
+}
+
+rs_status rs_canonical(rs_ctx* h, double eps, int* rank) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!rank || !(eps >= 0.0) || !std::isfinite(eps)) return fail(c, RS_ERR_INVALID_ARG, "rank pointer and eps >= 0");
+  if (!c.solved) return fail(c, RS_ERR_NOT_READY, "no solve");
+  int rk[3] = {0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(rk, c.sc->rank, sizeof(rk), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, RS_ERR_CUDA, std::string("canonical: ") + cudaGetErrorString(e));
+  }
+  const int r1 = rk[0], r2 = rk[1], r3 = rk[2];
+  const int rm = r2 > r3 ? r2 : r3;
+  const long long M = (long long)r1 * r3;
+  if (rm > RS_CANONICAL_RMAX || M > RS_CANONICAL_TERMS)
+    return fail(c, RS_ERR_CAPACITY, "canonical: Tucker ranks above the slice-SVD limits (112, 16384 terms)");
+  const int cap = (int)(M > 0 ? M : 1);
+  if (cap > c.cn_cap) {
+    free_canonical(c);
+    const size_t rmx = (size_t)c.rmax;
+    const size_t need[7] = {8 * rmx * rmx, 8 * rmx * rmx * rmx, 8 * rmx * rmx * rmx, 4 * (size_t)cap, 4,
+                            8 * 3 * (size_t)c.n * cap, 8 * (size_t)cap};
+    void** dst[7] = {(void**)&c.cn_sig, (void**)&c.cn_X, (void**)&c.cn_Y, (void**)&c.cn_kept, (void**)&c.cn_count,
+                     (void**)&c.cn_U, (void**)&c.cn_xi};
+    for (int i = 0; i < 7; ++i) {
+      if (cudaMalloc(dst[i], need[i]) != cudaSuccess) {
+        cudaGetLastError();
+        free_canonical(c);
+        return fail(c, RS_ERR_OOM, "canonical: device allocation failed");
+      }
+    }
+    c.cn_cap = cap;
+  }
+  if (M == 0) {
+    cudaMemsetAsync(c.cn_count, 0, sizeof(int), c.stream);
+  } else {
+    int P = 1;
+    while (P < M) P <<= 1;
+    launch_canonical(c, eps, r1, r2, r3, P);
+  }
+  rs_status st = check_launch(c, "canonical");
+  if (st != RS_OK) return st;
+  int cnt = 0;
+  e = cudaMemcpyAsync(&cnt, c.cn_count, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, RS_ERR_CUDA, std::string("canonical: ") + cudaGetErrorString(e));
+  }
+  c.cn_rank = cnt;
+  *rank = cnt;
+  return RS_OK;
+}
+
+rs_status rs_canonical_eval_points(rs_ctx* h, int M, const int* idx, double* out) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.solved || c.cn_rank < 0) return fail(c, RS_ERR_NOT_READY, "no canonical form of the current solve");
+  if (M < 0 || (M > 0 && (!idx || !out))) return fail(c, RS_ERR_INVALID_ARG, "bad point list");
+  launch_canonical_eval(c, M, idx, out);
+  return check_launch(c, "canonical_eval_points");
+}
+
+rs_status rs_get_canonical(rs_ctx* h, int* rank, const double** xi, const double** U, int* ld) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!rank || !xi || !U || !ld) return fail(c, RS_ERR_INVALID_ARG, "null output");
+  if (!c.solved || c.cn_rank < 0) return fail(c, RS_ERR_NOT_READY, "no canonical form of the current solve");
+  *rank = c.cn_rank;
+  *xi = c.cn_xi;
+  *U = c.cn_U;
+  *ld = c.cn_cap;
+  return RS_OK;
 }
 
 rs_status rs_profile_enable(rs_ctx* h, int enable) {

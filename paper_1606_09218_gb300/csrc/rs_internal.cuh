@@ -79,6 +79,16 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t aux = nullptr;    // window lists and particle bins, overlapped with the eigen stage
   GemmScratch gscr;              // deterministic K split of the FP64 products
+  // RS-canonical form of the last solve (allocated by the first rs_canonical call)
+  double* cn_sig = nullptr;      // rmax x rmax singular values of the core slices
+  double* cn_X = nullptr;        // rmax^3: left singular vectors per (slice, term)
+  double* cn_Y = nullptr;        // rmax^3: right singular vectors per (slice, term)
+  int* cn_kept = nullptr;        // kept terms a * r3 + c
+  int* cn_count = nullptr;       // R* (device)
+  double* cn_U = nullptr;        // 3 x n x cn_cap side matrices (row length cn_cap)
+  double* cn_xi = nullptr;       // cn_cap weights
+  int cn_cap = 0;                // capacity in terms
+  int cn_rank = -1;              // R* of the current solve, -1 before rs_canonical
   cudaEvent_t ev_part = nullptr, ev_bins = nullptr, ev_side = nullptr;
   int n = 0, R = 0, R_l = 0, R_s = 0, L = 0;   // L = 2n - 1
   int ksub = 0;        // subspace width (multiple of KB)
@@ -177,6 +187,34 @@ struct DevView {
   const int* nz_idx;
 };
 
+// Short-range windows at grid point (i1, i2, i3): adds this lane's share of
+// sum_{nu in L(i)} z_nu U_nu(i) to v (Lemma 3.10 and Lemma 3.8, second term), FP64 factors; the
+// lanes of a warp take the particle bins around the point in turn.
+__device__ __forceinline__ void window_add(const DevView& c, int i1, int i2, int i3, int lane, double& v) {
+  const int n = c.n;
+  const int g = c.sc->gamma, L = 2 * n - 1, nb = c.nbin;
+  const int b1a = max(0, i1 - g) / BIN, b1b = min(n - 1, i1 + g) / BIN;
+  const int b2a = max(0, i2 - g) / BIN, b2b = min(n - 1, i2 + g) / BIN;
+  const int b3a = max(0, i3 - g) / BIN, b3b = min(n - 1, i3 + g) / BIN;
+  const int nb3 = b3b - b3a + 1, nb2 = b2b - b2a + 1;
+  const int nbt = (b1b - b1a + 1) * nb2 * nb3;
+  for (int t = lane; t < nbt; t += 32) {
+    const int b3 = b3a + t % nb3, b2 = b2a + (t / nb3) % nb2, b1 = b1a + t / (nb3 * nb2);
+    const int b = (b1 * nb + b2) * nb + b3;
+    for (int it = c.bin_start[b]; it < c.bin_start[b + 1]; ++it) {
+      const int q = c.bin_items[it];
+      const int d1 = i1 - c.j[3 * q], d2 = i2 - c.j[3 * q + 1], d3 = i3 - c.j[3 * q + 2];
+      if (abs(d1) > g || abs(d2) > g || abs(d3) > g) continue;
+      double s = 0.0;
+      for (int k = c.R_l; k < c.R; ++k) {
+        const double* row = c.pk64 + (long long)k * L + n - 1;
+        s += row[d1] * row[d2] * row[d3];
+      }
+      v += c.Z[q] * s;
+    }
+  }
+}
+
 inline DevView make_view(const Ctx& c) {
   DevView v;
   v.n = c.n; v.rmax = c.rmax; v.R = c.R; v.R_l = c.R_l; v.nbin = c.nbin;
@@ -223,6 +261,11 @@ cudaError_t set_attributes_tc(int optin);
 cudaError_t set_attributes_core(int optin);
 int launch_core_tc(Ctx& c);
 int launch_energy_t2(Ctx& c, double* part, int blocks);
+int launch_canonical(Ctx& c, double eps, int r1, int r2, int r3, int P);
+int launch_canonical_eval(Ctx& c, int M, const int* idx, double* out);
+size_t canonical_svd_smem(int r);
+size_t canonical_select_smem(int P);
+cudaError_t set_attributes_canonical(int optin);
 cudaError_t set_attributes_plain(int optin);
 rs_status launch_plain(Ctx& c, int which, float* out);
 rs_status launch_pair_energy_forces(Ctx& c, int N, const double* xyz, const double* Z, double* E, double* F);

@@ -582,28 +582,7 @@ __device__ double rs_point_value(const DevView& c, const T* Zb, const T* T1, int
     double t1 = (double)T1[((long long)a * rmax + b) * n + i3];
     v += (double)Zb[(long long)i1 * rmax + a] * (double)Zb[sZ + (long long)i2 * rmax + b] * t1;
   }
-  // short-range windows (FP64 factors)
-  const int g = c.sc->gamma, L = 2 * n - 1, nb = c.nbin;
-  const int b1a = max(0, i1 - g) / BIN, b1b = min(n - 1, i1 + g) / BIN;
-  const int b2a = max(0, i2 - g) / BIN, b2b = min(n - 1, i2 + g) / BIN;
-  const int b3a = max(0, i3 - g) / BIN, b3b = min(n - 1, i3 + g) / BIN;
-  const int nb3 = b3b - b3a + 1, nb2 = b2b - b2a + 1;
-  const int nbt = (b1b - b1a + 1) * nb2 * nb3;
-  for (int t = lane; t < nbt; t += 32) {
-    int b3 = b3a + t % nb3, b2 = b2a + (t / nb3) % nb2, b1 = b1a + t / (nb3 * nb2);
-    int b = (b1 * nb + b2) * nb + b3;
-    for (int it = c.bin_start[b]; it < c.bin_start[b + 1]; ++it) {
-      int p = c.bin_items[it];
-      int d1 = i1 - c.j[3 * p], d2 = i2 - c.j[3 * p + 1], d3 = i3 - c.j[3 * p + 2];
-      if (abs(d1) > g || abs(d2) > g || abs(d3) > g) continue;
-      double s = 0.0;
-      for (int k = c.R_l; k < c.R; ++k) {
-        const double* row = c.pk64 + (long long)k * L + n - 1;
-        s += row[d1] * row[d2] * row[d3];
-      }
-      v += c.Z[p] * s;
-    }
-  }
+  window_add(c, i1, i2, i3, lane, v);      // short-range windows (FP64 factors)
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;     // valid in lane 0
 }
