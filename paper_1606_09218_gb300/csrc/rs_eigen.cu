@@ -1002,12 +1002,6 @@ int launch_subspace(Ctx& c) {
     cudaLaunchCooperativeKernel((void*)bcgs2_kernel, dim3(3 * NBC), dim3(256), args, shm, c.stream);
   }
   const int* ke = c.sc->k_eff;
-  // RS_DEBUG_SUBSPACE_STEPS=s stops the eigen stage after s sub-steps (inspection only)
-  static const int dbg_steps = [] {
-    const char* e = std::getenv("RS_DEBUG_SUBSPACE_STEPS");
-    return e ? std::atoi(e) : 99;
-  }();
-  if (dbg_steps <= 1) return 5;
   // Y = G Q ; T = Q^T Y
   gemm_batched<double>(c.stream, false, false, n, ks, n, 1.0, c.G, n, sG, c.Q, ks, sQ, 0.0, c.Y,
                        ks, sQ, 3, 4, nullptr, ke, nullptr, &c.gscr);
@@ -1016,8 +1010,7 @@ int launch_subspace(Ctx& c) {
   // Rayleigh-Ritz refinement; the rotated basis ends in c.X
   double* Qa = c.Q;
   double* Qb = c.X;
-  int k = 6;
-  if (dbg_steps <= 2) return k;
+  int k = 5;                    // range finder, traces, Gram-Schmidt, two products
   k += refine(c, Qa, Qb);
   // Qa holds the final basis
   rank_select_kernel<<<3, 128, 0, c.stream>>>(c.T, ks, c.cfg.eps, c.cfg.rank_cap, c.rmax, c.order,

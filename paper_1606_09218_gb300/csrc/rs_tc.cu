@@ -109,8 +109,8 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
                 int ntiles, const DevScalars* sc, unsigned char* __restrict__ out,
                 unsigned long long tile_bytes) {
   extern __shared__ __align__(16) float tsm[];
-  float* T1s = tsm;                          // [8][rmax][32]
-  float* V2s = tsm + 8 * rmax * 32;          // [32][rmax]
+  float* T1s = tsm;                          // [rmax][2][32][4]: ranks a0 + 4h + (0..3) of (b, i3)
+  float* V2s = tsm + 8 * rmax * 32;          // [rmax][8][4]: V2[i2b + w + 8q][b] at (b, w, q)
   __shared__ float s_scale;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int t3 = blockIdx.x, i2b = blockIdx.y * TT_ROWS, i3 = t3 * AS_T3 + lane;
@@ -141,7 +141,8 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
   }
   for (int r = warp; r < TT_ROWS; r += 8) {
     const int i2 = i2b + r;
-    for (int b = lane; b < rmax; b += 32) V2s[r * rmax + b] = (i2 < n && b < r2) ? V2[(long long)i2 * rmax + b] : 0.f;
+    for (int b = lane; b < rmax; b += 32)
+      V2s[(b * 8 + (r & 7)) * 4 + (r >> 3)] = (i2 < n && b < r2) ? V2[(long long)i2 * rmax + b] : 0.f;
   }
   for (int a0 = 0; a0 < kp; a0 += 8) {
     if (a0 >= r1) {
@@ -167,7 +168,7 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
       for (int b = warp; b < r2; b += 8) {
         const float* src = in ? T1 + ((long long)a * rmax + b) * n + i3 : T1;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
-                         smem_addr(&T1s[(x * rmax + b) * AS_T3 + lane])),
+                         smem_addr(&T1s[((b * 2 + (x >> 2)) * 32 + lane) * 4 + (x & 3)])),
                      "l"(src), "r"(in ? 4 : 0)
                      : "memory");
       }
@@ -179,12 +180,12 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int x = 0; x < 8; ++x) acc[q][x] = 0.f;
+    const float4* T4 = reinterpret_cast<const float4*>(T1s);
+    const float4* V4 = reinterpret_cast<const float4*>(V2s);
     for (int b = 0; b < r2; ++b) {
-      float tv[8], vv[4];
-#pragma unroll
-      for (int x = 0; x < 8; ++x) tv[x] = T1s[(x * rmax + b) * AS_T3 + lane];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) vv[q] = V2s[(warp + 8 * q) * rmax + b];
+      const float4 t0 = T4[(b * 2) * 32 + lane], t1 = T4[(b * 2 + 1) * 32 + lane], v = V4[b * 8 + warp];
+      const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+      const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
