@@ -131,14 +131,22 @@ gemm_small_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __res
   T acc = T(0);
   for (int k0 = kbeg; k0 < kend; k0 += BT) {
     {
-      int ar = row0 + ty, gk = k0 + tx;      // A element (ar, gk)
-      T v = T(0);
-      if (ar < m && gk < kend) v = tA ? A[(long long)gk * lda + ar] : A[(long long)ar * lda + gk];
-      As[ty][tx] = v;
-      int gk2 = k0 + ty, bc = col0 + tx;     // B element (gk2, bc)
-      T w = T(0);
-      if (bc < nn && gk2 < kend) w = tB ? B[(long long)bc * ldb + gk2] : B[(long long)gk2 * ldb + bc];
-      Bs[ty][tx] = w;
+      // consecutive threads read consecutive addresses: a transposed operand is loaded along its
+      // rows and stored transposed in shared memory
+      if (!tA) {
+        const int ar = row0 + ty, gk = k0 + tx;            // A element (ar, gk)
+        As[ty][tx] = (ar < m && gk < kend) ? A[(long long)ar * lda + gk] : T(0);
+      } else {
+        const int ar = row0 + tx, gk = k0 + ty;            // A element (ar, gk), stored at A[gk][ar]
+        As[tx][ty] = (ar < m && gk < kend) ? A[(long long)gk * lda + ar] : T(0);
+      }
+      if (!tB) {
+        const int gk2 = k0 + ty, bc = col0 + tx;           // B element (gk2, bc)
+        Bs[ty][tx] = (bc < nn && gk2 < kend) ? B[(long long)gk2 * ldb + bc] : T(0);
+      } else {
+        const int gk2 = k0 + tx, bc = col0 + ty;           // B element (gk2, bc), stored at B[bc][gk2]
+        Bs[tx][ty] = (bc < nn && gk2 < kend) ? B[(long long)bc * ldb + gk2] : T(0);
+      }
     }
     __syncthreads();
 #pragma unroll
