@@ -117,6 +117,7 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.Qp, ts * 3 * n * Rl * rm);
   if (c.use_tc_core) add(v, c.kmeta, 16 * (size_t)N * Rl);
   add(v, c.pe, 8 * (size_t)N);
+  add(v, c.ewin, 8 * (size_t)N);
   add(v, c.beta64, 8 * rm * rm * rm);
   add(v, c.beta, ts * rm * rm * rm);
   add(v, c.T1, ts * rm * rm * n);
@@ -417,6 +418,8 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   c.stream = c.aux;
   k += launch_bins(c);                     // window lists
   cudaEventRecord(c.ev_bins, c.aux);
+  if ((flags & RS_ENERGY) && c.use_tc && !c.fp64)
+    k += launch_energy_windows(c);         // a8, the neighbours' windows at every particle
   if (flags & RS_FORCES) k += launch_forces(c);                          // a9 (particles and bins only)
   c.stream = s;
   k += launch_gram(c);                     // a3, a4: Gram matrices of the long-range side matrices
@@ -425,8 +428,8 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   mark(4);
   k += launch_projection_core(c);          // a5: projection and core
   mark(5);
-  // (the energy stays on this stream after the assembly: beside it, its blocks delay the
-  // persistent assembly CTAs more than they save)
+  // (the energy's Tucker part stays on this stream after the assembly: beside it, its blocks
+  // delay the persistent assembly CTAs more than they save)
   cudaEventRecord(c.ev_side, c.aux);
   cudaStreamWaitEvent(s, c.ev_bins, 0);    // window lists ready
   mark(6);
@@ -436,8 +439,8 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   mark(7);
   if (flags & RS_POTENTIAL) k += launch_windows(c, potential_out);      // a6
   mark(8);
+  cudaStreamWaitEvent(s, c.ev_side, 0);    // energy windows and forces (second stream) done
   if (flags & RS_ENERGY) k += launch_energy(c, N);                      // a8
-  cudaStreamWaitEvent(s, c.ev_side, 0);    // forces (second stream) done
   mark(9);
   st = check_launch(c, "solve");
   if (st != RS_OK) return st;

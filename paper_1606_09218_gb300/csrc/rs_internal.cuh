@@ -57,6 +57,7 @@ struct DevScalars {
   int chunk_w[32];               // windows per i1 chunk (tensor-core assembly schedule)
   unsigned zmax_bits;            // max |z| over the particles (float bits; window operand scale)
   unsigned qmax_bits;            // max |Qp| of the FP32 projections (float bits; core operand scale)
+  int t2_shift;                  // scale exponent S of the T2 tiles (written by the tile kernel)
   double beta_a2[RMAX_LIMIT];    // ||beta[a, :, :]||^2 (scale of the FP16 Tucker operands)
   // barriers of the cooperative Gram-Schmidt kernel, one per mode: arrival counter and
   // generation of mode l at [32 l], each on its own 128-byte line, so that the waiters' polling
@@ -157,6 +158,7 @@ struct Ctx {
   bool use_tc_core = false;     // tensor-core core contraction (FP32 bulk path)
   void*   kmeta = nullptr;      // per K term of the core: Qp row offsets and charge (int4)
   double* pe = nullptr;         // per-particle pair energies (off-grid energy and forces)
+  double* ewin = nullptr;       // window part of each charged particle's value (energy)
   long long wl_cap = 0;         // capacity of the window lists (entries)
   int*       wl_count = nullptr;   // ntiles + 1
   int*       wl_start = nullptr;   // ntiles + 1
@@ -261,6 +263,7 @@ cudaError_t set_attributes_tc(int optin);
 cudaError_t set_attributes_core(int optin);
 int launch_core_tc(Ctx& c);
 int launch_energy_t2(Ctx& c, double* part, int blocks);
+int launch_energy_windows(Ctx& c);
 int launch_canonical(Ctx& c, double eps, int r1, int r2, int r3, int P);
 int launch_canonical_eval(Ctx& c, int M, const int* idx, double* out);
 size_t canonical_svd_smem(int r);

@@ -106,7 +106,7 @@ constexpr uint32_t SLOT_HALF = AS_M * 16 * 2;    // one pair slot: 128 rows x K 
 // of 8 (one 16-byte chunk of a row).
 __global__ void __launch_bounds__(256)
 t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int n, int rmax, int kp,
-                int ntiles, const DevScalars* sc, unsigned char* __restrict__ out,
+                int ntiles, DevScalars* sc, unsigned char* __restrict__ out,
                 unsigned long long tile_bytes) {
   extern __shared__ __align__(16) float tsm[];
   float* T1s = tsm;                          // [rmax][2][32][4]: ranks a0 + 4h + (0..3) of (b, i3)
@@ -120,7 +120,11 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
     double m = 0.0;
     for (int a = lane; a < r1; a += 32) m = fmax(m, sc->beta_a2[a]);
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) s_scale = ldexpf(1.0f, (m > 0.0 ? max(-100, min(100, 22 - exp2_above(sqrt(m)))) : 0) - 8);
+    if (lane == 0) {
+      const int S = m > 0.0 ? max(-100, min(100, 22 - exp2_above(sqrt(m)))) : 0;
+      s_scale = ldexpf(1.0f, S - 8);
+      if (blockIdx.x == 0 && blockIdx.y == 0) sc->t2_shift = S;
+    }
   }
   __syncthreads();
   const float scale = s_scale;
@@ -218,7 +222,7 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
 // factors).  One warp per charged particle; one partial sum per CTA.
 __global__ void __launch_bounds__(256)
 energy_t2_kernel(DevView c, const float* __restrict__ V1, const unsigned char* __restrict__ T2t,
-                 unsigned long long tile_bytes, int kp, double* part) {
+                 unsigned long long tile_bytes, int kp, const double* __restrict__ ewin, double* part) {
   __shared__ double red[8];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int mi = blockIdx.x * 8 + warp;
@@ -247,9 +251,8 @@ energy_t2_kernel(DevView c, const float* __restrict__ V1, const unsigned char* _
       }
       v += (double)s;
     }
-    v = ldexp(v, -(operand_shift(c.sc, r1) - 8));
-    window_add(c, i1, i2, i3, lane, v);    // short-range windows of the neighbours (FP64 factors)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    v = ldexp(v, -(c.sc->t2_shift - 8)) + ewin[mi];   // plus the neighbours' windows
     const double z = c.Z[p];
     e = z * (v - z * c.sc->P_R0);
   }
@@ -265,7 +268,27 @@ energy_t2_kernel(DevView c, const float* __restrict__ V1, const unsigned char* _
 int launch_energy_t2(Ctx& c, double* part, int blocks) {
   const unsigned long long tile_bytes = 4ull * AS_M * (unsigned long long)c.tc_kpad;   // hi + lo FP16
   energy_t2_kernel<<<blocks, 256, 0, c.stream>>>(make_view(c), (const float*)c.Z32, (const unsigned char*)c.T2,
-                                                 tile_bytes, c.tc_kpad, part);
+                                                 tile_bytes, c.tc_kpad, c.ewin, part);
+  return 1;
+}
+
+// The window part of every charged particle's value, sum_{nu in L(j)} z_nu U_nu(j): it needs
+// only the particles and their bins, so it runs on the second stream beside the Gram and eigen
+// stages.  One warp per charged particle.
+__global__ void __launch_bounds__(256) energy_windows_kernel(DevView c, double* ewin) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int mi = blockIdx.x * 8 + warp;
+  if (mi >= c.sc->n_nz) return;
+  const int p = c.nz_idx[mi];
+  double v = 0.0;
+  window_add(c, c.j[3 * p], c.j[3 * p + 1], c.j[3 * p + 2], lane, v);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) ewin[mi] = v;
+}
+
+int launch_energy_windows(Ctx& c) {
+  const int blocks = (c.maxN + 7) / 8 > 0 ? (c.maxN + 7) / 8 : 1;
+  energy_windows_kernel<<<blocks, 256, 0, c.stream>>>(make_view(c), c.ewin);
   return 1;
 }
 
