@@ -143,6 +143,7 @@ core_kernel(const T* __restrict__ Qp, const int* __restrict__ jidx, const int* _
   int* off1 = (int*)(csm + sizeof(T) * (2 * 32 * 100 + CORE_KMAX));
   int* off2 = off1 + CORE_KMAX;
   int* off3 = off2 + CORE_KMAX;
+  __shared__ T zs[32][4];                         // z_K q2[K][b] of the current chunk
   const int tid = threadIdx.x;
   const int nK = (int)(ke - kb);                  // <= CORE_KMAX (host sizes the split)
   const long long sL = (long long)n * R_l * rmax;
@@ -193,10 +194,15 @@ core_kernel(const T* __restrict__ Qp, const int* __restrict__ jidx, const int* _
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
+    // z_K q2[K][b] of the chunk, once per (K, b) instead of once per thread
+    if (tid < 128) {
+      const int kk = tid >> 2, bq = tid & 3, kl = ch * 32 + kk;
+      zs[kk][bq] = (kl < nK ? zK[kl] : T(0)) * s2[bf][kk][bq];
+    }
+    __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < 32; ++kk) {
-      const int kl = ch * 32 + kk;
-      const T zb = (kl < nK ? zK[kl] : T(0)) * s2[bf][kk][tb];
+      const T zb = zs[kk][tb];
       T t[4], q3[8];
 #pragma unroll
       for (int x = 0; x < 4; ++x) t[x] = s1[bf][kk][4 * ta + x] * zb;
