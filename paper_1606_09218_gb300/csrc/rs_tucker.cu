@@ -56,13 +56,17 @@ proj_kernel(const T* __restrict__ Zb, const T* __restrict__ pk, const int* __res
       }
       __syncthreads();
       const int ilim = min(32, n - i0);
+      // factor rows p_k[i - j] of this thread's four j, as pointers advancing with i (a padding
+      // row, jj < 0, reads the row of j = 0 and is never stored)
+      const T* pr[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) pr[x] = sp + (i0 + n - 1) - max(jj[x], 0);
       for (int ii = 0; ii < ilim; ++ii) {
-        const int i = i0 + ii;
         T v[4], pj[4];
 #pragma unroll
         for (int y = 0; y < 4; ++y) v[y] = sV[ii * 64 + 4 * ta + y];
 #pragma unroll
-        for (int x = 0; x < 4; ++x) pj[x] = jj[x] >= 0 ? sp[i - jj[x] + n - 1] : T(0);
+        for (int x = 0; x < 4; ++x) pj[x] = pr[x][ii];
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
