@@ -233,6 +233,28 @@ def serving_report(max_slots: int = 8, hbm_budget: int = 16 << 30):
             "latency": "submit (host inputs) to result (energy on host, potential in a device buffer)"}
 
 
+def replica_seed(rank: int, index: int):
+    """Particle seed of a rank's replica: rank 0 solves the workload itself (its own seed), every
+    other rank an independent seeded problem of the same shape (weak scaling, no collective on
+    the data path)."""
+    return None if rank == 0 else 160609218 + 1000 * rank + index
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's x (the slowest rank's time); x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_step: float, steps: int, world: int, t_max_s: float) -> float:
+    """Grid points per second of the whole job: every rank's points over the slowest rank's time."""
+    return points_per_step * steps * world / t_max_s
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -245,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     cfg = load_config(args.workload)
-    parts = make_particles(cfg, seed=None if rank == 0 else 160609218 + 1000 * rank + int(cfg["index"]))
+    parts = make_particles(cfg, seed=replica_seed(rank, int(cfg["index"])))
     n = int(cfg["n"])
     N = int(len(parts.Z))
     ccfg = config_from_workload(cfg, max_particles=N)
@@ -285,11 +307,8 @@ def run_ours(args, rank, world, local_rank):
     stages, nsolves = ctx.profile_read()
     ctx.profile(False)
     launches = ctx.report()["kernel_launches"] * args.steps
-    t_max = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_ms = float(t_max.item())
-    value = n ** 3 * args.steps * world / (t_ms * 1e-3)
+    t_ms = max_over_ranks(t_ms, dist, "cuda")
+    value = whole_job_rate(n ** 3, args.steps, world, t_ms * 1e-3)
 
     # end to end through the C ABI with host buffers (pinned), energy read back each step
     hx = torch.tensor(parts.xyz).pin_memory()
@@ -302,10 +321,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.solve(hxn, hzn, potential=pot, energy=True)
         ctx.energy()
     t_e2e = time.perf_counter() - t0
-    t_e = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-    e2e_value = n ** 3 * e2e_steps * world / float(t_e.item())
+    e2e_value = whole_job_rate(n ** 3, e2e_steps, world, max_over_ranks(t_e2e, dist, "cuda"))
 
     # plain RS path on the same GPU: every stage in FP64
     plain = None
