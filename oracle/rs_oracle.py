@@ -596,7 +596,7 @@ def rs_direct_long_forces(j, z, pk, dpk, klong, kshort, gamma: int, n: int):
     """Forces of the untruncated long-range canonical sum plus the windows at snapped centres:
     F_j = -z_j [grad P_l(x_j) + window terms], grad P_l(x_j) = sum_{nu != j} z_nu sum_{k long}
     grad (p_k (x) p_k (x) p_k)(x_j - x_nu) with the Galerkin factors and their derivatives on the
-    grid offsets (the survey's F = -z grad P_l, exact for P_l by symmetry)."""
+    grid offsets (F = -z grad P_l of Sec. 4.3, exact for P_l by symmetry)."""
     c = n - 1
     z = np.asarray(z, dtype=np.float64)
     N = len(z)
