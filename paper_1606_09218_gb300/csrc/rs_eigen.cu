@@ -173,7 +173,7 @@ gemm_small_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __res
 template <typename T>
 void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha,
                   const T* A, int lda, long long sA, const T* B, int ldb, long long sB, T beta,
-                  T* C, int ldc, long long sC, int batch, int splitK, const int* dynM,
+                  T* C, int ldc, long long sC, int batch, const int* dynM,
                   const int* dynN, const int* dynK, const GemmScratch* scr) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   // FP64 products (C overwritten) use 16x16 tiles with a deterministic K split when the tiles
@@ -192,7 +192,6 @@ void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K,
                                              sk > 1 ? (T*)scr->part : nullptr, sk > 1 ? scr->count : nullptr);
     return;
   }
-  (void)splitK;
   dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
   gemm_kernel<T><<<grid, 256, 0, s>>>(transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB,
                                       beta, C, ldc, sC, dynM, dynN, dynK);
@@ -200,11 +199,11 @@ void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K,
 
 template void gemm_batched<double>(cudaStream_t, bool, bool, int, int, int, double, const double*,
                                    int, long long, const double*, int, long long, double, double*,
-                                   int, long long, int, int, const int*, const int*, const int*,
+                                   int, long long, int, const int*, const int*, const int*,
                                    const GemmScratch*);
 template void gemm_batched<float>(cudaStream_t, bool, bool, int, int, int, float, const float*,
                                   int, long long, const float*, int, long long, float, float*,
-                                  int, long long, int, int, const int*, const int*, const int*,
+                                  int, long long, int, const int*, const int*, const int*,
                                   const GemmScratch*);
 
 // ------------------------------------------------------------------ helpers
@@ -953,9 +952,9 @@ static void congruence(Ctx& c, double* Tm, const double* Wm) {
   const long long sK = (long long)ks * ks;
   const int* ke = c.sc->k_eff;
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, Tm, ks, sK, Wm, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
+                       c.T2k, ks, sK, 3, ke, ke, ke, &c.gscr);
   gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, Wm, ks, sK, c.T2k, ks, sK, 0.0,
-                       Tm, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
+                       Tm, ks, sK, 3, ke, ke, ke, &c.gscr);
 }
 
 // Rayleigh-Ritz refinement: two FP32 Jacobi passes on the graded T (rotations accumulated in
@@ -976,19 +975,19 @@ static int refine(Ctx& c, double*& Qa, double*& Qb) {
   congruence(c, c.T, c.W2);
   // T2k = W = W1 W2 ; W2 = E = W^T W - I ; c.W = E^2 ; W2 = M
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W2, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
+                       c.T2k, ks, sK, 3, ke, ke, ke, &c.gscr);
   gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.T2k, ks, sK, c.T2k, ks, sK, 0.0,
-                       c.W2, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
+                       c.W2, ks, sK, 3, ke, ke, ke, &c.gscr);
   dim3 g2((ks * ks + 255) / 256, 3);
   sub_identity_kernel<<<g2, 256, 0, c.stream>>>(c.W2, ks, c.sc);
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W2, ks, sK, c.W2, ks, sK, 0.0,
-                       c.W, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
+                       c.W, ks, sK, 3, ke, ke, ke, &c.gscr);
   ns_matrix_kernel<<<g2, 256, 0, c.stream>>>(c.W2, c.W, c.W2, ks, c.sc);
   // c.W = W M ; Qb = Qa (W M) ; T = M^T T M
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.T2k, ks, sK, c.W2, ks, sK, 0.0,
-                       c.W, ks, sK, 3, 1, ke, ke, ke, &c.gscr);
+                       c.W, ks, sK, 3, ke, ke, ke, &c.gscr);
   gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, c.W, ks, sK, 0.0, Qb,
-                       ks, sQ, 3, 1, nullptr, ke, ke, &c.gscr);
+                       ks, sQ, 3, nullptr, ke, ke, &c.gscr);
   congruence(c, c.T, c.W2);
   std::swap(Qa, Qb);
   return 2 + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1 + 1 + 2;
@@ -1012,9 +1011,9 @@ int launch_subspace(Ctx& c) {
   const int* ke = c.sc->k_eff;
   // Y = G Q ; T = Q^T Y
   gemm_batched<double>(c.stream, false, false, n, ks, n, 1.0, c.G, n, sG, c.Q, ks, sQ, 0.0, c.Y,
-                       ks, sQ, 3, 4, nullptr, ke, nullptr, &c.gscr);
+                       ks, sQ, 3, nullptr, ke, nullptr, &c.gscr);
   gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, c.Q, ks, sQ, c.Y, ks, sQ, 0.0, c.T,
-                       ks, sK, 3, 8, ke, ke, nullptr, &c.gscr);
+                       ks, sK, 3, ke, ke, nullptr, &c.gscr);
   // Rayleigh-Ritz refinement; the rotated basis ends in c.X
   double* Qa = c.Q;
   double* Qb = c.X;

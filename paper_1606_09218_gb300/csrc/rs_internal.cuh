@@ -301,7 +301,7 @@ template <typename T>
 void gemm_batched(cudaStream_t s, bool transA, bool transB, int M, int N, int K,
                   T alpha, const T* A, int lda, long long sA,
                   const T* B, int ldb, long long sB, T beta, T* C, int ldc, long long sC,
-                  int batch, int splitK, const int* dynM = nullptr, const int* dynN = nullptr,
+                  int batch, const int* dynM = nullptr, const int* dynN = nullptr,
                   const int* dynK = nullptr, const GemmScratch* scr = nullptr);
 
 }  // namespace rs

@@ -311,12 +311,12 @@ static int projection_core_t(Ctx& c) {
   const T* Zb = Bulk<T>::Z(c);
   const long long sZ = (long long)n * rmax;
   gemm_batched<T>(c.stream, false, true, rmax * rmax, n, rmax, T(1), (const T*)c.beta, rmax, 0,
-                  Zb + 2 * sZ, rmax, 0, T(0), (T*)c.T1, n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 2, &c.gscr);
+                  Zb + 2 * sZ, rmax, 0, T(0), (T*)c.T1, n, 0, 1, nullptr, nullptr, c.sc->rank + 2, &c.gscr);
   // T2[a][i2][i3] = sum_b V2[i2][b] T1[a][b][i3]        (batch a < r1, K = r2)
   if (c.use_tc && !c.fp64) return 3 + kcore + launch_t2_tiles(c);   // tiled FP16 operands
   batch_dims_kernel<<<(rmax + 127) / 128, 128, 0, c.stream>>>(c.adims, c.kdims, rmax, n, c.sc);
   gemm_batched<T>(c.stream, false, false, n, n, rmax, T(1), Zb + sZ, rmax, 0, (const T*)c.T1, n,
-                  (long long)rmax * n, T(0), (T*)c.T2, c.t2_ld, (long long)n * c.t2_ld, rmax, 1,
+                  (long long)rmax * n, T(0), (T*)c.T2, c.t2_ld, (long long)n * c.t2_ld, rmax,
                   c.adims, nullptr, c.kdims, &c.gscr);
   return 5 + kcore;
 }
@@ -545,12 +545,12 @@ static int recon_gemm_t(Ctx& c, T* out) {
   if (c.t2_ld == n) {
     // P[i1][(i2,i3)] = sum_a V1[i1][a] T2[a][(i2,i3)]
     gemm_batched<T>(c.stream, false, false, n, n * n, rmax, T(1), Zb, rmax, 0, (const T*)c.T2,
-                    n * n, 0, T(0), out, n * n, 0, 1, 1, nullptr, nullptr, c.sc->rank + 0, &c.gscr);
+                    n * n, 0, T(0), out, n * n, 0, 1, nullptr, nullptr, c.sc->rank + 0, &c.gscr);
   } else {
     // padded T2 rows: one batch per i2, P[i1][i2][i3] = sum_a V1[i1][a] T2[a][i2][i3]
     const long long ldb = (long long)n * c.t2_ld;
     gemm_batched<T>(c.stream, false, false, n, n, rmax, T(1), Zb, rmax, 0, (const T*)c.T2,
-                    (int)ldb, c.t2_ld, T(0), out, n * n, n, n, 1, nullptr, nullptr,
+                    (int)ldb, c.t2_ld, T(0), out, n * n, n, n, nullptr, nullptr,
                     c.sc->rank + 0, &c.gscr);
   }
   return 1;
