@@ -280,6 +280,41 @@ def rhosvd(Us, xi, eps: float, cap: int = 0, ranks=None):
     return Z0s, beta, rk, sig
 
 
+def als_mode_matrix(Us, xi, Vs, l: int):
+    """Partially projected image of the canonical tensor for mode l (Sec. 6, step (IV)):
+    sum_K xi_K u_K^(l) (x) (V^(l')^T u_K^(l')) (x) (V^(l'')^T u_K^(l'')), with l' < l'' the two
+    other modes, reshaped to the n x (r_l' r_l'') matrix M_{U_l} (column index b * r_l'' + c)."""
+    o1, o2 = [m for m in range(3) if m != l]
+    Y1 = Vs[o1].T @ Us[o1]                       # r_l' x K
+    Y2 = Vs[o2].T @ Us[o2]                       # r_l'' x K
+    M = np.einsum("iK,bK,cK,K->ibc", Us[l], Y1, Y2, xi, optimize=True)
+    return M.reshape(Us[l].shape[0], -1)
+
+
+def c2t_als(Us, xi, Z0s, eps: float, cap: int = 0, sweeps: int = 1, ranks=None):
+    """ALS refinement of the canonical-to-Tucker transform (Sec. 6, steps (III)-(V)).
+
+    Step (III) starts from the RHOSVD bases ``Z0s``.  Each sweep of step (IV) runs the modes in
+    the order l = 1, 2, 3.  It forms M_{U_l} (``als_mode_matrix``) from the current bases of the
+    other two modes and takes its SVD.  The r_l dominant left singular vectors become the new
+    basis of mode l, so a later mode already sees the updated earlier ones.  r_l is the eps-rank of
+    the singular values of M_{U_l} (the rule of ``rhosvd_rank``: the eps-truncation variant that
+    the text allows), or ``ranks[l]`` when ranks are given.  Step (V) projects onto the final bases
+    and forms the core.  Returns (bases, beta, ranks)."""
+    Vs = [np.asarray(Z, dtype=np.float64) for Z in Z0s]
+    rk = [V.shape[1] for V in Vs]
+    for _ in range(int(sweeps)):
+        for l in range(3):
+            M = als_mode_matrix(Us, xi, Vs, l)
+            Zl, s, _ = np.linalg.svd(M, full_matrices=False)
+            r = rhosvd_rank(s, eps, cap) if ranks is None else int(ranks[l])
+            Vs[l] = Zl[:, :r]
+            rk[l] = r
+    Y = [Vs[l].T @ Us[l] for l in range(3)]
+    beta = np.einsum("aK,bK,cK,K->abc", Y[0], Y[1], Y[2], xi, optimize=True)
+    return Vs, beta, rk
+
+
 def tucker_full(beta, Vs):
     """beta x_1 V^(1) x_2 V^(2) x_3 V^(3) on the full grid (Eq. (2.3))."""
     return np.einsum("abc,ia,jb,kc->ijk", beta, Vs[0], Vs[1], Vs[2], optimize=True)

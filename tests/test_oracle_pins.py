@@ -572,3 +572,113 @@ def test_canonical_points_match_full_tensor():
     assert np.allclose(v, C[idx[:, 0], idx[:, 1], idx[:, 2]], rtol=0, atol=1e-14 * np.abs(C).max())
     T = O.tucker_points(beta, Vs, idx)
     assert np.abs(v - T).max() <= math.sqrt(disc) + 1e-14
+
+
+# ---------------------------------------------------------------- Sec. 6 steps (III)-(V): ALS
+@pytest.fixture(scope="module")
+def small_problem():
+    rng = np.random.default_rng(21)
+    cfg = small_cfg()
+    xyz, z = random_particles(rng, 6, 3.0, 1.0)
+    pr = O.Problem(cfg, xyz, z)
+    return pr, pr.Pl_grid()
+
+
+def _unfold_projected(T, Vs, l):
+    """Mode-l unfolding of T projected onto the bases of the two other modes, computed on the
+    dense tensor (columns ordered by the lower other mode first)."""
+    if l == 0:
+        return np.einsum("ijk,jb,kc->ibc", T, Vs[1], Vs[2]).reshape(T.shape[0], -1)
+    if l == 1:
+        return np.einsum("ijk,ia,kc->jac", T, Vs[0], Vs[2]).reshape(T.shape[1], -1)
+    return np.einsum("ijk,ia,jb->kab", T, Vs[0], Vs[1]).reshape(T.shape[2], -1)
+
+
+def test_als_mode_matrix_is_the_projected_dense_unfolding(small_problem):
+    """Step (IV): M_{U_l} is the partially projected image of the full tensor, reshaped.  Checked
+    against the dense long-range tensor (pinned by brute force above), projected with random
+    orthonormal bases that do not come from the oracle."""
+    pr, Pl = small_problem
+    Us, xi = O.side_matrices(pr.j, pr.z, pr.pk, pr.klong, pr.n)
+    rng = np.random.default_rng(22)
+    Vs = [np.linalg.qr(rng.standard_normal((pr.n, r)))[0] for r in (5, 7, 6)]
+    for l in range(3):
+        M = O.als_mode_matrix(Us, xi, Vs, l)
+        D = _unfold_projected(Pl, Vs, l)
+        assert M.shape == D.shape
+        assert np.abs(M - D).max() <= 1e-12 * np.abs(D).max()
+
+
+@pytest.mark.parametrize("fixed", [True, False])
+def test_als_matches_dense_hooi(small_problem, fixed):
+    """Steps (III)-(V) against textbook higher-order orthogonal iteration on the dense tensor.
+    It starts from the same RHOSVD bases and updates the modes in order, each from the SVD of the
+    projected unfolding (numpy on the dense tensor).  The bases (as projectors), ranks and core
+    norm agree."""
+    pr, Pl = small_problem
+    eps = 1e-4
+    Z0s, _, rk0, _, Us, xi = pr.tucker(eps=eps, cap=0)
+    ranks = [max(2, r - 2) for r in rk0] if fixed else None
+    Vs, beta, rk = O.c2t_als(Us, xi, Z0s, eps, 0, sweeps=2, ranks=ranks)
+    D = [Z.copy() for Z in Z0s]
+    rd = list(rk0)
+    for _ in range(2):
+        for l in range(3):
+            W, s, _ = np.linalg.svd(_unfold_projected(Pl, D, l), full_matrices=False)
+            if ranks is None:
+                e2 = s ** 2
+                tail = np.concatenate([np.cumsum(e2[::-1])[::-1], [0.0]])
+                r = max(1, int(np.argmax(tail <= (eps * eps / 3.0) * e2.sum())))
+            else:
+                r = ranks[l]
+            D[l] = W[:, :r]
+            rd[l] = r
+    assert rk == rd
+    for V, W in zip(Vs, D):
+        assert np.abs(V @ V.T - W @ W.T).max() <= 1e-9
+    core = np.einsum("ijk,ia,jb,kc->abc", Pl, D[0], D[1], D[2])
+    assert abs(np.linalg.norm(beta) - np.linalg.norm(core)) <= 1e-12 * np.linalg.norm(core)
+
+
+def test_als_full_rank_is_exact(small_problem):
+    """At full rank every projector is the identity on the column space: exact reconstruction."""
+    pr, Pl = small_problem
+    Z0s, _, _, _, Us, xi = pr.tucker(ranks=[pr.n] * 3)
+    Vs, beta, rk = O.c2t_als(Us, xi, Z0s, 0.0, 0, sweeps=1, ranks=[pr.n] * 3)
+    assert np.max(np.abs(O.tucker_full(beta, Vs) - Pl)) <= 1e-11 * np.max(np.abs(Pl))
+
+
+def test_als_fixed_ranks_never_worse_and_monotone(c1_problem):
+    """Each mode update of step (IV) maximises ||U x_1 P1 x_2 P2 x_3 P3|| over the projector of its
+    mode with the others fixed, so at fixed ranks ||beta|| does not decrease from the RHOSVD start
+    (Def. 6.1) or from one sweep to the next.  The Tucker error (full grid, with Pythagoras)
+    therefore does not increase either."""
+    pr, Pl = c1_problem
+    Z0s, beta0, rk0, _, Us, xi = pr.tucker(eps=1e-5, cap=0)
+    nrm = np.linalg.norm(Pl)
+    e0 = np.linalg.norm(Pl - O.tucker_full(beta0, Z0s))
+    b_prev = np.linalg.norm(beta0)
+    for sweeps in (1, 2):
+        Vs, beta, rk = O.c2t_als(Us, xi, Z0s, 1e-5, 0, sweeps=sweeps, ranks=rk0)
+        assert rk == rk0
+        b = np.linalg.norm(beta)
+        assert b >= b_prev * (1 - 1e-14)
+        b_prev = b
+        err = np.linalg.norm(Pl - O.tucker_full(beta, Vs))
+        assert err <= e0 * (1 + 1e-9)
+        assert abs(nrm ** 2 - b * b - err ** 2) <= 1e-9 * nrm ** 2
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+def test_als_eps_ranks_within_eps(c1_problem, eps):
+    """The eps-truncation variant of the ALS (Sec. 6, remark after step (V)) keeps the Tucker error
+    of the long part within eps on the full grid.  On this workload its ranks are at most the
+    RHOSVD ranks in every mode and lower in total."""
+    pr, Pl = c1_problem
+    Z0s, _, rk0, _, Us, xi = pr.tucker(eps=eps, cap=0)
+    Vs, beta, rk = O.c2t_als(Us, xi, Z0s, eps, 0, sweeps=1)
+    err = np.linalg.norm(Pl - O.tucker_full(beta, Vs)) / np.linalg.norm(Pl)
+    assert err <= eps
+    assert all(a <= b for a, b in zip(rk, rk0)) and sum(rk) < sum(rk0)
+    for V in Vs:
+        assert np.allclose(V.T @ V, np.eye(V.shape[1]), atol=1e-12)
