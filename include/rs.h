@@ -177,6 +177,31 @@ rs_status rs_canonical_eval_points(rs_ctx* ctx, int M, const int* idx, double* o
  * xi (R*), U: three side matrices, U[(l*n + i)*ld + k] for mode l, grid index i, term k < R*. */
 rs_status rs_get_canonical(rs_ctx* ctx, int* rank, const double** xi, const double** U, int* ld);
 
+/* ALS refinement of the canonical-to-Tucker transform of the last solve (Sec. 6, steps (III)-(V)).
+ * It starts from the RHOSVD bases.  Each sweep updates the modes in the order l = 1, 2, 3.  Mode l
+ * takes the dominant left singular vectors of M_{U_l}: the long-range canonical tensor projected
+ * onto the current bases of the other two modes and reshaped to n x (r_l' r_l'').  The new rank
+ * r_l is the eps rule of rs_solve applied to the singular values of M_{U_l} (the eps-truncation
+ * variant of the algorithm), capped by rank_cap and max_rank.  The core is then formed from the
+ * final bases (step (V)).  The mode matrices and their Gram matrices M M^T are FP64 in every
+ * precision.  The eigenvectors come from the eigen stage of rs_solve, and the core from its core
+ * contraction.
+ *   sweeps: 1..RS_ALS_MAX_SWEEPS.  A second call continues from the refined form.
+ *   flags: RS_POTENTIAL writes the refined full-grid RS-Tucker potential into potential_out (as for
+ *   rs_solve).  RS_ENERGY recomputes the energy; it needs a solve that computed one.  Without
+ *   RS_ENERGY, rs_energy returns RS_ERR_NOT_READY until the next solve (the old energy belonged to
+ *   the RHOSVD tensor).  Forces are unchanged (they use the untruncated long-range kernel).
+ * Afterwards rs_report (ranks, tail_rel of the mode matrices), rs_get_tucker, rs_eval_points and
+ * rs_canonical see the refined tensor, and an earlier RS-canonical form is invalidated.
+ * Synchronises once per mode update to read the ranks.  The first call allocates
+ * 8 (3 n R_l rmax + n rmax^2 + n K_c + K_c rmax^2) bytes of device memory (rmax the context's
+ * rank bound, K_c = min(n R_l, 2^24 / rmax^2) rows of one chunk, so the last term is at most
+ * 128 MiB), kept until rs_destroy.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_NOT_READY (no solve, or RS_ENERGY without a solve energy),
+ * the status of a failed solve, RS_ERR_OOM, RS_ERR_CUDA. */
+#define RS_ALS_MAX_SWEEPS 8
+rs_status rs_tucker_als(rs_ctx* ctx, int sweeps, int flags, void* potential_out);
+
 /* Stage timing (tracing): with enable != 0, each rs_solve records one CUDA event per stage
  * boundary on the context stream (ring of 512 solves).  Errors: RS_ERR_CUDA. */
 rs_status rs_profile_enable(rs_ctx* ctx, int enable);

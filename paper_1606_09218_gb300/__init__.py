@@ -242,6 +242,25 @@ class RSContext:
                                                      C.c_void_p(out.data_ptr())), self.h)
         return out
 
+    def tucker_als(self, sweeps: int = 1, energy: bool = True, potential=None, want_potential: bool = True) -> int:
+        """ALS refinement of the last solve's canonical-to-Tucker transform (Sec. 6, steps
+        (III)-(V)): ``sweeps`` sweeps over the modes with eps-truncated ranks.  With
+        ``want_potential`` the refined full-grid potential is written to ``potential`` (a new
+        tensor if None, kept as ``self.potential``); with ``energy`` the energy is recomputed."""
+        flags = RS_ENERGY if energy else 0
+        out = 0
+        if want_potential:
+            if potential is None:
+                potential = self.new_potential()
+            assert potential.dtype == self.dtype and potential.is_cuda and potential.numel() == self.n ** 3
+            out = potential.data_ptr()
+            flags |= RS_POTENTIAL
+        st = self.lib.rs_tucker_als(self.h, int(sweeps), flags, C.c_void_p(out))
+        _lib.check(st, self.h)
+        if want_potential:
+            self.potential = potential
+        return st
+
     def get_canonical(self):
         """(xi (R*,), [U1, U2, U3] (n, R*)) float64 CUDA views of the RS-canonical form."""
         torch = self._torch

@@ -35,6 +35,7 @@ RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_FORCES, RS_VALIDATE_SEPARATION = 1, 2
 #: every symbol ``include/rs.h`` declares
 EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_energy", "rs_forces", "rs_report",
             "rs_get_tucker", "rs_eval_points", "rs_canonical", "rs_canonical_eval_points", "rs_get_canonical",
+            "rs_tucker_als",
             "rs_profile_enable", "rs_profile_read", "rs_stage_name",
             "rs_debug_buffer", "rs_gram_noalloc", "rs_plain_direct", "rs_plain_canonical",
             "rs_pair_energy_forces",
@@ -126,6 +127,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.rs_canonical_eval_points.restype = C.c_int
     lib.rs_get_canonical.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int)]
     lib.rs_get_canonical.restype = C.c_int
+    lib.rs_tucker_als.argtypes = [vp, C.c_int, C.c_int, vp]
+    lib.rs_tucker_als.restype = C.c_int
     lib.rs_profile_enable.argtypes = [vp, C.c_int]
     lib.rs_profile_enable.restype = C.c_int
     lib.rs_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]

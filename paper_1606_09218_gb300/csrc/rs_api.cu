@@ -170,6 +170,7 @@ void free_all(Ctx& c) {
   if (c.h_sc) cudaFreeHost(c.h_sc);
   c.h_sc = nullptr;
   free_canonical(c);
+  free_als(c);
   if (c.ev_part) cudaEventDestroy(c.ev_part);
   if (c.ev_bins) cudaEventDestroy(c.ev_bins);
   if (c.ev_side) cudaEventDestroy(c.ev_side);
@@ -603,6 +604,36 @@ rs_status rs_canonical_eval_points(rs_ctx* h, int M, const int* idx, double* out
   if (M < 0 || (M > 0 && (!idx || !out))) return fail(c, RS_ERR_INVALID_ARG, "bad point list");
   launch_canonical_eval(c, M, idx, out);
   return check_launch(c, "canonical_eval_points");
+}
+
+rs_status rs_tucker_als(rs_ctx* h, int sweeps, int flags, void* potential_out) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (sweeps < 1 || sweeps > RS_ALS_MAX_SWEEPS) return fail(c, RS_ERR_INVALID_ARG, "tucker_als: sweeps in [1, 8]");
+  if (flags & ~(RS_POTENTIAL | RS_ENERGY))
+    return fail(c, RS_ERR_INVALID_ARG, "tucker_als: flags other than RS_POTENTIAL | RS_ENERGY");
+  if ((flags & RS_POTENTIAL) && (!potential_out || ((uintptr_t)potential_out & 15u)))
+    return fail(c, RS_ERR_INVALID_ARG, "tucker_als: RS_POTENTIAL needs a 16-byte aligned potential_out");
+  if (!c.solved) return fail(c, RS_ERR_NOT_READY, "no solve");
+  if ((flags & RS_ENERGY) && !(c.last_flags & RS_ENERGY))
+    return fail(c, RS_ERR_NOT_READY, "tucker_als: RS_ENERGY needs a solve that computed the energy");
+  rs_status st = sync_scalars(c);
+  if (st != RS_OK) return st;
+  const rs_status solved = status_of(*c.h_sc);
+  if (solved < 0) return fail(c, solved, "tucker_als: the last solve failed");
+  const int k = als_refine(c, sweeps);
+  if (k < 0) return fail(c, c.err.find("allocation") != std::string::npos ? RS_ERR_OOM : RS_ERR_CUDA, c.err);
+  c.cn_rank = -1;                          // the canonical form described the previous core
+  int k2 = 0;
+  if (flags & RS_POTENTIAL) {
+    k2 += launch_recon_gemm(c, potential_out);
+    k2 += launch_windows(c, potential_out);
+  }
+  if (flags & RS_ENERGY) k2 += launch_energy(c, c.last_N);
+  // an energy not recomputed here belonged to the previous Tucker tensor
+  c.last_flags = (c.last_flags & ~RS_ENERGY) | (flags & RS_ENERGY);
+  c.launches = k + k2;
+  return check_launch(c, "tucker_als");
 }
 
 rs_status rs_get_canonical(rs_ctx* h, int* rank, const double** xi, const double** U, int* ld) {

@@ -90,6 +90,15 @@ struct Ctx {
   double* cn_xi = nullptr;       // cn_cap weights
   int cn_cap = 0;                // capacity in terms
   int cn_rank = -1;              // R* of the current solve, -1 before rs_canonical
+  // ALS refinement of the canonical-to-Tucker transform (allocated by the first rs_tucker_als call)
+  double* als_Qp = nullptr;      // 3 x n x R_l x rmax: FP64 projections onto the current bases
+  double* als_P = nullptr;       // n x als_kc: shifted long-range factor columns of one K chunk
+  double* als_A = nullptr;       // als_kc x rmax^2: charge-weighted projected rows of one K chunk
+  double* als_M = nullptr;       // n x rmax^2: the mode matrix M_{U_l}
+  int* als_inv = nullptr;        // 3 x n: compacted index of each charged coordinate, -1 elsewhere
+  int* als_start = nullptr;      // 3 x (n + 1): charged particles grouped by coordinate (CSR)
+  int* als_items = nullptr;      // 3 x maxN
+  int als_kc = 0;                // rows of one K chunk
   cudaEvent_t ev_part = nullptr, ev_bins = nullptr, ev_side = nullptr;
   int n = 0, R = 0, R_l = 0, R_s = 0, L = 0;   // L = 2n - 1
   int ksub = 0;        // subspace width (multiple of KB)
@@ -273,6 +282,10 @@ cudaError_t set_attributes_plain(int optin);
 rs_status launch_plain(Ctx& c, int which, float* out);
 rs_status launch_pair_energy_forces(Ctx& c, int N, const double* xyz, const double* Z, double* E, double* F);
 int launch_eval_points(Ctx& c, int M, const int* idx, double* out);
+// ALS refinement (rs_als.cu): FP64 projections of every mode onto its current basis
+int launch_proj64(Ctx& c, double* Qp);
+int als_refine(Ctx& c, int sweeps);      // kernels launched, or -1 with c.err set
+void free_als(Ctx& c);
 
 // generic batched GEMM on row-major matrices:
 //   C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b]

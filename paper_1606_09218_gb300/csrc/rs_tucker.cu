@@ -325,6 +325,16 @@ int launch_projection_core(Ctx& c) {
   return c.fp64 ? projection_core_t<double>(c) : projection_core_t<float>(c);
 }
 
+// FP64 projections of all three modes onto the FP64 bases (any precision of the context): the
+// input of the ALS mode matrices.  Same layout as Qp; rows of uncharged coordinates untouched.
+int launch_proj64(Ctx& c, double* Qp) {
+  const int n = c.n, rmax = c.rmax;
+  const size_t psmem = sizeof(double) * ((size_t)((2 * n - 1 + 3) & ~3) + 32 * 64);
+  dim3 g1(((n + 63) / 64) * ((rmax + 63) / 64), c.R_l, 3);
+  proj_kernel<double><<<g1, 256, psmem, c.stream>>>(c.Z64, c.pk64, c.nzj, n, rmax, c.R_l, c.sc, Qp);
+  return 1;
+}
+
 // ------------------------------------------------------------------ particle bins
 __global__ void bin_count_kernel(const int* jidx, const int* nz_idx, const DevScalars* sc, int nb,
                                  int* count) {
