@@ -92,7 +92,7 @@ typedef struct {
     double P_R0, P_Rl0;         /* P_R and P_{R_l} at the origin (self-interaction terms) */
     double energy;              /* last energy (if computed) */
     int    status;              /* status of the last solve (rs_status) */
-    int    kernel_launches;     /* CUDA kernels the last rs_solve enqueued */
+    int    kernel_launches;     /* CUDA kernels the last rs_solve (or rs_tucker_als after it) enqueued */
 } rs_stats;
 
 /* Pipeline stages timed by rs_profile_read (in this order). */

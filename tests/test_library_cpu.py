@@ -55,3 +55,9 @@ def test_invalid_config_is_rejected_on_host(lib):
         assert lib.rs_create(C.byref(c), None, C.byref(h)) == _lib.RS_ERR_INVALID_ARG
         assert h.value is None
         assert lib.rs_last_error(None)
+
+
+def test_als_entry_rejects_a_null_context(lib):
+    """rs_tucker_als checks its context before any device work."""
+    from paper_1606_09218_gb300 import _lib
+    assert lib.rs_tucker_als(None, 1, 0, None) == _lib.RS_ERR_INVALID_ARG
