@@ -198,7 +198,8 @@ rs_status rs_get_canonical(rs_ctx* ctx, int* rank, const double** xi, const doub
  * rank bound, K_c = min(n R_l, 2^24 / rmax^2) rows of one chunk, so the last term is at most
  * 128 MiB), kept until rs_destroy.
  * Errors: RS_ERR_INVALID_ARG, RS_ERR_NOT_READY (no solve, or RS_ENERGY without a solve energy),
- * the status of a failed solve, RS_ERR_OOM, RS_ERR_CUDA. */
+ * the status of a failed solve, RS_ERR_OOM (nothing changed), RS_ERR_CUDA (the solve's results are
+ * withdrawn: later calls return RS_ERR_NOT_READY until the next rs_solve). */
 #define RS_ALS_MAX_SWEEPS 8
 rs_status rs_tucker_als(rs_ctx* ctx, int sweeps, int flags, void* potential_out);
 

@@ -622,7 +622,13 @@ rs_status rs_tucker_als(rs_ctx* h, int sweeps, int flags, void* potential_out) {
   const rs_status solved = status_of(*c.h_sc);
   if (solved < 0) return fail(c, solved, "tucker_als: the last solve failed");
   const int k = als_refine(c, sweeps);
-  if (k < 0) return fail(c, c.err.find("allocation") != std::string::npos ? RS_ERR_OOM : RS_ERR_CUDA, c.err);
+  if (k < 0) {
+    // an allocation failure happens before any change; a CUDA error may leave the Tucker part
+    // half refined, so the results of the solve are withdrawn
+    const bool oom = c.err.find("allocation") != std::string::npos;
+    if (!oom) c.solved = false;
+    return fail(c, oom ? RS_ERR_OOM : RS_ERR_CUDA, c.err);
+  }
   c.cn_rank = -1;                          // the canonical form described the previous core
   int k2 = 0;
   if (flags & RS_POTENTIAL) {
