@@ -89,15 +89,6 @@ def reference_factors(t, a, h: float, n: int):
     return out
 
 
-def collocation_factors_at(t, a, y):
-    """Collocated 1-D factors a_k^{1/3} * exp(-t_k^2 y^2) at offsets ``y`` (any shape),
-    returned with a leading axis over k.  Sec. 3.2 (remark before Theorem 3.2) allows
-    collocation of the Gaussians at cell centres in place of the Galerkin projection;
-    used for particles that are not on grid points."""
-    y = np.asarray(y, dtype=np.float64)
-    return (a ** (1.0 / 3.0)).reshape((-1,) + (1,) * y.ndim) * np.exp(-(t.reshape((-1,) + (1,) * y.ndim) * y) ** 2)
-
-
 def split(R: int, R_s: int):
     """Index sets of the long- and short-range terms (Sec. 2.3, Eqs. (2.11)-(2.12)).
 
@@ -222,22 +213,6 @@ def side_matrices(j, z, pk, klong, n: int):
         idx = i[:, None] - j[None, :, l] + c
         U = pk[klong][:, idx] * w[None, None, :]             # (R_l, n, N)
         Us.append(np.ascontiguousarray(U.transpose(1, 2, 0).reshape(n, -1)))
-    xi = np.repeat(np.sign(z), len(klong))
-    return Us, xi
-
-
-def collocated_side_matrices(xyz, z, t, a, klong, xgrid):
-    """Side matrices for centres off the grid: column (nu, k) of U^(l) is
-    w_nu * a_k^{1/3} * exp(-t_k^2 (x_i - x_l^(nu))^2) (collocation, Sec. 3.2 remark before
-    Theorem 3.2), weights as in ``side_matrices``."""
-    z = np.asarray(z, dtype=np.float64)
-    w = np.abs(z) ** (1.0 / 3.0)
-    Us = []
-    for l in range(3):
-        y = xgrid[:, None] - xyz[None, :, l]                   # (n, N)
-        f = collocation_factors_at(t[klong], a[klong], y)      # (R_l, n, N)
-        U = f * w[None, None, :]
-        Us.append(np.ascontiguousarray(U.transpose(1, 2, 0).reshape(len(xgrid), -1)))
     xi = np.repeat(np.sign(z), len(klong))
     return Us, xi
 
@@ -378,15 +353,6 @@ def windows_points(j, z, pk, kshort, gamma: int, idx_pts):
     return out
 
 
-def rs_tucker_full(beta, Vs, j, z, pk, kshort, gamma, n):
-    """Full-grid value of the RS-Tucker tensor (Def. 3.9, Eq. (3.11)):
-    Tucker long-range part plus the cumulated short-range windows."""
-    return tucker_full(beta, Vs) + windows_full(j, z, pk, kshort, gamma, n)
-
-
-# ----------------------------------------------------------------------------
-# Tucker-to-canonical transform: the RS-canonical format  (Def. 3.7, Lemma 3.8)
-# ----------------------------------------------------------------------------
 def tucker_to_canonical(beta, Vs, eps: float):
     """Canonical form of the Tucker tensor beta x_1 V^(1) x_2 V^(2) x_3 V^(3), the long-range
     part of an RS-canonical tensor (Def. 3.7).  Sec. 3 reports RS-canonical ranks after a
