@@ -40,7 +40,7 @@ bool derive(const rs_config& cfg, Ctx& c, std::string& err) {
   if (cfg.rank_cap < 0 || cfg.max_rank < 0) { err = "rank_cap and max_rank must be >= 0"; return false; }
   if (!(cfg.delta_rel >= 0.0)) { err = "delta_rel must be >= 0"; return false; }
   if (cfg.precision < RS_FP64 || cfg.precision > RS_FP32) { err = "unknown precision"; return false; }
-  if (cfg.snap != 1) { err = "only snapped centres (snap = 1) are supported by this build"; return false; }
+  if (cfg.snap != 1) { err = "only snapped centres (snap = 1) are supported by rs_solve"; return false; }
   if (cfg.max_particles < 1) { err = "max_particles must be >= 1"; return false; }
   c.cfg = cfg;
   c.n = cfg.n;
