@@ -193,7 +193,9 @@ rs_status rs_get_canonical(rs_ctx* ctx, int* rank, const double** xi, const doub
  *   the RHOSVD tensor).  Forces are unchanged (they use the untruncated long-range kernel).
  * Afterwards rs_report (ranks, tail_rel of the mode matrices), rs_get_tucker, rs_eval_points and
  * rs_canonical see the refined tensor, and an earlier RS-canonical form is invalidated.
- * Synchronises once per mode update to read the ranks.  The first call allocates
+ * Synchronises: once per mode update to read the ranks, and at the end, where a device-side
+ * error of the refinement (RS_ERR_TIMEOUT of a bounded wait) is returned; warnings such as
+ * RS_RANK_CAPPED are left to rs_report.  The first call allocates
  * 8 (3 n R_l rmax + n rmax^2 + n K_c + K_c rmax^2) bytes of device memory (rmax the context's
  * rank bound, K_c = min(n R_l, 2^24 / rmax^2) rows of one chunk, so the last term is at most
  * 128 MiB), kept until rs_destroy.

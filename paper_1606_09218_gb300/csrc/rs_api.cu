@@ -639,7 +639,13 @@ rs_status rs_tucker_als(rs_ctx* h, int sweeps, int flags, void* potential_out) {
   // an energy not recomputed here belonged to the previous Tucker tensor
   c.last_flags = (c.last_flags & ~RS_ENERGY) | (flags & RS_ENERGY);
   c.launches = k + k2;
-  return check_launch(c, "tucker_als");
+  st = check_launch(c, "tucker_als");
+  if (st != RS_OK) return st;
+  // device-side errors of the refinement (a bounded wait of the eigen stage that ran out)
+  st = sync_scalars(c);
+  if (st != RS_OK) return st;
+  const rs_status dev = status_of(*c.h_sc);
+  return dev < 0 ? dev : RS_OK;
 }
 
 rs_status rs_get_canonical(rs_ctx* h, int* rank, const double** xi, const double** U, int* ld) {
