@@ -23,6 +23,14 @@
  *   - Work is asynchronous on the stream given to rs_create, except where a call says it
  *     synchronises.  Device pointers belong to the caller unless stated otherwise.
  *   - A context is not thread-safe; use one context per host thread or serialise calls.
+ *
+ * Typical sequence:
+ *     rs_create(&cfg, stream, &ctx);                       // workspace for cfg, once
+ *     rs_solve(ctx, N, xyz, Z, RS_POTENTIAL | RS_ENERGY, 0.0, P);   // per particle set
+ *     rs_energy(ctx, &E);                                  // synchronises
+ *     rs_report(ctx, &stats);                              // ranks, eps bound, status
+ *     rs_tucker_als(ctx, 1, RS_POTENTIAL | RS_ENERGY, P);  // optional: lower ranks, same eps
+ *     rs_destroy(ctx);
  */
 #ifndef RS_H
 #define RS_H
