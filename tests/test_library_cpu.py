@@ -61,3 +61,12 @@ def test_als_entry_rejects_a_null_context(lib):
     """rs_tucker_als checks its context before any device work."""
     from paper_1606_09218_gb300 import _lib
     assert lib.rs_tucker_als(None, 1, 0, None) == _lib.RS_ERR_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library the binding raises; there is no CPU fallback."""
+    from paper_1606_09218_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(_lib.RSError) as e:
+        _lib.load(str(tmp_path / "librs_gb300.so"))
+    assert "missing" in str(e.value)
