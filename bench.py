@@ -10,8 +10,10 @@ The metric is grid points per second (n^3 per solve).  For N > 1 (torchrun) ever
 solves its own seeded replica (independent problems, weak scaling, no data-path
 collective); the reported value is the whole-job rate over the slowest rank's time.
 
-The JSON line also carries a serving sub-report (``serving``): the 256-request workload
-c4 replayed with Poisson arrivals through the library's request loop, p50/p99 latency.
+The JSON line also carries sub-reports: the largest workload (the n = 1025 lattice) timed the
+same way (``large``), the forces workload (``forces``), the plain GPU paths, and the serving
+workload (``serving``: 256 requests through the library's request loop, replayed at their
+Poisson arrival times and all at once for the loop's capacity, p50/p99 latency).
 
 ``--impl reference`` times the FP64 CPU oracle (full-rank canonical sum at sampled grid
 points) on the host cores, on the same workload and metric.
@@ -128,23 +130,94 @@ def kernel_hash() -> str:
 NCU_TRAFFIC = {"9a7a9af54e93": 568.0e6}
 
 
-def oracle_rate(cfg, parts, seconds: float, seed: int = 0):
-    """Grid points per second of the CPU oracle's full-rank canonical sum on a random sample
-    of grid points (bounded to about ``seconds`` of work)."""
-    import numpy as np
+_WORKER_PROBLEM = None
+
+
+def _oracle_worker_init(cfg, xyz, Z):
+    """Pool initializer: one thread per process, and the oracle's problem built once."""
+    global _WORKER_PROBLEM
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
     from oracle import rs_oracle as O
-    pr = O.Problem(cfg, parts.xyz, parts.Z)
-    rng = np.random.default_rng(seed)
-    m = 64
-    t0 = time.perf_counter()
-    pr.P0_points(rng.integers(0, pr.n, (m, 3)))
-    dt = max(time.perf_counter() - t0, 1e-4)
-    M = int(max(64, min(2_000_000, m * seconds / dt)))
-    idx = rng.integers(0, pr.n, (M, 3))
-    t0 = time.perf_counter()
-    pr.P0_points(idx)
-    dt = time.perf_counter() - t0
-    return M / dt, M, dt
+    _WORKER_PROBLEM = O.Problem(cfg, xyz, Z)
+
+
+def _oracle_chunk(idx):
+    """Worker of the CPU baseline: the oracle's full-rank canonical sum at one chunk of grid
+    points (one process per host core, numpy on one thread each)."""
+    _WORKER_PROBLEM.P0_points(idx)
+    return len(idx)
+
+
+def host_cpu():
+    """(cores usable by this process, CPU model name) of the host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return cores, f"{model or 'unknown'} ({platform.machine()})"
+
+
+class OraclePool:
+    """The CPU oracle run over every host core: a process pool (spawn start) whose workers each
+    evaluate the full-rank canonical sum on their share of a random sample of grid points."""
+
+    def __init__(self, cfg, parts):
+        import multiprocessing as mp
+        self.cores, self.model = host_cpu()
+        self.cfg, self.xyz, self.Z = dict(cfg), parts.xyz, parts.Z
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init,
+                                                 initargs=(self.cfg, self.xyz, self.Z))
+        self.per_point = None
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def run(self, M: int, seed: int):
+        """Wall time of the M-point sample over the pool."""
+        import numpy as np
+        rng = np.random.default_rng(seed)
+        idx = rng.integers(0, int(self.cfg["n"]), (M, 3))
+        chunks = np.array_split(idx, self.cores * 4)
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_chunk, [c for c in chunks if len(c)])
+        return time.perf_counter() - t0
+
+    def rate(self, seconds: float, seed: int = 0):
+        """Grid points per second over the pool on a random sample sized for about ``seconds``
+        of wall time; returns (rate, points, wall seconds)."""
+        if self.per_point is None:
+            m = 64 * self.cores
+            self.per_point = max(self.run(m, 12345), 1e-4) / m
+        M = int(max(64 * self.cores, min(20_000_000, seconds / self.per_point)))
+        dt = self.run(M, seed)
+        self.per_point = dt / M
+        return M / dt, M, dt
+
+
+def workload_config(cfg, N):
+    """The workload keys shared by both arms of the bench line."""
+    return {"workload": cfg["name"], "N": int(N), "n": int(cfg["n"]), "R": int(cfg["R"]),
+            "R_s": int(cfg["R_s"]), "eps": cfg["eps"], "precision": cfg.get("precision")}
 
 
 def run_reference(args, rank, world):
@@ -153,27 +226,29 @@ def run_reference(args, rank, world):
     from workloads import load_config, make_particles
     cfg = load_config(args.workload)
     parts = make_particles(cfg)
-    n = int(cfg["n"])
     per_step = float(os.environ.get("RS_REF_STEP_S", "2.0"))
-    rates = []
-    for _ in range(args.warmup):
-        oracle_rate(cfg, parts, 0.2)
-    t_total, pts_total, M_last = 0.0, 0, 0
-    for s in range(args.steps):
-        r, M, dt = oracle_rate(cfg, parts, per_step, seed=s + 1)
-        rates.append(r)
-        t_total += dt
-        pts_total += M
-        M_last = M
+    pool = OraclePool(cfg, parts)
+    try:
+        for w in range(args.warmup):
+            pool.rate(0.2, seed=1000 + w)
+        t_total, pts_total, M_last = 0.0, 0, 0
+        for s in range(args.steps):
+            r, M, dt = pool.rate(per_step, seed=s + 1)
+            t_total += dt
+            pts_total += M
+            M_last = M
+    finally:
+        pool.close()
     value = pts_total / t_total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "N": int(len(parts.Z)), "n": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": workload_config(cfg, len(parts.Z)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "cpu_model": pool.model,
+                             "kind": "oracle",
                              "sample": f"{M_last} random grid points per step, full-rank canonical sum "
-                                       f"(N*R terms per point), numpy FP64, one thread"},
+                                       f"(N*R terms per point), numpy FP64, a process per core"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -181,12 +256,15 @@ def run_reference(args, rank, world):
 
 SERVING_WORKLOAD = "c4_serving256"
 FORCES_WORKLOAD = "c5_forces4096_n513"
+LARGE_WORKLOAD = "c3_nacl28_n1025"
 
 
-def serving_report(max_slots: int = 8, hbm_budget: int = 16 << 30):
+def serving_report(max_slots: int = 8, hbm_budget: int = 16 << 30, saturate: bool = False):
     """Replay the serving workload through the library's request loop (``rs_server_*``):
     requests of varying N and n arrive at their Poisson times with host inputs, each computes
-    the potential into its own device buffer and the energy; latency is submit to result."""
+    the potential into its own device buffer and the energy; latency is submit to result.
+    With ``saturate`` every request is submitted at t = 0 (the loop's capacity: solves/s and
+    latency under a full queue)."""
     import numpy as np
     import torch
     from paper_1606_09218_gb300 import RSServer, config_from_workload
@@ -206,9 +284,10 @@ def serving_report(max_slots: int = 8, hbm_budget: int = 16 << 30):
     t0 = time.perf_counter()
     tickets = []
     for r, pot in zip(reqs, pots):
-        dt = t0 + r.arrival_s - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
+        if not saturate:
+            dt = t0 + r.arrival_s - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
         tickets.append(srv.submit(cfgs[r.n], r.particles.xyz, r.particles.Z, potential=pot))
     res = [srv.wait(t) for t in tickets]
     span = time.perf_counter() - t0
@@ -223,14 +302,54 @@ def serving_report(max_slots: int = 8, hbm_budget: int = 16 << 30):
             errors[x["message"]] = errors.get(x["message"], 0) + 1
     pts = sum(r.n ** 3 for r in reqs)
     del pots
+    arrivals = (f"all {len(reqs)} submitted at t = 0 (saturation)" if saturate else
+                f"Poisson, mean gap {sv['mean_gap_ms']} ms, last at {reqs[-1].arrival_s:.3f} s")
     return {"workload": SERVING_WORKLOAD, "requests": len(reqs), "ok": ok, "errors": errors,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "queue_p50_ms": float(np.percentile(que, 50)),
             "queue_p99_ms": float(np.percentile(que, 99)), "span_s": span,
             "solves_per_s": len(reqs) / span, "grid_pts_per_s": pts / span,
-            "arrivals": f"Poisson, mean gap {sv['mean_gap_ms']} ms, last at {reqs[-1].arrival_s:.3f} s",
+            "arrivals": arrivals,
             "max_slots": max_slots, "hbm_budget_bytes": hbm_budget, "slots_at_end": info["slots"],
             "latency": "submit (host inputs) to result (energy on host, potential in a device buffer)"}
+
+
+def timed_solves(ctx, xyz, Z, pot, steps, flush, stream, forces=False):
+    """Device milliseconds of ``steps`` solves (CUDA events on the context stream, L2 flushed
+    before each) and the per-stage milliseconds per solve."""
+    import torch
+    ctx.profile(True)
+    ctx.profile_read()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s in range(steps):
+        flush.zero_()
+        starts[s].record(stream)
+        ctx.solve(xyz, Z, potential=pot, energy=True, want_potential=pot is not None, forces=forces)
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    stages, nsolves = ctx.profile_read()
+    ctx.profile(False)
+    return t_ms, {k: v / max(nsolves, 1) for k, v in stages.items()}
+
+
+def assembly_roofline(n, r1, per_launch_ms, pk, traffic=None):
+    """Roofline of the assembly kernel (Tucker mode-1 product plus the short-range windows, one
+    launch per solve): algorithmic bytes = the FP32 output written once, 4 n^3; the Tucker slab
+    it reads (T2, r1 x n^2 values stored as FP16 hi/lo pairs, 4 r1 n^2 bytes) is an intermediate
+    of this implementation and is reported beside it, not counted."""
+    bytes_alg = 4 * n ** 3
+    ach = bytes_alg / (per_launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / pk["hbm_gbs"],
+            "kernel": "assemble_kernel (tcgen05 kind::f16: FP16-split Tucker product and windows, one pass)",
+            "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "peak_source": pk["source"] + " hbm_gbs (copy, burst)",
+            "ms_per_launch": per_launch_ms, "algorithmic_bytes": bytes_alg,
+            "bytes_formula": "4*n^3 (FP32 output written once)",
+            "t2_read_bytes": 4 * r1 * n * n}
 
 
 def replica_seed(rank: int, index: int):
@@ -277,6 +396,7 @@ def run_ours(args, rank, world, local_rank):
     Z = torch.tensor(parts.Z, device="cuda")
     pot = ctx.new_potential()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    pk = peaks()
 
     def barrier():
         torch.cuda.synchronize()
@@ -289,28 +409,18 @@ def run_ours(args, rank, world, local_rank):
     E = ctx.energy()
     rep = ctx.report()
     # timed region: device time of K solves, L2 flushed before each
-    ctx.profile(True)
-    ctx.profile_read()
     sampler = ClockSampler(local_rank)
     sampler.start()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
-    for s in range(args.steps):
-        flush.zero_()
-        starts[s].record(stream)
-        ctx.solve(xyz, Z, potential=pot, energy=True)
-        ends[s].record(stream)
+    t_ms, stages = timed_solves(ctx, xyz, Z, pot, args.steps, flush, stream)
     barrier()
     clocks = sampler.stop()
-    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    stages, nsolves = ctx.profile_read()
-    ctx.profile(False)
     launches = ctx.report()["kernel_launches"] * args.steps
     t_ms = max_over_ranks(t_ms, dist, "cuda")
     value = whole_job_rate(n ** 3, args.steps, world, t_ms * 1e-3)
 
-    # end to end through the C ABI with host buffers (pinned), energy read back each step
+    # end to end through the C ABI with host buffers (pinned): the inputs copied in and the
+    # energy read back every step, the potential left in the caller's device buffer
     hx = torch.tensor(parts.xyz).pin_memory()
     hz = torch.tensor(parts.Z).pin_memory()
     hxn, hzn = hx.numpy(), hz.numpy()
@@ -322,6 +432,19 @@ def run_ours(args, rank, world, local_rank):
         ctx.energy()
     t_e2e = time.perf_counter() - t0
     e2e_value = whole_job_rate(n ** 3, e2e_steps, world, max_over_ranks(t_e2e, dist, "cuda"))
+    # the same with the whole potential grid copied back to pinned host memory every step
+    hpot = torch.empty(pot.shape, dtype=pot.dtype).pin_memory()
+    grid_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(grid_steps):
+        ctx.solve(hxn, hzn, potential=pot, energy=True)
+        hpot.copy_(pot, non_blocking=True)
+        ctx.energy()
+        torch.cuda.current_stream().synchronize()
+    t_grid = time.perf_counter() - t0
+    e2e_grid_value = whole_job_rate(n ** 3, grid_steps, world, max_over_ranks(t_grid, dist, "cuda"))
+    del hpot
 
     # plain RS path on the same GPU: every stage in FP64
     plain = None
@@ -332,18 +455,8 @@ def run_ours(args, rank, world, local_rank):
         ppot = pctx.new_potential()
         for _ in range(2):
             pctx.solve(xyz, Z, potential=ppot, energy=True)
-        torch.cuda.synchronize()
         ps = max(3, min(args.steps, 10))
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        tp = 0.0
-        for _ in range(ps):
-            flush.zero_()
-            a.record(stream)
-            pctx.solve(xyz, Z, potential=ppot, energy=True)
-            b.record(stream)
-            torch.cuda.synchronize()
-            tp += a.elapsed_time(b)
+        tp, _ = timed_solves(pctx, xyz, Z, ppot, ps, flush, stream)
         plain = {"value": n ** 3 * ps / (tp * 1e-3), "unit": UNIT, "ms_per_step": tp / ps,
                  "path": "same RS pipeline with every stage in FP64 (Tucker core, mode products, output)"}
         pctx.close()
@@ -355,29 +468,14 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel: the assembly of the grid (Tucker mode-1 product plus the
-    # short-range windows, one launch per step, "reconstruct" stage).  Algorithmic bytes per
-    # launch: the FP32 output written once plus the Tucker slab T2 (r1 x n^2 values) read once;
-    # the FP16 hi/lo tiles of T2 hold 4 bytes per value, the same as one FP32 copy.
-    pk = peaks()
-    r1 = rep["ranks"][0]
-    per_launch_ms = stages["reconstruct"] / max(nsolves, 1)
-    bytes_alg = 4 * n ** 3 + 4 * r1 * n * n
-    ach = bytes_alg / (per_launch_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / pk["hbm_gbs"],
-            "kernel": "assemble_kernel (tcgen05 kind::f16: FP16-split Tucker product and windows, one pass)",
-            "traffic": NCU_TRAFFIC.get(kernel_hash()) if args.workload == DEFAULT_WORKLOAD else None,
-            "traffic_unit": "bytes per launch (ncu dram read + write)",
-            "peak_source": pk["source"] + " hbm_gbs (copy, burst)",
-            "ms_per_launch": per_launch_ms, "algorithmic_bytes": bytes_alg,
-            "bytes_formula": "4*n^3 (output) + 4*r1*n^2 (T2 slab)"}
+    roof = assembly_roofline(n, rep["ranks"][0], stages["reconstruct"], pk,
+                             NCU_TRAFFIC.get(kernel_hash()) if args.workload == DEFAULT_WORKLOAD else None)
 
     # plain-method GPU paths on the same particles and grid: direct sum and full-rank
     # canonical sum (one timed run each after a warm-up), with the RS grid's relative
     # difference from the canonical sum over the whole grid
     plain_methods = None
-    if rank == 0 and not args.no_plain:
+    if not args.no_plain:
         plain_methods = {}
         ctx.solve(xyz, Z, potential=pot, energy=True)
         a = torch.cuda.Event(enable_timing=True)
@@ -399,16 +497,50 @@ def run_ours(args, rank, world, local_rank):
             plain_methods[name] = entry
         del outp
 
-    # energy and forces at centres off the grid (forces workload, N = 4096): the RS kernel in
-    # pair form, one timed call after a warm-up
+    # the largest workload (lattice, n = 1025, N = 19,757, eps = 1e-5): whole solves timed the
+    # same way, with its stage breakdown and the assembly roofline
+    large = None
+    if not args.no_plain and args.workload != LARGE_WORKLOAD:
+        try:
+            lcfg = load_config(LARGE_WORKLOAD)
+            lp = make_particles(lcfg)
+            lctx = RSContext(config_from_workload(lcfg))
+            lx = torch.tensor(lp.xyz, device="cuda")
+            lz = torch.tensor(lp.Z, device="cuda")
+            lpot = lctx.new_potential()
+            for _ in range(2):
+                lctx.solve(lx, lz, potential=lpot, energy=True)
+            lrep = lctx.report()
+            ls = 5
+            tl, lst = timed_solves(lctx, lx, lz, lpot, ls, flush, stream)
+            ln = int(lcfg["n"])
+            large = {"workload": LARGE_WORKLOAD, "N": int(len(lp.Z)), "n": ln, "eps": lcfg["eps"],
+                     "ms_per_step": tl / ls, "value": ln ** 3 * ls / (tl * 1e-3), "unit": UNIT,
+                     "ranks": lrep["ranks"], "subspace": lrep["subspace"], "status": lrep["status"],
+                     "energy": lctx.energy(), "stages_ms_per_step": lst,
+                     "roofline": assembly_roofline(ln, lrep["ranks"][0], lst["reconstruct"], pk)}
+            lctx.close()
+            del lpot
+        except Exception as e:  # reported, not fatal to the bench line
+            large = {"error": str(e)}
+
+    # forces workload (N = 4096, Z = +-1): the RS solve with forces at snapped centres (adjoint,
+    # Sec. 4.3), and energy and forces at centres off the grid (the RS kernel in pair form)
     forces = None
-    if rank == 0 and not args.no_plain:
+    if not args.no_plain:
         fcfg = load_config(FORCES_WORKLOAD)
         fp = make_particles(fcfg)
         fN = int(len(fp.Z))
         fctx = RSContext(config_from_workload(dict(fcfg, snap=True), max_particles=fN))
         fx = torch.tensor(fp.xyz, device="cuda")
         fz = torch.tensor(fp.Z, device="cuda")
+        fn_ = int(fcfg["n"])
+        fpot = fctx.new_potential()
+        for _ in range(2):
+            fctx.solve(fx, fz, potential=fpot, energy=True, forces=True)
+        fs = 5
+        tf, fst = timed_solves(fctx, fx, fz, fpot, fs, flush, stream, forces=True)
+        frep = fctx.report()
         fctx.pair_energy_forces(fx, fz)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -418,17 +550,24 @@ def run_ours(args, rank, world, local_rank):
         b.record(torch.cuda.current_stream())
         torch.cuda.synchronize()
         fms = a.elapsed_time(b)
-        forces = {"workload": FORCES_WORKLOAD, "N": fN, "ms": fms, "pairs_per_s": fN * (fN - 1) / (fms * 1e-3),
-                  "energy": fE, "path": "rs_pair_energy_forces: RS kernel in pair form at unsnapped centres, "
-                                        "FP32 factors, FP64 sums (energy and adjoint forces, one call)"}
+        forces = {"workload": FORCES_WORKLOAD, "N": fN, "n": fn_,
+                  "solve_with_forces": {"ms_per_step": tf / fs, "value": fn_ ** 3 * fs / (tf * 1e-3),
+                                        "unit": UNIT, "ranks": frep["ranks"], "stages_ms_per_step": fst,
+                                        "path": "rs_solve with RS_POTENTIAL | RS_ENERGY | RS_FORCES at "
+                                                "snapped centres"},
+                  "offgrid_pair": {"ms": fms, "pairs_per_s": fN * (fN - 1) / (fms * 1e-3), "energy": fE,
+                                   "path": "rs_pair_energy_forces: RS kernel in pair form at unsnapped "
+                                           "centres, FP32 factors, FP64 sums (energy and forces, one call)"}}
         fctx.close()
+        del fpot
 
     # RS-canonical form of the last solve (Def. 3.7): the Tucker-to-canonical transform at the
     # accuracy the paper's RS-canonical ranks are quoted at (eps_T2C = 4e-6), and point values of
     # the canonical form (3 R* products per point, Lemma 3.8) against those of the Tucker form
     # (r1 r2 per point, Lemma 3.10), both with the windows, on 2^20 random grid points
     canonical = None
-    if rank == 0 and not args.no_plain:
+    if not args.no_plain:
+        ctx.solve(xyz, Z, potential=pot, energy=True)
         eps_c = 4e-6
         ctx.canonical(eps_c)
         torch.cuda.synchronize()
@@ -459,7 +598,7 @@ def run_ours(args, rank, world, local_rank):
     # eps-truncated ranks after a fresh solve, timed as one call (it synchronises once per mode
     # update to read the ranks), the refined grid against the full-rank canonical sum
     als = None
-    if rank == 0 and not args.no_plain:
+    if not args.no_plain:
         try:
             ctx.solve(xyz, Z, potential=pot, energy=True)
             ctx.tucker_als(1, potential=pot)           # the first call allocates its buffers
@@ -486,33 +625,42 @@ def run_ours(args, rank, world, local_rank):
 
     serving = None
     if not args.no_serving:
-        serving = serving_report()
+        serving = {"poisson": serving_report(), "saturation": serving_report(saturate=True)}
 
     cpu = None
     if not args.no_cpu:
-        r, M, dt = oracle_rate(cfg, parts, float(os.environ.get("RS_CPU_SAMPLE_S", "12")))
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+        pool = OraclePool(cfg, parts)
+        try:
+            r, M, dt = pool.rate(float(os.environ.get("RS_CPU_SAMPLE_S", "12")))
+        finally:
+            pool.close()
+        cpu = {"value": r, "unit": UNIT, "cores": pool.cores, "cpu_model": pool.model, "kind": "oracle",
                "sample": f"{M} random grid points, full-rank canonical sum (N*R terms per point), "
-                         f"numpy FP64, one thread, {dt:.1f} s"}
+                         f"numpy FP64, a process per core, {dt:.1f} s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "N": N, "n": n, "R": int(cfg["R"]), "R_s": int(cfg["R_s"]),
-                   "eps": cfg["eps"], "precision": cfg.get("precision"), "ranks": rep["ranks"],
-                   "gamma": rep["gamma"], "l2": "256 MiB written before every timed step",
-                   "replicas": "one independent seeded problem per rank"},
+        "config": dict(workload_config(cfg, N), l2="256 MiB written before every timed step",
+                       replicas="one independent seeded problem per rank"),
+        "solve": {"ranks": rep["ranks"], "subspace": rep["subspace"], "gamma": rep["gamma"],
+                  "status": rep["status"], "energy": E},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * 4 * 8),
-                "d2h_bytes_per_step": 16, "steps": e2e_steps},
+                "d2h_bytes_per_step": 16, "steps": e2e_steps,
+                "output": "potential device-resident (caller's buffer); energy and status read back"},
+        "e2e_host_grid": {"value": e2e_grid_value, "unit": UNIT, "h2d_bytes_per_step": int(N * 4 * 8),
+                          "d2h_bytes_per_step": int(pot.numel() * pot.element_size()) + 16, "steps": grid_steps,
+                          "output": "potential copied to pinned host memory every step"},
         "gpu_launches": launches,
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "stages_ms_per_step": {k: v / max(nsolves, 1) for k, v in stages.items()},
+        "stages_ms_per_step": stages,
         "plain_gpu": plain,
         "plain_methods": plain_methods,
+        "large": large,
         "forces": forces,
         "canonical": canonical,
         "als": als,

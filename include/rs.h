@@ -156,6 +156,26 @@ rs_status rs_report(rs_ctx* ctx, rs_stats* st);
 rs_status rs_get_tucker(rs_ctx* ctx, int ranks[3], int* ld_V, int* ld_b,
                         const void* V[3], const void** beta);
 
+/* Device pointers to the short-range part of the RS-Tucker tensor of the last solve
+ * (Def. 3.9): the uniform cumulated canonical tensor of Def. 3.6, one local reference tensor of
+ * R_s canonical terms on a window of n_s = 2 gamma + 1 grid points per axis (Def. 3.4, the window
+ * width of Sec. 2.3, criterion (A)), shifted to every centre and weighted by its charge:
+ *   W[i1][i2][i3] = sum_nu z_nu sum_{k < R_s} f_k[i1 - j1 + gamma] f_k[i2 - j2 + gamma] f_k[i3 - j3 + gamma]
+ * over the centres nu with |i_l - j_l| <= gamma in every mode (j = the centre's grid indices).
+ * Together with rs_get_tucker this is the whole RS-Tucker state (storage r1 r2 r3 + 3 n r +
+ * R_s n_s + 4 N numbers).  Outputs (valid until the next rs_solve or rs_destroy; synchronises to
+ * read gamma):
+ *   *n_s, *R_s: window width and number of short-range terms;  *N: centres of the last solve;
+ *   factors: FP64 table of R_s rows, row k at factors + k * (*ld_f), entries n_s: the Galerkin
+ *            factors p_k (Eq. (2.5)) of the R_s short-range sinc nodes at the offsets
+ *            -gamma..gamma (in every precision);
+ *   grid_idx: int32 N x 3 row-major, the snapped grid indices of the centres (Sec. 3.2);
+ *   charges: FP64 N, the charges as given (zero charges add nothing).
+ * The buffers belong to the context.  Errors: RS_ERR_INVALID_ARG (null pointer),
+ * RS_ERR_NOT_READY (no solve), RS_ERR_CUDA. */
+rs_status rs_get_windows(rs_ctx* ctx, int* n_s, int* R_s, int* N, const double** factors, int* ld_f,
+                         const int** grid_idx, const double** charges);
+
 /* Evaluate the RS-Tucker tensor of the last solve at M grid multi-indices (Lemma 3.10):
  * idx: device int32 array (M x 3), out: device double array (M).  Asynchronous. */
 rs_status rs_eval_points(rs_ctx* ctx, int M, const int* idx, double* out);
@@ -242,12 +262,15 @@ const char* rs_stage_name(int stage);
  * for centres snapped to the grid of cfg (only b, n, R, R_s, h_q, u0, delta_rel are used):
  *   xyz (N x 3) and Z (N): device pointers, float64;   G: device output, 3 x n x n, C order.
  * Scratch: a fixed 16 MiB device array inside the library, held by every GPU that loads the
- * library until the process exits; problems that do not fit (roughly n > 513) are rejected
- * with RS_ERR_CAPACITY and a message in rs_last_error(NULL).  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  Every call reuses the same array, so calls that overlap on the
- * GPU (different streams, or several host threads) race: serialise them.  Centres outside
- * the box are clamped to its boundary; errors: RS_ERR_INVALID_ARG, RS_ERR_CAPACITY, RS_ERR_CUDA. */
+ * library until the process exits; problems that do not fit (n above 513, or more centres than
+ * the message states) are rejected with RS_ERR_CAPACITY and a message in rs_last_error(NULL).
+ * Every call looks up the array's device address (cudaGetSymbolAddress, which allocates
+ * nothing) for the current device.  Every call reuses the same array, so calls that overlap on
+ * the GPU (different streams, or several host threads) race: serialise them.  The call
+ * synchronises the stream at its end to read the status word of the particle kernels: a centre
+ * outside [-b,b]^3 or a non-finite coordinate or charge gives RS_ERR_OUTSIDE_BOX (G is then not
+ * the Gram matrix of the input).  Errors: RS_ERR_INVALID_ARG, RS_ERR_OUTSIDE_BOX, RS_ERR_CAPACITY,
+ * RS_ERR_CUDA. */
 rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* xyz, const double* Z,
                           double* G, void* cuda_stream);
 
@@ -260,7 +283,7 @@ rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* xyz, const 
  * configurations are released to make room) and at most max_slots slots exist; admitted requests
  * run concurrently.  The queue is scanned in arrival order; a request that cannot be admitted
  * yet does not hold back later ones that can.  Results match a solve of the same request alone
- * (separate workspaces; only the order of FP64 atomic sums may differ). */
+ * (separate workspaces and a fixed order of every floating-point sum: bit for bit). */
 typedef struct rs_server rs_server;
 
 typedef struct {

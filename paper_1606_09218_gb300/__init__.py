@@ -218,6 +218,25 @@ class RSContext:
         del es
         return list(ranks), Vs, bfull[: ranks[0], : ranks[1], : ranks[2]]
 
+    def windows(self):
+        """Short-range part of the last solve (rs_get_windows; Defs. 3.4, 3.6): (gamma, factors
+        (R_s, n_s) float64, grid indices (N, 3) int32, charges (N,) float64) as torch views of
+        the library's buffers (valid until the next solve)."""
+        torch = self._torch
+        ns, rs_, N, ld = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        f, j, z = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _lib.check(self.lib.rs_get_windows(self.h, C.byref(ns), C.byref(rs_), C.byref(N), C.byref(f), C.byref(ld),
+                                           C.byref(j), C.byref(z)), self.h)
+        R_s, n_s, L, NN = rs_.value, ns.value, ld.value, N.value
+        fac = torch.as_tensor(_DevArray(f.value, (R_s, n_s), "<f8", strides=(8 * L, 8)), device="cuda")
+        if NN > 0:
+            jj = torch.as_tensor(_DevArray(j.value, (NN, 3), "<i4"), device="cuda")
+            zz = torch.as_tensor(_DevArray(z.value, (NN,), "<f8"), device="cuda")
+        else:
+            jj = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
+            zz = torch.zeros(0, dtype=torch.float64, device="cuda")
+        return (n_s - 1) // 2, fac, jj, zz
+
     def debug_buffer(self, name: str, dtype=None):
         """A torch (uint8 or ``dtype``) view of an internal device buffer (inspection hook)."""
         torch = self._torch

@@ -34,7 +34,7 @@ RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_FORCES, RS_VALIDATE_SEPARATION = 1, 2
 
 #: every symbol ``include/rs.h`` declares
 EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_energy", "rs_forces", "rs_report",
-            "rs_get_tucker", "rs_eval_points", "rs_canonical", "rs_canonical_eval_points", "rs_get_canonical",
+            "rs_get_tucker", "rs_get_windows", "rs_eval_points", "rs_canonical", "rs_canonical_eval_points", "rs_get_canonical",
             "rs_tucker_als",
             "rs_profile_enable", "rs_profile_read", "rs_stage_name",
             "rs_debug_buffer", "rs_gram_noalloc", "rs_plain_direct", "rs_plain_canonical",
@@ -119,6 +119,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.rs_get_tucker.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(vp), C.POINTER(vp)]
     lib.rs_get_tucker.restype = C.c_int
+    ip = C.POINTER(C.c_int)
+    lib.rs_get_windows.argtypes = [vp, ip, ip, ip, C.POINTER(vp), ip, C.POINTER(vp), C.POINTER(vp)]
+    lib.rs_get_windows.restype = C.c_int
     lib.rs_eval_points.argtypes = [vp, C.c_int, vp, vp]
     lib.rs_eval_points.restype = C.c_int
     lib.rs_canonical.argtypes = [vp, C.c_double, C.POINTER(C.c_int)]

@@ -533,6 +533,28 @@ rs_status rs_get_tucker(rs_ctx* h, int ranks[3], int* ld_V, int* ld_b, const voi
   return RS_OK;
 }
 
+rs_status rs_get_windows(rs_ctx* h, int* n_s, int* R_s, int* N, const double** factors, int* ld_f,
+                         const int** grid_idx, const double** charges) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!n_s || !R_s || !N || !factors || !ld_f || !grid_idx || !charges)
+    return fail(c, RS_ERR_INVALID_ARG, "get_windows: null output");
+  if (!c.solved) return fail(c, RS_ERR_NOT_READY, "no solve");
+  rs_status st = sync_scalars(c);
+  if (st != RS_OK) return st;
+  const int g = c.h_sc->gamma;
+  *n_s = 2 * g + 1;
+  *R_s = c.R_s;
+  *N = c.last_N;
+  // the short-range rows of the factor table, from offset -gamma (the table holds the offsets
+  // -(n-1)..(n-1), row length L)
+  *factors = c.pk64 + (size_t)c.R_l * c.L + (size_t)(c.n - 1 - g);
+  *ld_f = c.L;
+  *grid_idx = c.j;
+  *charges = c.Z;
+  return RS_OK;
+}
+
 rs_status rs_eval_points(rs_ctx* h, int M, const int* idx, double* out) {
   if (!h) return RS_ERR_INVALID_ARG;
   Ctx& c = h->c;

@@ -11,7 +11,6 @@
 #include "rs_internal.cuh"
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 namespace rs {
@@ -39,11 +38,6 @@ namespace {
 constexpr size_t kNoAllocBytes = 16u << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// device address of g_noalloc_scratch, looked up once per device
-constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
@@ -61,50 +55,38 @@ extern "C" rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* 
     return RS_ERR_INVALID_ARG;
   }
   const int L = 2 * n - 1, R_l = R - R_s;
-  // scratch layout: scalars | pk64 | pk32 | dpk64 | dpk32 | j | C | nzj | F
+  // scratch layout: scalars | pk64 | C | nzj | F | j (the grid indices last: they grow with N)
   size_t off = 0;
   const size_t o_sc = off;   off = align256(off + sizeof(DevScalars));
   const size_t o_pk64 = off; off = align256(off + sizeof(double) * (size_t)R * L);
-  const size_t o_pk32 = off; off = align256(off + sizeof(float) * (size_t)R * L);
-  const size_t o_dpk64 = off; off = align256(off + sizeof(double) * (size_t)R * L);
-  const size_t o_dpk32 = off; off = align256(off + sizeof(float) * (size_t)R * L);
-  const size_t o_j = off;    off = align256(off + sizeof(int) * 3 * (size_t)(N > 0 ? N : 1));
   const size_t o_C = off;    off = align256(off + sizeof(double) * 3 * (size_t)n);
   const size_t o_nzj = off;  off = align256(off + sizeof(int) * 3 * (size_t)n);
   const size_t o_F = off;    off = align256(off + sizeof(double) * (size_t)L * L);
+  const size_t o_j = off;
+  const size_t fixed = off;
+  off = align256(off + sizeof(int) * 3 * (size_t)(N > 0 ? N : 1));
   if (off > kNoAllocBytes) {
+    const long long nmax = fixed < kNoAllocBytes ? (long long)((kNoAllocBytes - fixed) / (3 * sizeof(int))) : 0;
     set_host_error("rs_gram_noalloc: problem needs " + std::to_string(off) +
-                   " bytes of scratch, above the fixed 16 MiB (n up to 513 with N up to ~100000)");
+                   " bytes of scratch, above the fixed 16 MiB (at n = " + std::to_string(n) + ", R = " +
+                   std::to_string(R) + " up to N = " + std::to_string(nmax) + " centres fit)");
     return RS_ERR_CAPACITY;
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    set_host_error("rs_gram_noalloc: no usable current device");
-    return RS_ERR_CUDA;
-  }
-  unsigned char* base = nullptr;
+  // The device address of the array is looked up on every call (the lookup allocates
+  // nothing): a cached address would be stale after the context of the device was reset.
+  void* sym = nullptr;
   {
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        set_host_error(std::string("rs_gram_noalloc: cudaGetSymbolAddress failed: ") +
-                       cudaGetErrorString(e));
-        return RS_ERR_CUDA;
-      }
-      g_scratch_ptr[dev] = p;
+    cudaError_t e = cudaGetSymbolAddress(&sym, g_noalloc_scratch);
+    if (e != cudaSuccess || !sym) {
+      cudaGetLastError();
+      set_host_error(std::string("rs_gram_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+      return RS_ERR_CUDA;
     }
-    base = (unsigned char*)g_scratch_ptr[dev];
   }
+  unsigned char* base = (unsigned char*)sym;
   cudaStream_t s = (cudaStream_t)stream;
   DevScalars* sc = (DevScalars*)(base + o_sc);
   double* pk64 = (double*)(base + o_pk64);
-  float* pk32 = (float*)(base + o_pk32);
-  double* dpk64 = (double*)(base + o_dpk64);
-  float* dpk32 = (float*)(base + o_dpk32);
   int* j = (int*)(base + o_j);
   double* C = (double*)(base + o_C);
   int* nzj = (int*)(base + o_nzj);
@@ -114,7 +96,8 @@ extern "C" rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* 
   cudaMemsetAsync(sc, 0, sizeof(DevScalars), s);
   cudaMemsetAsync(C, 0, sizeof(double) * 3 * (size_t)n, s);
   const int tot = R * L;
-  factors_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pk64, pk32, nullptr, dpk64, dpk32, R, n, h, cfg->h_q, cfg->u0);
+  factors_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pk64, nullptr, nullptr, nullptr, nullptr, R, n, h, cfg->h_q,
+                                                   cfg->u0);
   scalars_kernel<<<1, 256, 0, s>>>(pk64, R, R_l, n, cfg->delta_rel, sc);
   if (N > 0) {
     prepare_kernel<<<(N + 255) / 256, 256, 0, s>>>(xyz, Z, N, n, cfg->b, h, j, sc);
@@ -128,6 +111,20 @@ extern "C" rs_status rs_gram_noalloc(const rs_config* cfg, int N, const double* 
   if (e != cudaSuccess) {
     set_host_error(std::string("rs_gram_noalloc: launch failed: ") + cudaGetErrorString(e));
     return RS_ERR_CUDA;
+  }
+  // the status word the particle kernels set: a centre outside the box or a non-finite input
+  // leaves that particle out of the sums, so the call reports it instead of returning G
+  unsigned flags = 0;
+  e = cudaMemcpyAsync(&flags, &sc->flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_host_error(std::string("rs_gram_noalloc: ") + cudaGetErrorString(e));
+    return RS_ERR_CUDA;
+  }
+  if (flags & FLAG_OUTSIDE) {
+    set_host_error("rs_gram_noalloc: a centre outside [-b,b]^3 or a non-finite coordinate or charge");
+    return RS_ERR_OUTSIDE_BOX;
   }
   return RS_OK;
 }

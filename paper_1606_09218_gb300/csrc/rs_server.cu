@@ -8,6 +8,11 @@
 // requests run concurrently on their streams; the worker polls the events, reads the results and
 // wakes the waiters.  The queue is scanned in arrival order, and a request that cannot be
 // admitted yet does not block later requests that can.
+//
+// Locking: the mutex guards the shared queue, the ticket table, the results and the counters
+// that rs_server_info reads.  The slots belong to the worker thread alone, so the worker creates
+// contexts (device allocations), runs the host-side checks of rs_solve and enqueues work without
+// the mutex: rs_submit and rs_wait never wait behind those calls.
 #include "rs_internal.cuh"
 
 #include <chrono>
@@ -52,7 +57,12 @@ struct Slot {
   std::shared_ptr<Job> job;
 };
 
-bool same_config(const rs_config& a, const rs_config& b) { return std::memcmp(&a, &b, sizeof(rs_config)) == 0; }
+// field by field: a caller's rs_config may carry uninitialised padding bytes
+bool same_config(const rs_config& a, const rs_config& b) {
+  return a.b == b.b && a.n == b.n && a.R == b.R && a.R_s == b.R_s && a.h_q == b.h_q && a.u0 == b.u0 &&
+         a.eps == b.eps && a.rank_cap == b.rank_cap && a.max_rank == b.max_rank && a.delta_rel == b.delta_rel &&
+         a.precision == b.precision && a.snap == b.snap && a.max_particles == b.max_particles;
+}
 
 }  // namespace
 
@@ -62,10 +72,13 @@ struct rs_server {
   int device = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<std::shared_ptr<Job>> pending;
-  std::unordered_map<unsigned long long, std::shared_ptr<Job>> jobs;
-  std::vector<std::unique_ptr<Slot>> slots;
-  size_t used = 0;
+  std::deque<std::shared_ptr<Job>> pending;       // submitted, not yet seen by the worker (mu)
+  std::unordered_map<unsigned long long, std::shared_ptr<Job>> jobs;   // (mu)
+  std::deque<std::shared_ptr<Job>> waiting;       // seen by the worker, not admitted (worker only)
+  std::vector<std::unique_ptr<Slot>> slots;       // (worker only)
+  size_t used = 0;                                // (worker only)
+  int info_slots = 0, info_waiting = 0;           // published copies for rs_server_info (mu)
+  size_t info_used = 0;
   unsigned long long next_ticket = 1;
   bool stop = false;
   std::thread worker;
@@ -105,15 +118,22 @@ struct rs_server {
     return slots.back().get();
   }
 
+  // publish a result (takes the mutex: rs_wait reads it)
   void finish(const std::shared_ptr<Job>& job, rs_status st, Slot* s) {
-    job->res.status = st;
+    const auto now = Clock::now();
+    char msg[sizeof(job->res.message)] = {0};
     if (st < 0) {
       const char* m = rs_last_error(s ? s->ctx : nullptr);
-      std::snprintf(job->res.message, sizeof(job->res.message), "%s", (m && *m) ? m : "error");
+      std::snprintf(msg, sizeof(msg), "%s", (m && *m) ? m : "error");
     }
-    job->res.latency_ms = ms_between(job->t_sub, Clock::now());
-    job->res.queue_ms = ms_between(job->t_sub, job->t_launch);
-    job->done = true;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      job->res.status = st;
+      if (st < 0) std::memcpy(job->res.message, msg, sizeof(msg));
+      job->res.latency_ms = ms_between(job->t_sub, now);
+      job->res.queue_ms = ms_between(job->t_sub, job->t_launch);
+      job->done = true;
+    }
     cv_done.notify_all();
   }
 
@@ -151,10 +171,11 @@ struct rs_server {
     finish(job, st, s);
   }
 
-  // one pass of admissions in arrival order; returns true if anything was launched
+  // one pass of admissions in arrival order (worker thread, without the mutex); returns true if
+  // anything was launched
   bool admit() {
     bool any = false;
-    for (auto it = pending.begin(); it != pending.end();) {
+    for (auto it = waiting.begin(); it != waiting.end();) {
       std::shared_ptr<Job> job = *it;
       Slot* chosen = nullptr;
       for (auto& s : slots)
@@ -162,7 +183,7 @@ struct rs_server {
       if (!chosen) {
         const size_t need = rs_workspace_bytes(&job->cfg);
         if (need == 0) {                                   // invalid configuration
-          it = pending.erase(it);
+          it = waiting.erase(it);
           job->t_launch = Clock::now();
           finish(job, RS_ERR_INVALID_ARG, nullptr);
           continue;
@@ -191,23 +212,29 @@ struct rs_server {
           }
         }
         if (!chosen && slots.empty()) {                    // cannot run even alone
-          it = pending.erase(it);
+          it = waiting.erase(it);
           job->t_launch = Clock::now();
           finish(job, RS_ERR_OOM, nullptr);
           continue;
         }
       }
       if (!chosen) { ++it; continue; }
-      it = pending.erase(it);
+      it = waiting.erase(it);
       launch(chosen, job);
       any = true;
     }
     return any;
   }
 
+  void publish_info() {
+    std::lock_guard<std::mutex> lk(mu);
+    info_slots = (int)slots.size();
+    info_used = used;
+    info_waiting = (int)waiting.size();
+  }
+
   void run() {
     cudaSetDevice(device);
-    std::unique_lock<std::mutex> lk(mu);
     while (true) {
       bool busy = false;
       for (auto& s : slots)
@@ -216,18 +243,32 @@ struct rs_server {
           if (cudaEventQuery(s->ev) == cudaSuccess) complete(s.get());
         }
       cudaGetLastError();                                  // cudaErrorNotReady from the polls
+      bool stopping = false;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        while (!pending.empty()) {
+          waiting.push_back(pending.front());
+          pending.pop_front();
+        }
+        stopping = stop;
+      }
       const bool launched = admit();
+      publish_info();
       bool running = false;
       for (auto& s : slots) running = running || (s->job != nullptr);
-      if (stop && pending.empty() && !running) break;
+      if (stopping && waiting.empty() && !running) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (pending.empty()) break;
+        continue;
+      }
       if (!launched) {
-        if (running || busy)
-          cv_work.wait_for(lk, std::chrono::microseconds(50));
-        else
-          cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        std::unique_lock<std::mutex> lk(mu);
+        if (pending.empty() && !stop)
+          cv_work.wait_for(lk, (running || busy) ? std::chrono::microseconds(50) : std::chrono::microseconds(5000));
       }
     }
     while (!slots.empty()) release_slot(slots.size() - 1);
+    publish_info();
   }
 };
 
@@ -300,8 +341,8 @@ extern "C" void rs_server_destroy(rs_server* s) {
 extern "C" rs_status rs_server_info(rs_server* s, int* slots, size_t* bytes_in_use, int* queued) {
   if (!s) return RS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
-  if (slots) *slots = (int)s->slots.size();
-  if (bytes_in_use) *bytes_in_use = s->used;
-  if (queued) *queued = (int)s->pending.size();
+  if (slots) *slots = s->info_slots;
+  if (bytes_in_use) *bytes_in_use = s->info_used;
+  if (queued) *queued = (int)s->pending.size() + s->info_waiting;
   return RS_OK;
 }

@@ -11,6 +11,7 @@ namespace rs {
 // Laplace-Gauss transform of 1/z, Eqs. (2.6)-(2.8); Galerkin cell averages, Eq. (2.5)).
 // dp_k[d] = d/dc of p_k at the centre offset c = d*h: a_k^{1/3} (exp(-t_k^2 (c+h/2)^2) -
 // exp(-t_k^2 (c-h/2)^2)) / h (the cell average differentiated in its centre; adjoint forces).
+// Any output pointer but pk64 may be null (that copy is then not written).
 __global__ void factors_kernel(double* pk64, float* pk32, float* pk32lo, double* dpk64, float* dpk32, int R,
                                int n, double h, double hq, double u0) {
   const int L = 2 * n - 1;
@@ -26,12 +27,13 @@ __global__ void factors_kernel(double* pk64, float* pk32, float* pk32lo, double*
   double ca = cbrt(a);
   double v = ca * (0.88622692545275801 / (t * h)) * diff;   // sqrt(pi)/2
   pk64[e] = v;
-  pk32[e] = (float)v;
+  if (pk32) pk32[e] = (float)v;
   if (pk32lo) pk32lo[e] = (float)(v - (double)(float)v);    // pk32 + pk32lo = p_k to 2^-48
+  if (!dpk64 && !dpk32) return;                              // the caller needs no derivatives
   const double up = t * (cs + 0.5 * h), dn = t * (cs - 0.5 * h);
   const double dv = ca * (exp(-up * up) - exp(-dn * dn)) / h;
-  dpk64[e] = dv;
-  dpk32[e] = (float)dv;
+  if (dpk64) dpk64[e] = dv;
+  if (dpk32) dpk32[e] = (float)dv;
 }
 
 // P_R(0), P_{R_l}(0), delta and the window half-width gamma (one CTA).

@@ -181,14 +181,14 @@ def test_edge_cases_empty_zero_and_single(prec):
     assert _rel(Pg, ref) < same_rank_tol(cfg, pr.Pl_grid(), ref, rnd)
     Eref = O.energy_from_potential(O.tucker_points(beta, Z0s, pr.j) + pr.windows_points(pr.j), pr.z, pr.PR0)
     assert abs(ctx.energy() - Eref) <= rnd * pr.PR0 * Z[0] ** 2
-    # host input path gives the same result (FP64 split-K sums use atomics, so the summation
-    # order may differ between runs: compare at the rounding level, far inside the oracle
-    # tolerance)
-    P1 = ctx.potential.clone().double()
+    # the host input path gives the same result bit for bit (every floating-point sum of a
+    # solve has a fixed order)
+    P1 = ctx.potential.clone()
+    E1 = ctx.energy()
     ctx.solve(xyz, Z)
     torch.cuda.synchronize()
-    d = float((P1 - ctx.potential.double()).norm() / P1.norm())
-    assert d < rnd, d
+    assert torch.equal(P1, ctx.potential)
+    assert ctx.energy() == E1
     ctx.close()
 
 
@@ -217,8 +217,15 @@ def test_invalid_inputs_raise():
 
 
 def test_c2_full_size_sampled_against_canonical_sum():
-    """Config 2 at full size (n = 513, N = 1000, FP32 bulk): the grid against the oracle's
-    full-rank canonical sum on sampled points (all particle sites plus random points)."""
+    """Config 2 at full size (n = 513, N = 1000, FP32 bulk, eps = 1e-6: the configuration the
+    throughput is quoted on), in the launch configuration the benchmark times: the grid against
+    the oracle's full-rank canonical sum P_0 (no split, no truncation) at every particle site and
+    4000 random grid points.  The relative error over the sample is bounded by the split
+      eps ||P_l|| / ||P_0||            (Tucker truncation of the long part, Sec. 6)
+    + delta sum|z| sqrt(M) / ||P_0||   (window cut-off, Sec. 2.3 criterion (A))
+    + 1e-6                             (FP32 bulk arithmetic)
+    with the norms taken over the sample, and it stays within the stated 1e-6 itself.  The energy
+    (Eq. (4.7)) is compared with the energy of P_0 at the stated tolerance of the energy scale."""
     cfg = load_config("c2_protein1000_n513")
     p = make_particles(cfg)
     pr = O.Problem(cfg, p.xyz, p.Z)
@@ -227,16 +234,23 @@ def test_c2_full_size_sampled_against_canonical_sum():
     assert rep["status"] == 0
     P = ctx.potential
     rng = np.random.default_rng(17)
-    idx = np.concatenate([pr.j, rng.integers(0, pr.n, (3000, 3))])
+    idx = np.concatenate([pr.j, rng.integers(0, pr.n, (4000, 3))])
     it = torch.tensor(idx, device="cuda", dtype=torch.long)
     g = P[it[:, 0], it[:, 1], it[:, 2]].double().cpu().numpy()
     ref = pr.P0_points(idx)
-    # Tucker eps on the long part + window cut-off + FP32 rounding
+    Pl = pr.Pl_points(idx)
+    nref = float(np.linalg.norm(ref))
+    tucker = cfg["eps"] * float(np.linalg.norm(Pl)) / nref
+    window = pr.delta * float(np.sum(np.abs(pr.z))) * np.sqrt(len(idx)) / nref
     err = _rel(g, ref)
-    assert err < 3e-6, err
+    print(f"c2 full size: sample error {err:.3e} (Tucker {tucker:.2e}, window {window:.2e}, rounding 1e-6)")
+    assert err <= tucker + window + 1e-6, err
+    assert err < 1e-6, err
     E = ctx.energy()
     scale = O.energy_scale(pr.xyz_snapped, pr.z)
-    assert abs(E - pr.energy_P0()) <= 3e-6 * scale
+    dE = abs(E - pr.energy_P0()) / scale
+    print(f"c2 full size: energy error {dE:.3e} of the energy scale")
+    assert dE <= 1e-6, dE
     ctx.close()
 
 
@@ -440,4 +454,61 @@ def test_forces_autograd_and_not_ready():
     ctx.solve(xyz.detach(), Z, forces=False)
     with pytest.raises(RSError):
         ctx.forces()
+    ctx.close()
+
+
+# ---------------------------------------------------------------- short-range part (rs_get_windows)
+def _windows_from_table(gamma, f, j, z, n):
+    """W[i] = sum_nu z_nu sum_k f_k[i1 - j1 + g] f_k[i2 - j2 + g] f_k[i3 - j3 + g] over the
+    centres whose window reaches i (Def. 3.6), assembled on the host from the returned table."""
+    W = np.zeros((n, n, n))
+    g = gamma
+    for q in range(len(z)):
+        if z[q] == 0.0:
+            continue
+        lo = [max(0, j[q, l] - g) for l in range(3)]
+        hi = [min(n - 1, j[q, l] + g) for l in range(3)]
+        sl = [f[:, lo[l] - j[q, l] + g: hi[l] - j[q, l] + g + 1] for l in range(3)]
+        W[lo[0]:hi[0] + 1, lo[1]:hi[1] + 1, lo[2]:hi[2] + 1] += z[q] * np.einsum("ka,kb,kc->abc", *sl)
+    return W
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
+def test_get_windows_rebuilds_oracle_short_range_part(c1, prec):
+    """rs_get_windows returns the uniform cumulated canonical tensor of the short-range part
+    (Defs. 3.4, 3.6): its factor table equals the oracle's short-range factors on -gamma..gamma,
+    the centres are the oracle's snapped indices, and the part rebuilt from the table on the host
+    equals the oracle's windows on the whole grid, element by element."""
+    cfg, p, pr = c1
+    cfg = dict(cfg, precision=prec)
+    ctx = _solve(cfg, p.xyz, p.Z, energy=False)
+    gamma, f, j, z = ctx.windows()
+    assert gamma == pr.gamma and f.shape == (cfg["R_s"], 2 * gamma + 1)
+    n = pr.n
+    fo = pr.pk[pr.kshort][:, n - 1 - gamma: n + gamma]
+    f = f.cpu().numpy()
+    assert np.abs(f - fo).max() <= 1e-14 * np.abs(fo).max()
+    j = j.cpu().numpy()
+    assert np.array_equal(j, pr.j)
+    assert np.array_equal(z.cpu().numpy(), p.Z)
+    W = _windows_from_table(gamma, f, j, p.Z, n)
+    Wo = pr.windows_grid()
+    assert np.abs(W - Wo).max() <= 1e-13 * np.abs(Wo).max()
+    ctx.close()
+
+
+def test_get_windows_needs_a_solve_and_follows_the_last_one():
+    from paper_1606_09218_gb300 import RSContext, RSError, config_from_workload
+    cfg = dict(b=4.0, n=33, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8,
+               precision="fp32_split", snap=True)
+    ctx = RSContext(config_from_workload(cfg, max_particles=3))
+    with pytest.raises(RSError):
+        ctx.windows()
+    xyz = np.array([[0.5, -1.0, 2.0], [-2.0, 1.5, 0.0]])
+    ctx.solve(xyz, np.array([0.7, -0.3]), energy=False)
+    g, f, j, z = ctx.windows()
+    assert j.shape == (2, 3) and z.shape == (2,) and f.shape[0] == 4
+    ctx.solve(xyz[:1], np.array([0.2]), energy=False)
+    g2, f2, j2, z2 = ctx.windows()
+    assert j2.shape == (1, 3) and float(z2[0]) == 0.2 and g2 == g
     ctx.close()
