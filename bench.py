@@ -207,6 +207,7 @@ class OraclePool:
         of wall time; returns (rate, points, wall seconds)."""
         if self.per_point is None:
             m = 64 * self.cores
+            self.run(m, 12344)                     # the workers start and build the problem
             self.per_point = max(self.run(m, 12345), 1e-4) / m
         M = int(max(64 * self.cores, min(20_000_000, seconds / self.per_point)))
         dt = self.run(M, seed)

@@ -30,6 +30,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// a request whose configuration has no slot waits at most this long before an idle slot of
+// another configuration is released for it
+constexpr double kStarveMs = 10.0;
+
 double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
 }
@@ -171,52 +175,100 @@ struct rs_server {
     finish(job, st, s);
   }
 
-  // one pass of admissions in arrival order (worker thread, without the mutex); returns true if
-  // anything was launched
+  // one pass of admissions (worker thread, without the mutex); returns true if anything was
+  // launched.  First every idle slot takes the earliest waiting request of its configuration;
+  // then the remaining requests, in arrival order, get new slots while the HBM budget and the
+  // slot limit allow.  To make room, only idle slots of configurations that no waiting request
+  // asks for are released (the one of the configuration with the most idle slots first): a
+  // slot that a later request of the queue can reuse is kept, so a full queue of mixed sizes
+  // does not create and free contexts (device allocations) over and over.
   bool admit() {
     bool any = false;
+    // fairness: the earliest waiting request whose configuration has no slot at all, once it
+    // has waited kStarveMs, takes the place of an idle slot of another configuration (the one
+    // with the most idle slots) even if later requests could reuse that slot
+    for (auto it = waiting.begin(); it != waiting.end(); ++it) {
+      bool has_slot = false;
+      for (auto& s : slots) has_slot = has_slot || same_config(s->cfg, (*it)->cfg);
+      if (has_slot) continue;
+      if (ms_between((*it)->t_sub, Clock::now()) < kStarveMs) break;
+      const size_t need = rs_workspace_bytes(&(*it)->cfg);
+      if (need == 0 || (used + need <= budget && (int)slots.size() < max_slots)) break;   // fits anyway
+      size_t victim = slots.size();
+      int best = 0;
+      for (size_t i = 0; i < slots.size(); ++i) {
+        if (slots[i]->job) continue;
+        int idle_same = 0;
+        for (auto& t : slots)
+          if (!t->job && same_config(t->cfg, slots[i]->cfg)) ++idle_same;
+        if (idle_same > best) { best = idle_same; victim = i; }
+      }
+      if (victim == slots.size()) break;
+      release_slot(victim);
+      if (used + need <= budget && (int)slots.size() < max_slots) {
+        if (Slot* ns = make_slot((*it)->cfg, need)) {
+          std::shared_ptr<Job> job = *it;
+          waiting.erase(it);
+          launch(ns, job);
+          any = true;
+        }
+      }
+      break;
+    }
+    for (auto& s : slots) {
+      if (s->job) continue;
+      for (auto it = waiting.begin(); it != waiting.end(); ++it) {
+        if (same_config(s->cfg, (*it)->cfg)) {
+          std::shared_ptr<Job> job = *it;
+          waiting.erase(it);
+          launch(s.get(), job);
+          any = true;
+          break;
+        }
+      }
+    }
+    auto wanted = [&](const rs_config& cfg) {
+      for (auto& j : waiting)
+        if (same_config(j->cfg, cfg)) return true;
+      return false;
+    };
     for (auto it = waiting.begin(); it != waiting.end();) {
       std::shared_ptr<Job> job = *it;
+      const size_t need = rs_workspace_bytes(&job->cfg);
+      if (need == 0) {                                   // invalid configuration
+        it = waiting.erase(it);
+        job->t_launch = Clock::now();
+        finish(job, RS_ERR_INVALID_ARG, nullptr);
+        continue;
+      }
+      // release idle slots that no waiting request can use while the new slot does not fit
+      while (used + need > budget || (int)slots.size() >= max_slots) {
+        size_t victim = slots.size();
+        int best = 0;
+        for (size_t i = 0; i < slots.size(); ++i) {
+          if (slots[i]->job || wanted(slots[i]->cfg)) continue;
+          int idle_same = 0;
+          for (auto& t : slots)
+            if (!t->job && same_config(t->cfg, slots[i]->cfg)) ++idle_same;
+          if (idle_same > best) { best = idle_same; victim = i; }
+        }
+        if (victim == slots.size()) break;
+        release_slot(victim);
+      }
       Slot* chosen = nullptr;
-      for (auto& s : slots)
-        if (!s->job && same_config(s->cfg, job->cfg)) { chosen = s.get(); break; }
-      if (!chosen) {
-        const size_t need = rs_workspace_bytes(&job->cfg);
-        if (need == 0) {                                   // invalid configuration
-          it = waiting.erase(it);
-          job->t_launch = Clock::now();
-          finish(job, RS_ERR_INVALID_ARG, nullptr);
-          continue;
-        }
-        // release idle slots of other configurations while the new one does not fit
-        // (the victim is an idle slot of the configuration with the most idle slots)
-        while ((used + need > budget || (int)slots.size() >= max_slots)) {
-          size_t victim = slots.size();
-          int best = 0;
-          for (size_t i = 0; i < slots.size(); ++i) {
-            if (slots[i]->job) continue;
-            int idle_same = 0;
-            for (auto& t : slots)
-              if (!t->job && same_config(t->cfg, slots[i]->cfg)) ++idle_same;
-            if (idle_same > best) { best = idle_same; victim = i; }
-          }
-          if (victim == slots.size()) break;
-          release_slot(victim);
-        }
-        if (used + need <= budget && (int)slots.size() < max_slots) {
+      if (used + need <= budget && (int)slots.size() < max_slots) {
+        chosen = make_slot(job->cfg, need);
+        if (!chosen) {                                   // device memory short: free idle slots, retry once
+          for (size_t i = slots.size(); i-- > 0;)
+            if (!slots[i]->job) release_slot(i);
           chosen = make_slot(job->cfg, need);
-          if (!chosen) {                                   // device memory short: free idle slots, retry once
-            for (size_t i = slots.size(); i-- > 0;)
-              if (!slots[i]->job) release_slot(i);
-            chosen = make_slot(job->cfg, need);
-          }
         }
-        if (!chosen && slots.empty()) {                    // cannot run even alone
-          it = waiting.erase(it);
-          job->t_launch = Clock::now();
-          finish(job, RS_ERR_OOM, nullptr);
-          continue;
-        }
+      }
+      if (!chosen && slots.empty()) {                    // cannot run even alone
+        it = waiting.erase(it);
+        job->t_launch = Clock::now();
+        finish(job, RS_ERR_OOM, nullptr);
+        continue;
       }
       if (!chosen) { ++it; continue; }
       it = waiting.erase(it);
