@@ -630,6 +630,126 @@ def reference_factor_derivatives(t, a, h: float, n: int):
 
 
 # ----------------------------------------------------------------------------
+# Discrete gradient of the RS tensor and the forces from it  (Sec. 4.3, Eq. (4.9))
+# ----------------------------------------------------------------------------
+def fd_first_derivative_weights(offsets, h: float):
+    """Weights w of the first-derivative difference formula on the given integer offsets,
+    sum_s w_s f(x + s h) ~ f'(x), from the Taylor conditions: sum_s w_s s^q = [q == 1] / h for
+    q = 0 .. len(offsets) - 1 (exact for polynomials of that degree).  Sec. 4.3 applies a
+    one-dimensional difference operator (backward or central) to the canonical vectors; the
+    order is a parameter here."""
+    s = np.asarray(offsets, dtype=np.float64)
+    m = len(s)
+    A = np.vander(s, m, increasing=True).T             # A[q][i] = s_i^q
+    rhs = np.zeros(m)
+    rhs[1] = 1.0
+    return np.linalg.solve(A, rhs) / h
+
+
+def fd_matrix(n: int, h: float, order: int = 8):
+    """The n x n matrix D_h of the first-derivative difference operator on the grid: row i uses
+    the order + 1 consecutive grid points centred on i where they fit, else the window of that
+    width nearest to i inside the grid (one-sided near the ends).  Reading: Sec. 4.3 names
+    backward or central differences; centred formulas of order ``order`` are used in the
+    interior, and the same width is kept at the ends of the grid."""
+    width = order + 1
+    D = np.zeros((n, n))
+    for i in range(n):
+        start = min(max(i - order // 2, 0), n - width)
+        cols = np.arange(start, start + width)
+        D[i, cols] = fd_first_derivative_weights(cols - i, h)
+    return D
+
+
+def canonical_fd_gradient_points(j, z, pk, kset, D, idx_pts):
+    """Discrete gradient (D_h applied along each mode, Sec. 4.3, Eq. (4.9)) of the full-rank
+    canonical sum sum_nu z_nu sum_{k in kset} p_k (x) p_k (x) p_k shifted to j^(nu), at the grid
+    multi-indices idx_pts (M, 3): returns (M, 3).  Each term's mode-l factor vector is replaced by
+    its difference D_h p_k(. - j_l^(nu)), written out per point and stencil entry."""
+    n = D.shape[0]
+    c = n - 1
+    idx_pts = np.asarray(idx_pts, dtype=np.int64)
+    z = np.asarray(z, dtype=np.float64)
+    sub = pk[kset]
+    out = np.zeros((len(idx_pts), 3))
+    for m, p in enumerate(idx_pts):
+        f = [sub[:, p[l] - j[:, l] + c] for l in range(3)]            # (|k|, N) factor values
+        for l in range(3):
+            cols = np.nonzero(D[p[l]])[0]
+            df = np.zeros_like(f[l])
+            for q in cols:
+                df += D[p[l], q] * sub[:, q - j[:, l] + c]
+            out[m, l] = float(((df * f[(l + 1) % 3] * f[(l + 2) % 3]).sum(0)) @ z)
+    return out
+
+
+def fd_self_gradient(j, pk, kset, D):
+    """D_h of the particle's own term sum_k p_k (x) p_k (x) p_k at its own grid point, per mode
+    (N, 3): zero for a centred formula (the term is even), the small value of a one-sided
+    formula near the ends of the grid.  The forces leave the particle's own term out."""
+    n = D.shape[0]
+    c = n - 1
+    sub = pk[kset]
+    p0 = sub[:, c]
+    out = np.zeros((len(j), 3))
+    for m in range(len(j)):
+        for l in range(3):
+            i = j[m, l]
+            cols = np.nonzero(D[i])[0]
+            df = sum(D[i, q] * sub[:, q - i + c] for q in cols)
+            out[m, l] = float((df * p0 * p0).sum())
+    return out
+
+
+def _window_forces(j, z, pk, dpk, kshort, gamma: int, n: int):
+    """Short-range part of the forces: the windows of the other particles (Def. 3.4)
+    differentiated term by term with the derivative factors, -z_m sum_{nu != m} z_nu grad U_nu."""
+    c = n - 1
+    z = np.asarray(z, dtype=np.float64)
+    F = np.zeros((len(z), 3))
+    for m in range(len(z)):
+        dj = j[m][None, :] - j
+        near = np.all(np.abs(dj) <= gamma, axis=1)
+        near[m] = False
+        if not near.any():
+            continue
+        d = dj[near] + c
+        f = [pk[kshort][:, d[:, l]] for l in range(3)]
+        g = [dpk[kshort][:, d[:, l]] for l in range(3)]
+        for l in range(3):
+            F[m, l] -= z[m] * float((g[l] * f[(l + 1) % 3] * f[(l + 2) % 3]).sum(0) @ z[near])
+    return F
+
+
+def canonical_fd_forces(j, z, pk, dpk, klong, kshort, gamma: int, D):
+    """Forces from the discrete gradient of the untruncated long-range canonical sum (Sec. 4.3):
+    F_m = -z_m [D_h P_l(x_m) - z_m D_h K_l(0)] - z_m sum_{nu != m, window} z_nu grad U_nu(x_m),
+    the particle's own long-range term taken out, the windows differentiated term by term."""
+    n = D.shape[0]
+    z = np.asarray(z, dtype=np.float64)
+    G = canonical_fd_gradient_points(j, z, pk, klong, D, j)
+    G -= z[:, None] * fd_self_gradient(j, pk, klong, D)
+    return -z[:, None] * G + _window_forces(j, z, pk, dpk, kshort, gamma, n)
+
+
+def rs_tucker_fd_forces(j, z, pk, dpk, klong, kshort, gamma: int, Z0s, beta, D):
+    """Forces from the discrete gradient of the RS-Tucker tensor (Sec. 4.3, Eq. (4.9) applied to
+    the Tucker form of Def. 3.9): the mode-l derivative of P_l^T = beta x_1 V1 x_2 V2 x_3 V3 is
+    beta with V_l replaced by D_h V_l, evaluated at the particle's grid point,
+    F_m = -z_m [(D_h P_l^T)(x_m) - z_m D_h K_l(0)] + window terms as in canonical_fd_forces."""
+    n = D.shape[0]
+    z = np.asarray(z, dtype=np.float64)
+    dV = [D @ V for V in Z0s]
+    V = [Z0s[l][j[:, l]] for l in range(3)]
+    Vd = [dV[l][j[:, l]] for l in range(3)]
+    G = np.stack([np.einsum("abc,ma,mb,mc->m", beta, Vd[0], V[1], V[2], optimize=True),
+                  np.einsum("abc,ma,mb,mc->m", beta, V[0], Vd[1], V[2], optimize=True),
+                  np.einsum("abc,ma,mb,mc->m", beta, V[0], V[1], Vd[2], optimize=True)], axis=1)
+    G -= z[:, None] * fd_self_gradient(j, pk, klong, D)
+    return -z[:, None] * G + _window_forces(j, z, pk, dpk, kshort, gamma, n)
+
+
+# ----------------------------------------------------------------------------
 # Whole-problem driver used by the tests
 # ----------------------------------------------------------------------------
 class Problem:
@@ -706,6 +826,23 @@ class Problem:
         dpk = reference_factor_derivatives(self.t, self.a, self.h, self.n)
         return rs_tucker_forces(self.j, self.z, self.pk, dpk, self.klong, self.kshort, self.gamma, Us,
                                 Z0s, beta, self.n), rk
+
+    def fd_matrix(self, order: int = 8):
+        return fd_matrix(self.n, self.h, order)
+
+    def forces_canonical_fd(self, order: int = 8):
+        """Forces from the discrete gradient of the untruncated long-range sum (Sec. 4.3)."""
+        dpk = reference_factor_derivatives(self.t, self.a, self.h, self.n)
+        return canonical_fd_forces(self.j, self.z, self.pk, dpk, self.klong, self.kshort, self.gamma,
+                                   self.fd_matrix(order))
+
+    def forces_rs_tucker_fd(self, ranks=None, eps=None, order: int = 8, cap: int = 0):
+        """Forces from the discrete gradient of the RS-Tucker tensor (Sec. 4.3, Def. 3.9), at the
+        given ranks or at the eps ranks (capped by ``cap``, 0 = none)."""
+        Z0s, beta, rk, _, _, _ = self.tucker(eps=eps, cap=cap, ranks=ranks)
+        dpk = reference_factor_derivatives(self.t, self.a, self.h, self.n)
+        return rs_tucker_fd_forces(self.j, self.z, self.pk, dpk, self.klong, self.kshort, self.gamma, Z0s, beta,
+                                   self.fd_matrix(order)), rk
 
     def forces_direct_long(self):
         """Untruncated long-range forces plus windows at the snapped centres."""

@@ -109,6 +109,20 @@ def forces_wrong_sign(xyz, z):
     return -ORIG["forces_direct"](xyz, z)
 
 
+def fd_matrix_transposed(n, h, order=8):
+    """The difference operator applied as D_h^T (rows and columns exchanged)."""
+    return ORIG["fd_matrix"](n, h, order).T.copy()
+
+
+def tucker_fd_wrong_mode(j, z, pk, dpk, klong, kshort, gamma, Z0s, beta, D):
+    """The mode-1 derivative taken along mode 2 (the difference of the wrong basis)."""
+    F = ORIG["rs_tucker_fd_forces"](j, z, pk, dpk, klong, kshort, gamma, Z0s, beta, D)
+    G = ORIG["rs_tucker_fd_forces"](j, z, pk, dpk, klong, kshort, gamma, [Z0s[1], Z0s[0], Z0s[2]],
+                                    beta.transpose(1, 0, 2), D)
+    F[:, 0] = G[:, 1]
+    return F
+
+
 def snap_half_to_even(xyz, b, h, n):
     """Ties rounded half to even instead of away from zero."""
     j = np.rint((np.asarray(xyz, float) + b) / h).astype(np.int64)
@@ -132,6 +146,9 @@ CASES = [
     ("energy_from_potential", energy_without_half, P.test_energy_tensor_formula_matches_direct),
     ("forces_direct", forces_wrong_sign, P.test_forces_direct_finite_difference),
     ("snap_to_grid", snap_half_to_even, P.test_snap_rounding_and_bounds),
+    ("fd_matrix", fd_matrix_transposed, lambda: P.test_fd_forces_converge_to_the_analytic_long_range_forces(_c1())),
+    ("rs_tucker_fd_forces", tucker_fd_wrong_mode,
+     lambda: P.test_tucker_fd_forces_exact_at_full_rank_and_within_eps(_c1())),
 ]
 
 

@@ -682,3 +682,84 @@ def test_als_eps_ranks_within_eps(c1_problem, eps):
     assert all(a <= b for a, b in zip(rk, rk0)) and sum(rk) < sum(rk0)
     for V in Vs:
         assert np.allclose(V.T @ V, np.eye(V.shape[1]), atol=1e-12)
+
+
+# ---------------------------------------------------------------- discrete gradient (Sec. 4.3)
+def test_fd_weights_closed_forms_and_polynomial_exactness():
+    """The Taylor-condition weights reproduce the textbook centred formulas of orders 2 and 4, and
+    every row of D_h (centred in the interior, one-sided at the ends) differentiates polynomials
+    of degree <= order exactly."""
+    h = 0.3
+    w2 = O.fd_first_derivative_weights([-1, 0, 1], h)
+    assert np.allclose(w2 * h, [-0.5, 0.0, 0.5], rtol=0, atol=1e-14)
+    w4 = O.fd_first_derivative_weights([-2, -1, 0, 1, 2], h)
+    assert np.allclose(w4 * h, [1 / 12, -2 / 3, 0.0, 2 / 3, -1 / 12], rtol=0, atol=1e-13)
+    n, order = 23, 8
+    D = O.fd_matrix(n, h, order)
+    x = h * np.arange(n)
+    xm, sc = x[n // 2], x[-1] / 2
+    for q in range(order + 1):
+        f = ((x - xm) / sc) ** q
+        df = q * ((x - xm) / sc) ** max(q - 1, 0) / sc if q > 0 else np.zeros(n)
+        assert np.abs(D @ f - df).max() <= 1e-8 * max(1.0, np.abs(df).max()), q
+    # centred rows are antisymmetric about their point; each row sums to zero
+    i = n // 2
+    assert np.allclose(D[i, i - 4:i + 5], -D[i, i - 4:i + 5][::-1], rtol=0, atol=1e-12 / h)
+    assert np.abs(D.sum(1)).max() <= 1e-11 / h
+
+
+def test_fd_forces_converge_to_the_analytic_long_range_forces(c1_problem):
+    """Forces from the discrete gradient of the untruncated long-range sum approach the forces
+    from the analytic derivative of the Galerkin factors (rs_direct_long_forces) as the order
+    of the difference formula rises."""
+    pr = c1_problem[0]
+    Fa = pr.forces_direct_long()
+    errs = [np.linalg.norm(pr.forces_canonical_fd(order) - Fa) / np.linalg.norm(Fa) for order in (2, 4, 6, 8)]
+    assert all(b < a / 8 for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-6, errs
+
+
+def test_fd_forces_converge_with_the_mesh_size():
+    """Second-order centred differences: halving h divides the error of the discrete gradient of
+    the long-range kernel by about four (same centres, same quadrature, grids n = 33, 65, 129)."""
+    xyz = np.array([[0.5, -1.0, 1.5], [-1.5, 0.5, -0.5], [1.0, 1.0, -1.0]])
+    z = np.array([0.8, -0.6, 0.4])
+    errs = []
+    for n in (33, 65, 129):
+        pr = O.Problem(dict(b=4.0, n=n, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0,
+                            delta_rel=1e-8), xyz, z)
+        Fa = pr.forces_direct_long()
+        errs.append(np.linalg.norm(pr.forces_canonical_fd(2) - Fa) / np.linalg.norm(Fa))
+    for a, b in zip(errs, errs[1:]):
+        assert 3.0 < a / b < 5.0, errs
+
+
+def test_tucker_fd_forces_exact_at_full_rank_and_within_eps(c1_problem):
+    """The discrete gradient applied to the Tucker form equals the discrete gradient of the
+    canonical sum at full rank, and approaches it as eps falls (within 10 eps here: the
+    difference operator weighs the discarded, more oscillatory directions by up to ~1/h)."""
+    pr = c1_problem[0]
+    Fc = pr.forces_canonical_fd(8)
+    Ff, _ = pr.forces_rs_tucker_fd(ranks=[60, 60, 60])
+    assert np.linalg.norm(Ff - Fc) <= 1e-12 * np.linalg.norm(Fc)
+    for eps in (1e-4, 1e-6):
+        Ft, _ = pr.forces_rs_tucker_fd(eps=eps)
+        assert np.linalg.norm(Ft - Fc) <= 10 * eps * np.linalg.norm(Fc), eps
+
+
+def test_fd_forces_momentum_and_self_term():
+    """Centred differences of an even kernel are odd, so the forces of particles away from the
+    ends of the grid add up to zero and a particle's own term has zero centred derivative; a
+    one-sided row gives its own term a small, nonzero derivative."""
+    rng = np.random.default_rng(41)
+    xyz, z = random_particles(rng, 7, 2.5, 0.8)
+    pr = O.Problem(small_cfg(), xyz, z)
+    F = pr.forces_canonical_fd(8)
+    assert np.abs(F.sum(0)).max() <= 1e-12 * np.abs(F).max()
+    D = pr.fd_matrix(8)
+    s = O.fd_self_gradient(pr.j, pr.pk, pr.klong, D)
+    assert np.abs(s).max() <= 1e-14 * pr.PRl0 / pr.h
+    jb = np.array([[0, pr.n // 2, pr.n // 2]])
+    sb = O.fd_self_gradient(jb, pr.pk, pr.klong, D)
+    tiny = 1e-14 * pr.PRl0 / pr.h
+    assert abs(sb[0, 1]) <= tiny and abs(sb[0, 2]) <= tiny and abs(sb[0, 0]) > 100 * tiny, sb
