@@ -315,7 +315,7 @@ def serving_report(max_slots: int = 8, hbm_budget: int = 16 << 30, saturate: boo
             "latency": "submit (host inputs) to result (energy on host, potential in a device buffer)"}
 
 
-def timed_solves(ctx, xyz, Z, pot, steps, flush, stream, forces=False):
+def timed_solves(ctx, xyz, Z, pot, steps, flush, stream, forces=False, forces_pair=False):
     """Device milliseconds of ``steps`` solves (CUDA events on the context stream, L2 flushed
     before each) and the per-stage milliseconds per solve."""
     import torch
@@ -327,7 +327,8 @@ def timed_solves(ctx, xyz, Z, pot, steps, flush, stream, forces=False):
     for s in range(steps):
         flush.zero_()
         starts[s].record(stream)
-        ctx.solve(xyz, Z, potential=pot, energy=True, want_potential=pot is not None, forces=forces)
+        ctx.solve(xyz, Z, potential=pot, energy=True, want_potential=pot is not None, forces=forces,
+                  forces_pair=forces_pair)
         ends[s].record(stream)
     torch.cuda.synchronize()
     t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
@@ -542,6 +543,7 @@ def run_ours(args, rank, world, local_rank):
         fs = 5
         tf, fst = timed_solves(fctx, fx, fz, fpot, fs, flush, stream, forces=True)
         frep = fctx.report()
+        tpf, pst = timed_solves(fctx, fx, fz, fpot, 2, flush, stream, forces=True, forces_pair=True)
         fctx.pair_energy_forces(fx, fz)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -555,7 +557,12 @@ def run_ours(args, rank, world, local_rank):
                   "solve_with_forces": {"ms_per_step": tf / fs, "value": fn_ ** 3 * fs / (tf * 1e-3),
                                         "unit": UNIT, "ranks": frep["ranks"], "stages_ms_per_step": fst,
                                         "path": "rs_solve with RS_POTENTIAL | RS_ENERGY | RS_FORCES at "
-                                                "snapped centres"},
+                                                "snapped centres (discrete gradient of the RS-Tucker "
+                                                "tensor, Sec. 4.3)"},
+                  "solve_with_pair_forces": {"ms_per_step": tpf / 2, "value": fn_ ** 3 * 2 / (tpf * 1e-3),
+                                             "unit": UNIT,
+                                             "path": "the same with RS_FORCES_PAIR (untruncated long-range "
+                                                     "pair kernel, O(N^2 R_l), on the second stream)"},
                   "offgrid_pair": {"ms": fms, "pairs_per_s": fN * (fN - 1) / (fms * 1e-3), "energy": fE,
                                    "path": "rs_pair_energy_forces: RS kernel in pair form at unsnapped "
                                            "centres, FP32 factors, FP64 sums (energy and forces, one call)"}}

@@ -86,6 +86,8 @@ typedef struct {
 #define RS_ENERGY              4   /* compute the interaction energy (read with rs_energy) */
 #define RS_FORCES              8   /* compute the forces (read with rs_forces) */
 #define RS_VALIDATE_SEPARATION 16  /* check that no two centres are closer than min_sep */
+#define RS_FORCES_PAIR         32  /* with RS_FORCES: the long part of the forces from the
+                                      untruncated pair kernel instead of the discrete gradient */
 
 typedef struct rs_ctx rs_ctx;
 
@@ -137,10 +139,20 @@ rs_status rs_solve(rs_ctx* ctx, int N, const double* xyz, const double* Z, int f
  * Synchronises the stream.  RS_ERR_NOT_READY if the last solve did not ask for RS_ENERGY. */
 rs_status rs_energy(rs_ctx* ctx, double* E);
 
-/* Forces of the last solve (Sec. 4.3): F_j = -z_j [grad P_l(x_j) + sum of the gradients of the
- * windows (Defs. 3.4, 3.6) of the other particles at x_j], the long part from the untruncated
- * long-range pair kernel (exact for P_l, within O(eps) of the gradient of the RS-Tucker tensor),
- * Galerkin factors and their centre derivatives, the charged centres at their grid points.
+/* Forces of the last solve (Sec. 4.3), F_j = -z_j grad_{x_j} of the potential of the other
+ * particles at x_j, with the charged centres at their grid points:
+ *   default: the discrete gradient of the RS-Tucker tensor (Eq. (4.9)): the long-range Tucker
+ *     part differentiated by a one-dimensional difference operator D_h applied to its bases (the
+ *     centred formula of order 8 in the interior, the same nine points shifted into the grid near
+ *     its ends), the particle's own long-range term taken out, plus the windows of the other
+ *     particles (Defs. 3.4, 3.6) differentiated term by term with the derivatives of the
+ *     Galerkin factors.  This is the gradient of the tensor whose energy rs_energy returns;
+ *     O(N r^2) work.  It differs from the gradient of the untruncated long-range sum by
+ *     O(eps / h) (the difference operator weighs the discarded directions) and by the
+ *     difference formula's error (below 1e-7 of the forces on the bundled workloads).
+ *   with RS_FORCES_PAIR: the long part from the untruncated long-range pair kernel, grad P_l(x_j) =
+ *     sum_{nu != j} z_nu sum_{k long} grad (p_k x p_k x p_k)(x_j - x_nu) (exact for P_l, O(N^2 R_l)
+ *     work), the windows as above.
  * F: N x 3 row-major float64, a device pointer, or a host pointer with to_host != 0; particles
  * with zero charge get zero force.  Synchronises the stream.  RS_ERR_NOT_READY if the last solve
  * did not ask for RS_FORCES; device-side input errors as for rs_energy. */

@@ -10,8 +10,8 @@ from __future__ import annotations
 import ctypes as C
 
 from . import _lib
-from ._lib import (RS_ENERGY, RS_FORCES, RS_FP32, RS_FP32_SPLIT, RS_FP64, RS_INPUT_HOST,  # noqa: F401
-                   RS_POTENTIAL, RS_VALIDATE_SEPARATION, RSError)
+from ._lib import (RS_ENERGY, RS_FORCES, RS_FORCES_PAIR, RS_FP32, RS_FP32_SPLIT, RS_FP64,  # noqa: F401
+                   RS_INPUT_HOST, RS_POTENTIAL, RS_VALIDATE_SEPARATION, RSError)
 
 PRECISIONS = {"fp64": RS_FP64, "fp32_split": RS_FP32_SPLIT, "fp32": RS_FP32}
 
@@ -89,9 +89,11 @@ class RSContext:
         return self._torch.empty((n, n, n), dtype=self.dtype, device="cuda")
 
     def solve(self, xyz, Z, potential=None, energy: bool = True, want_potential: bool = True,
-              min_sep: float = 0.0, forces: bool = False) -> int:
+              min_sep: float = 0.0, forces: bool = False, forces_pair: bool = False) -> int:
         """Enqueue one solve.  ``xyz`` (N,3) and ``Z`` (N,) float64: CUDA tensors, or host
-        (CPU tensors / numpy) which the library copies in.  Returns the launch status."""
+        (CPU tensors / numpy) which the library copies in.  ``forces``: the discrete gradient of
+        the RS-Tucker tensor; with ``forces_pair`` the long part from the untruncated pair
+        kernel instead.  Returns the launch status."""
         torch = self._torch
         flags = 0
         if isinstance(xyz, torch.Tensor) and xyz.is_cuda:
@@ -120,6 +122,8 @@ class RSContext:
             flags |= RS_ENERGY
         if forces:
             flags |= RS_FORCES
+            if forces_pair:
+                flags |= RS_FORCES_PAIR
         self.last_N = N
         if min_sep > 0:
             flags |= RS_VALIDATE_SEPARATION
@@ -136,8 +140,8 @@ class RSContext:
 
     def forces(self):
         """Forces of the last solve (it must have asked for ``forces=True``) as an (N, 3)
-        float64 CUDA tensor: the long part from the untruncated pair kernel, the windows term by
-        term (Sec. 4.3)."""
+        float64 CUDA tensor (Sec. 4.3): the discrete gradient of the RS-Tucker tensor (or the
+        untruncated pair kernel with ``forces_pair``), the windows term by term."""
         torch = self._torch
         F = torch.empty((self.last_N, 3), dtype=torch.float64, device="cuda")
         _lib.check(self.lib.rs_forces(self.h, C.c_void_p(F.data_ptr()), 0), self.h)
@@ -358,8 +362,8 @@ def _energy_function():
     import torch
 
     class RSEnergy(torch.autograd.Function):
-        """E(xyz) of the RS tensor with the forces as the gradient: dE/dxyz = -F (within O(eps)
-        of the gradient of the RS-Tucker energy)."""
+        """E(xyz) of the RS-Tucker tensor with the forces as the gradient: dE/dxyz = -F, the
+        discrete gradient (Sec. 4.3, Eq. (4.9)) of the same tensor whose energy forward returns."""
 
         @staticmethod
         def forward(fctx, xyz, Z, rs):

@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "RS_OK", 1: "RS_RANK_CAPPED", -1: "RS_ERR_INVALID_ARG", -2: "
 # precisions
 RS_FP64, RS_FP32_SPLIT, RS_FP32 = 0, 1, 2
 # solve flags
-RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_FORCES, RS_VALIDATE_SEPARATION = 1, 2, 4, 8, 16
+RS_INPUT_HOST, RS_POTENTIAL, RS_ENERGY, RS_FORCES, RS_VALIDATE_SEPARATION, RS_FORCES_PAIR = 1, 2, 4, 8, 16, 32
 
 #: every symbol ``include/rs.h`` declares
 EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_energy", "rs_forces", "rs_report",

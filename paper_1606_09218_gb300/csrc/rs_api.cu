@@ -129,6 +129,11 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.adims, 4 * rm);
   add(v, c.kdims, 4 * rm);
   add(v, c.Fout, 8 * 3 * N);
+  add(v, c.fd_w, 8 * n * FD_WIDTH);
+  add(v, c.fd_s, 4 * n);
+  add(v, c.dZ64, 8 * 3 * n * rm);
+  add(v, c.dZ32, 4 * 3 * n * rm);
+  add(v, c.T1d, ts * rm * rm * n);
   add(v, c.sc, sizeof(DevScalars));
   if (c.use_tc) {
     const size_t nT = (size_t)c.tc_ntiles;
@@ -362,6 +367,20 @@ rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
       return RS_ERR_CUDA;
     }
   }
+  // rows of the first-derivative difference operator (forces)
+  {
+    std::vector<double> w((size_t)c.n * FD_WIDTH);
+    std::vector<int> st(c.n);
+    if (!fd_table(c.n, c.h, w.data(), st.data()) ||
+        cudaMemcpy(c.fd_w, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c.fd_s, st.data(), sizeof(int) * st.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      g_create_err = "upload of the difference operator failed";
+      free_all(c);
+      delete h;
+      return RS_ERR_CUDA;
+    }
+  }
   *out = h;
   return RS_OK;
 }
@@ -421,7 +440,7 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   cudaEventRecord(c.ev_bins, c.aux);
   if ((flags & RS_ENERGY) && c.use_tc && !c.fp64)
     k += launch_energy_windows(c);         // a8, the neighbours' windows at every particle
-  if (flags & RS_FORCES) k += launch_forces(c);                          // a9 (particles and bins only)
+  if ((flags & RS_FORCES) && (flags & RS_FORCES_PAIR)) k += launch_forces(c);   // a9, pair kernel
   c.stream = s;
   k += launch_gram(c);                     // a3, a4: Gram matrices of the long-range side matrices
   mark(3);
@@ -442,6 +461,7 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
   mark(8);
   cudaStreamWaitEvent(s, c.ev_side, 0);    // energy windows and forces (second stream) done
   if (flags & RS_ENERGY) k += launch_energy(c, N);                      // a8
+  if ((flags & RS_FORCES) && !(flags & RS_FORCES_PAIR)) k += launch_forces_rs(c);   // a9
   mark(9);
   st = check_launch(c, "solve");
   if (st != RS_OK) return st;

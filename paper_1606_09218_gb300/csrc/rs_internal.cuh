@@ -153,6 +153,12 @@ struct Ctx {
   int*    adims = nullptr;      // rmax: per-batch row counts of the mode-2 product
   int*    kdims = nullptr;      // rmax: per-batch inner sizes of the mode-2 product
   double* Fout = nullptr;       // maxN x 3 forces of the last solve
+  // discrete gradient of the Tucker part (forces, rs_forces.cu)
+  double* fd_w = nullptr;       // n x FD_WIDTH weights of the first-derivative rows (1/h included)
+  int*    fd_s = nullptr;       // n: first grid index of each row's stencil
+  double* dZ64 = nullptr;       // 3 x n x rmax: D_h applied to the Tucker bases
+  float*  dZ32 = nullptr;
+  void*   T1d = nullptr;        // rmax x rmax x n (T): beta x_3 (D_h V3)
   // tensor-core assembly of the FP32 output (rs_tc.cu), planned at create
   bool use_tc = false;
   int t2_ld = 0;                // i3 stride of T2 on the CUDA-core path
@@ -226,6 +232,46 @@ __device__ __forceinline__ void window_add(const DevView& c, int i1, int i2, int
   }
 }
 
+// Gradient of the short-range windows at grid point (i1, i2, i3) (Defs. 3.4, 3.6 differentiated
+// term by term): adds this lane's share of sum_{nu in L(i), nu != p} z_nu grad U_nu(i) to
+// (g1, g2, g3), with the FP64 factor table and its derivatives in the centre offset (dpk64); the
+// lanes of a warp take the particle bins around the point in turn.  The particle's own window
+// (index p) is left out; its derivative at its own centre is zero in any case (p_k' is odd).
+__device__ __forceinline__ void window_grad_add(const DevView& c, const double* __restrict__ dpk64, int i1,
+                                                int i2, int i3, int p, int lane, double& g1, double& g2,
+                                                double& g3) {
+  const int n = c.n, L = 2 * n - 1;
+  const int g = c.sc->gamma, nb = c.nbin;
+  const int b1a = max(0, i1 - g) / BIN, b1b = min(n - 1, i1 + g) / BIN;
+  const int b2a = max(0, i2 - g) / BIN, b2b = min(n - 1, i2 + g) / BIN;
+  const int b3a = max(0, i3 - g) / BIN, b3b = min(n - 1, i3 + g) / BIN;
+  const int nb3 = b3b - b3a + 1, nb2 = b2b - b2a + 1;
+  const int nbt = (b1b - b1a + 1) * nb2 * nb3;
+  for (int t = lane; t < nbt; t += 32) {
+    const int b3 = b3a + t % nb3, b2 = b2a + (t / nb3) % nb2, b1 = b1a + t / (nb3 * nb2);
+    const int b = (b1 * nb + b2) * nb + b3;
+    for (int it = c.bin_start[b]; it < c.bin_start[b + 1]; ++it) {
+      const int q = c.bin_items[it];
+      if (q == p) continue;
+      const int d1 = i1 - c.j[3 * q], d2 = i2 - c.j[3 * q + 1], d3 = i3 - c.j[3 * q + 2];
+      if (abs(d1) > g || abs(d2) > g || abs(d3) > g) continue;
+      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      for (int k = c.R_l; k < c.R; ++k) {
+        const double* row = c.pk64 + (long long)k * L + n - 1;
+        const double* drow = dpk64 + (long long)k * L + n - 1;
+        const double f1 = row[d1], f2 = row[d2], f3 = row[d3];
+        s1 += drow[d1] * f2 * f3;
+        s2 += f1 * drow[d2] * f3;
+        s3 += f1 * f2 * drow[d3];
+      }
+      const double zq = c.Z[q];
+      g1 += zq * s1;
+      g2 += zq * s2;
+      g3 += zq * s3;
+    }
+  }
+}
+
 inline DevView make_view(const Ctx& c) {
   DevView v;
   v.n = c.n; v.rmax = c.rmax; v.R = c.R; v.R_l = c.R_l; v.nbin = c.nbin;
@@ -254,7 +300,12 @@ int launch_window_lists(Ctx& c);         // per-tile-column window lists
 int launch_assemble(Ctx& c, float* out); // Tucker product + windows in one kernel
 int launch_windows(Ctx& c, void* out);
 int launch_energy(Ctx& c, int N);
-int launch_forces(Ctx& c);
+int launch_forces(Ctx& c);              // long part from the untruncated pair kernel
+// forces from the discrete gradient of the RS-Tucker tensor (rs_forces.cu)
+constexpr int FD_ORDER = 8;             // order of the centred difference formula
+constexpr int FD_WIDTH = FD_ORDER + 1;  // points per row
+bool fd_table(int n, double h, double* w, int* start);   // host: the rows of D_h
+int launch_forces_rs(Ctx& c);
 
 // Kernels launched with more than 48 KB of dynamic shared memory.  The limit is an attribute of
 // the kernel (process-wide per device), so it is raised once per device to the opt-in maximum

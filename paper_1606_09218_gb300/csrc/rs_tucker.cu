@@ -708,34 +708,7 @@ __global__ void forces_direct_kernel(DevView c, const T* __restrict__ pk, const 
     g2 += zq * (double)s2;
     g3 += zq * (double)s3;
   }
-  const int g = c.sc->gamma, nb = c.nbin;
-  const int b1a = max(0, i1 - g) / BIN, b1b = min(n - 1, i1 + g) / BIN;
-  const int b2a = max(0, i2 - g) / BIN, b2b = min(n - 1, i2 + g) / BIN;
-  const int b3a = max(0, i3 - g) / BIN, b3b = min(n - 1, i3 + g) / BIN;
-  const int nb3 = b3b - b3a + 1, nb2 = b2b - b2a + 1;
-  const int nbt = (b1b - b1a + 1) * nb2 * nb3;
-  for (int t = lane; t < nbt; t += 32) {
-    const int b3 = b3a + t % nb3, b2 = b2a + (t / nb3) % nb2, b1 = b1a + t / (nb3 * nb2);
-    const int b = (b1 * nb + b2) * nb + b3;
-    for (int it = c.bin_start[b]; it < c.bin_start[b + 1]; ++it) {
-      const int q = c.bin_items[it];
-      const int d1 = i1 - c.j[3 * q], d2 = i2 - c.j[3 * q + 1], d3 = i3 - c.j[3 * q + 2];
-      if (abs(d1) > g || abs(d2) > g || abs(d3) > g) continue;
-      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      for (int k = c.R_l; k < c.R; ++k) {
-        const double* row = c.pk64 + (long long)k * L + n - 1;
-        const double* drow = dpk64 + (long long)k * L + n - 1;
-        const double f1 = row[d1], f2 = row[d2], f3 = row[d3];
-        s1 += drow[d1] * f2 * f3;
-        s2 += f1 * drow[d2] * f3;
-        s3 += f1 * f2 * drow[d3];
-      }
-      const double zq = c.Z[q];
-      g1 += zq * s1;
-      g2 += zq * s2;
-      g3 += zq * s3;
-    }
-  }
+  window_grad_add(c, dpk64, i1, i2, i3, p, lane, g1, g2, g3);
   for (int o = 16; o > 0; o >>= 1) {
     g1 += __shfl_down_sync(0xffffffffu, g1, o);
     g2 += __shfl_down_sync(0xffffffffu, g2, o);

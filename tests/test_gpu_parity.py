@@ -377,21 +377,57 @@ def test_plain_method_paths_match_oracle(prec):
     ctx.close()
 
 
-# ---------------------------------------------------------------- adjoint forces (Sec. 4.3)
+# ---------------------------------------------------------------- forces (Sec. 4.3)
 def _forces_tol(cfg, rounding):
     """Both the GPU and the oracle RS-Tucker forces are within O(eps) of the untruncated forces
-    (oracle pin: relative error <= 1e-5 at eps = 1e-6); 20*eps covers both, plus the rounding of
-    the bulk precision."""
+    (oracle pins: about 6 eps for the discrete gradient, 1e-5 at eps = 1e-6 for the adjoint of
+    the continued basis); 20*eps covers both, plus the rounding of the bulk precision."""
     return 20 * cfg["eps"] + rounding
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
-def test_forces_match_oracle(prec):
-    """Forces through the C ABI: the untruncated long-range pair kernel plus the windows, against
-    the oracle's direct form element by element (FP64 products: 1e-10; FP32 products: 2e-6),
-    and against the oracle's RS-Tucker forces at the same ranks and the forces of the
-    untruncated Galerkin kernel (both within O(eps)); zero-charge particles get zero force and
-    the total force is (nearly) zero."""
+def test_forces_discrete_gradient_match_oracle(prec):
+    """Forces through the C ABI from the discrete gradient of the RS-Tucker tensor (Sec. 4.3,
+    Eq. (4.9)): against the oracle's discrete gradient of its own RS-Tucker tensor at the same
+    ranks and of the untruncated long-range sum (both within O(eps) of each other, element by
+    element in the norm of the forces), against the analytic derivative of the untruncated kernel
+    within the same bound (the order-8 difference formula adds far less); zero-charge particles
+    get zero force, the total force is nearly zero, and a particle on the boundary of the box
+    (one-sided rows) is covered."""
+    rng = np.random.default_rng(12)
+    cfg = dict(b=4.0, n=45, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8,
+               precision=prec, snap=True)
+    N = 16
+    xyz = rng.uniform(-3.2, 3.2, (N, 3))
+    xyz[5] = [-4.0, 0.3, 3.9]
+    Z = rng.uniform(-1, 1, N)
+    Z[3] = 0.0
+    pr = O.Problem(cfg, xyz, Z)
+    ctx = _ctx(cfg, N)
+    ctx.solve(torch.tensor(xyz, device="cuda"), torch.tensor(Z, device="cuda"), forces=True)
+    F = ctx.forces().cpu().numpy()
+    rep = ctx.report()
+    assert rep["status"] == 0
+    Ft, _ = pr.forces_rs_tucker_fd(ranks=rep["ranks"])
+    Fc = pr.forces_canonical_fd()
+    Fa = pr.forces_direct_long()
+    rounding = 1e-10 if prec == "fp64" else 2e-6
+    tol = _forces_tol(cfg, rounding)
+    scale = np.abs(Fc).max()
+    assert np.abs(F - Ft).max() <= tol * scale
+    assert np.abs(F - Fc).max() <= tol * scale
+    assert np.linalg.norm(F - Fa) / np.linalg.norm(Fa) < tol
+    assert np.all(F[3] == 0.0)
+    assert np.abs(F.sum(0)).max() <= tol * scale * N
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
+def test_forces_pair_kernel_match_oracle(prec):
+    """RS_FORCES_PAIR: the untruncated long-range pair kernel plus the windows, against the
+    oracle's direct form element by element (FP64 products: 1e-10; FP32 products: 2e-6), and
+    against the oracle's RS-Tucker forces at the same ranks and the forces of the untruncated
+    Galerkin kernel (both within O(eps))."""
     rng = np.random.default_rng(12)
     cfg = dict(b=4.0, n=45, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8,
                precision=prec, snap=True)
@@ -401,7 +437,7 @@ def test_forces_match_oracle(prec):
     Z[3] = 0.0
     pr = O.Problem(cfg, xyz, Z)
     ctx = _ctx(cfg, N)
-    ctx.solve(torch.tensor(xyz, device="cuda"), torch.tensor(Z, device="cuda"), forces=True)
+    ctx.solve(torch.tensor(xyz, device="cuda"), torch.tensor(Z, device="cuda"), forces=True, forces_pair=True)
     F = ctx.forces().cpu().numpy()
     rep = ctx.report()
     assert rep["status"] == 0
@@ -418,10 +454,13 @@ def test_forces_match_oracle(prec):
     ctx.close()
 
 
-def test_forces_c2_full_size_sampled():
-    """Config 2 at full size (FP32 bulk): adjoint forces against the untruncated Galerkin
-    forces of the oracle on a sample of particles."""
-    cfg = load_config("c2_protein1000_n513")
+@pytest.mark.parametrize("name", ["c2_protein1000_n513", "c5_forces4096_n513"])
+def test_forces_full_size_sampled(name):
+    """Full size, FP32 bulk (the protein workload, and the forces workload's N = 4096 at snapped
+    centres): the discrete-gradient forces against the oracle's discrete gradient of the
+    untruncated long-range sum (plus windows) on a sample of particles, and against the forces of
+    the untruncated Galerkin kernel; O(eps) bounds as above."""
+    cfg = dict(load_config(name), snap=True)
     p = make_particles(cfg)
     pr = O.Problem(cfg, p.xyz, p.Z)
     ctx = _ctx(cfg, len(p.Z))
@@ -429,10 +468,20 @@ def test_forces_c2_full_size_sampled():
               want_potential=False)
     F = ctx.forces().cpu().numpy()
     assert ctx.report()["status"] == 0
+    sel = np.nonzero(pr.z != 0)[0][::29]
+    D = pr.fd_matrix()
+    G = O.canonical_fd_gradient_points(pr.j, pr.z, pr.pk, pr.klong, D, pr.j[sel])
+    G -= pr.z[sel, None] * O.fd_self_gradient(pr.j[sel], pr.pk, pr.klong, D)
+    dpk = O.reference_factor_derivatives(pr.t, pr.a, pr.h, pr.n)
+    Fw = O._window_forces(pr.j, pr.z, pr.pk, dpk, pr.kshort, pr.gamma, pr.n)[sel]
+    Fc = -pr.z[sel, None] * G + Fw
+    tol = _forces_tol(cfg, 2e-6)
+    err = np.linalg.norm(F[sel] - Fc) / np.linalg.norm(Fc)
+    print(f"{name}: discrete-gradient forces vs the oracle's untruncated discrete gradient {err:.2e}")
+    assert err < tol, err
     Fg = pr.forces_galerkin()
-    sel = np.nonzero(pr.z != 0)[0][::7]
-    err = np.linalg.norm(F[sel] - Fg[sel]) / np.linalg.norm(Fg[sel])
-    assert err < _forces_tol(cfg, 2e-6), err
+    err_g = np.linalg.norm(F[sel] - Fg[sel]) / np.linalg.norm(Fg[sel])
+    assert err_g < tol, err_g
     ctx.close()
 
 
