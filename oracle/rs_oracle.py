@@ -750,6 +750,65 @@ def rs_tucker_fd_forces(j, z, pk, dpk, klong, kshort, gamma: int, Z0s, beta, D):
 
 
 # ----------------------------------------------------------------------------
+# RS interaction matrix and its matrix-vector product  (Sec. 4.1 problem (B), Sec. 4.2)
+# ----------------------------------------------------------------------------
+def toeplitz_factor(pk_row, n: int, cut: int = -1):
+    """The n x n symmetric Toeplitz matrix T[i][i'] = p_k[i - i'] generated by one factor vector
+    (Sec. 4.1, case (A): the univariate matrices A_k^(l) of the Kronecker product sum), with the
+    entries beyond |i - i'| > cut set to zero when cut >= 0 (the window of a short-range term,
+    Def. 3.4)."""
+    c = n - 1
+    i = np.arange(n)
+    d = i[:, None] - i[None, :]
+    T = pk_row[d + c].copy()
+    if cut >= 0:
+        T[np.abs(d) > cut] = 0.0
+    return T
+
+
+def rs_matrix_dense(pk, klong, kshort, gamma: int, n: int):
+    """The RS interaction matrix of the n^3 grid points, A = A_l + A_s (Sec. 4.1, case (A)), as a
+    dense n^3 x n^3 array (C order, i3 fastest): the long part is the R_l-term Kronecker product
+    sum of Toeplitz factors, A_l = sum_{k long} T_k (x) T_k (x) T_k; the short part keeps the
+    R_s short terms inside the window |i_l - i'_l| <= gamma of every mode (the cumulated
+    canonical tensor of Defs. 3.4, 3.6), A_s = sum_{k short} T_k^gamma (x) T_k^gamma (x) T_k^gamma.
+    For small n only (n^6 entries)."""
+    N3 = n ** 3
+    A = np.zeros((N3, N3))
+    for k in klong:
+        T = toeplitz_factor(pk[k], n)
+        A += np.kron(np.kron(T, T), T)
+    for k in kshort:
+        T = toeplitz_factor(pk[k], n, gamma)
+        A += np.kron(np.kron(T, T), T)
+    return A
+
+
+def rs_matvec_dense(pk, klong, kshort, gamma: int, n: int, X, offdiag: bool = False):
+    """Y = A X with the dense RS interaction matrix (X an n^3 tensor); with ``offdiag`` the
+    diagonal part diag(A) X is left out (the matrix A - diag A of Eq. (4.6))."""
+    A = rs_matrix_dense(pk, klong, kshort, gamma, n)
+    if offdiag:
+        A = A - np.diag(np.diag(A))
+    return (A @ np.asarray(X, dtype=np.float64).ravel()).reshape((n, n, n))
+
+
+def charge_grid(j, z, n: int):
+    """The charges as an n^3 tensor: z_nu at the grid point j^(nu) (added if several share it)."""
+    C = np.zeros((n, n, n))
+    np.add.at(C, (j[:, 0], j[:, 1], j[:, 2]), np.asarray(z, dtype=np.float64))
+    return C
+
+
+def energy_matvec(pk, klong, kshort, gamma: int, n: int, j, z):
+    """E_N = 1/2 <(A - diag A) z, z> (Sec. 4.2, Eq. (4.6)) with the RS interaction matrix of the
+    grid and z the charges embedded in the grid (distinct grid points)."""
+    C = charge_grid(j, z, n)
+    Y = rs_matvec_dense(pk, klong, kshort, gamma, n, C, offdiag=True)
+    return 0.5 * float(np.sum(C * Y))
+
+
+# ----------------------------------------------------------------------------
 # Whole-problem driver used by the tests
 # ----------------------------------------------------------------------------
 class Problem:

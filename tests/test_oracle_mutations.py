@@ -30,6 +30,14 @@ def _small():
     return pr, pr.Pl_grid()
 
 
+def _matvec():
+    rng = np.random.default_rng(3)
+    cfg = P.small_cfg(b=2.0, n=11, R=10, R_s=3, h_q=0.8, u0=-4.0, delta_rel=1e-6)
+    xyz, z = P.random_particles(rng, 6, 1.8, 0.7)
+    pr = O.Problem(cfg, xyz, z)
+    return pr, O.rs_matrix_dense(pr.pk, pr.klong, pr.kshort, pr.gamma, pr.n)
+
+
 # -- planted mistakes ---------------------------------------------------------------------------
 def cell_integral_not_average(t, h, c):
     """Eq. (2.5) without the 1/h of the cell average."""
@@ -123,6 +131,18 @@ def tucker_fd_wrong_mode(j, z, pk, dpk, klong, kshort, gamma, Z0s, beta, D):
     return F
 
 
+def rs_matrix_short_uncut(pk, klong, kshort, gamma, n):
+    """The short-range terms of the RS matrix without their window."""
+    return ORIG["rs_matrix_dense"](pk, klong, kshort, n, n)
+
+
+def energy_matvec_with_diagonal(pk, klong, kshort, gamma, n, j, z):
+    """1/2 <A z, z> with the diagonal (self-interaction) left in."""
+    C = ORIG["charge_grid"](j, z, n)
+    return ORIG["energy_matvec"](pk, klong, kshort, gamma, n, j, z) + 0.5 * float(
+        np.sum(C * C)) * float(np.sum(pk[:, n - 1] ** 3))
+
+
 def snap_half_to_even(xyz, b, h, n):
     """Ties rounded half to even instead of away from zero."""
     j = np.rint((np.asarray(xyz, float) + b) / h).astype(np.int64)
@@ -146,6 +166,9 @@ CASES = [
     ("energy_from_potential", energy_without_half, P.test_energy_tensor_formula_matches_direct),
     ("forces_direct", forces_wrong_sign, P.test_forces_direct_finite_difference),
     ("snap_to_grid", snap_half_to_even, P.test_snap_rounding_and_bounds),
+    ("rs_matrix_dense", rs_matrix_short_uncut,
+     lambda: P.test_rs_matvec_of_the_charges_is_the_rs_canonical_tensor(_matvec())),
+    ("energy_matvec", energy_matvec_with_diagonal, lambda: P.test_energy_through_the_matrix(_matvec())),
     ("fd_matrix", fd_matrix_transposed, lambda: P.test_fd_forces_converge_to_the_analytic_long_range_forces(_c1())),
     ("rs_tucker_fd_forces", tucker_fd_wrong_mode,
      lambda: P.test_tucker_fd_forces_exact_at_full_rank_and_within_eps(_c1())),

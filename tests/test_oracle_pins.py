@@ -763,3 +763,78 @@ def test_fd_forces_momentum_and_self_term():
     sb = O.fd_self_gradient(jb, pr.pk, pr.klong, D)
     tiny = 1e-14 * pr.PRl0 / pr.h
     assert abs(sb[0, 1]) <= tiny and abs(sb[0, 2]) <= tiny and abs(sb[0, 0]) > 100 * tiny, sb
+
+
+# ---------------------------------------------------------------- RS interaction matrix (Sec. 4.1, 4.2)
+@pytest.fixture(scope="module")
+def matvec_problem():
+    rng = np.random.default_rng(3)
+    cfg = small_cfg(b=2.0, n=11, R=10, R_s=3, h_q=0.8, u0=-4.0, delta_rel=1e-6)
+    xyz, z = random_particles(rng, 6, 1.8, 0.7)
+    pr = O.Problem(cfg, xyz, z)
+    A = O.rs_matrix_dense(pr.pk, pr.klong, pr.kshort, pr.gamma, pr.n)
+    return pr, A
+
+
+def test_rs_matrix_is_symmetric_translation_invariant_kronecker(matvec_problem):
+    """A = A^T; an entry depends only on the difference of the two multi-indices (the d-level
+    Toeplitz structure of Sec. 4.1, case (A)); the diagonal is P_R(0); the short part vanishes
+    outside the window; on a 3-point grid the long part equals the brute-force sum of
+    separable products."""
+    pr, A = matvec_problem
+    n = pr.n
+    assert np.array_equal(A, A.T)
+    idx = np.stack(np.unravel_index(np.arange(n ** 3), (n, n, n)), 1)
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        a, b = rng.integers(0, n ** 3, 2)
+        s = rng.integers(-2, 3, 3)
+        ia, ib = idx[a] + s, idx[b] + s
+        if np.all((ia >= 0) & (ia < n) & (ib >= 0) & (ib < n)):
+            fa = np.ravel_multi_index(ia, (n, n, n))
+            fb = np.ravel_multi_index(ib, (n, n, n))
+            assert A[fa, fb] == A[a, b]
+    assert np.allclose(np.diag(A), pr.PR0, rtol=1e-14, atol=0)
+    # far apart (outside the window) only the long terms remain
+    i0 = np.ravel_multi_index((0, 0, 0), (n, n, n))
+    i1 = np.ravel_multi_index((n - 1, 0, 0), (n, n, n))
+    c = n - 1
+    assert abs(A[i0, i1] - sum(pr.pk[k, c - (n - 1)] * pr.pk[k, c] ** 2 for k in pr.klong)) <= 1e-15 * A[i0, i0]
+    # 3-point grid: every entry from its definition, k by k
+    m = 3
+    t, a = O.sinc_quadrature(4, 0.9, -2.0)
+    pk = O.reference_factors(t, a, 0.5, m)
+    A3 = O.rs_matrix_dense(pk, np.arange(4), np.arange(0), 0, m)
+    for p in range(m ** 3):
+        for q in range(m ** 3):
+            ip, iq = np.unravel_index(p, (m, m, m)), np.unravel_index(q, (m, m, m))
+            ref = sum(np.prod([pk[k, ip[l] - iq[l] + m - 1] for l in range(3)]) for k in range(4))
+            assert abs(A3[p, q] - ref) <= 1e-15 * abs(ref)
+
+
+def test_rs_matvec_of_the_charges_is_the_rs_canonical_tensor(matvec_problem):
+    """A applied to the charges embedded in the grid is the untruncated long-range canonical sum
+    plus the windows of the cumulated canonical tensor (Eq. (3.5) and Defs. 3.4, 3.6, computed by
+    their own functions): the matrix form of the RS tensor."""
+    pr, A = matvec_problem
+    C = O.charge_grid(pr.j, pr.z, pr.n)
+    Y = (A @ C.ravel()).reshape(C.shape)
+    ref = pr.Pl_grid() + pr.windows_grid()
+    assert np.abs(Y - ref).max() <= 1e-14 * np.abs(ref).max()
+    Y2 = O.rs_matvec_dense(pr.pk, pr.klong, pr.kshort, pr.gamma, pr.n, C, offdiag=True)
+    assert np.abs(Y2 - (Y - pr.PR0 * C)).max() <= 1e-14 * np.abs(ref).max()
+
+
+def test_energy_through_the_matrix(matvec_problem):
+    """E_N = 1/2 <(A - diag A) z, z> (Eq. (4.6)) equals Eq. (4.7) on the RS tensor at the
+    particles, the pair energy of the Galerkin kernel up to the window cut of the short terms,
+    and the direct Coulomb energy within the quadrature error."""
+    pr, _ = matvec_problem
+    E = O.energy_matvec(pr.pk, pr.klong, pr.kshort, pr.gamma, pr.n, pr.j, pr.z)
+    E47 = O.energy_from_potential(pr.Pl_points(pr.j) + pr.windows_points(pr.j), pr.z, pr.PR0)
+    scale = O.energy_scale(pr.xyz_snapped, pr.z)
+    assert abs(E - E47) <= 1e-13 * scale
+    Ep = O.galerkin_pair_energy(pr.xyz_snapped, pr.z, pr.t, pr.a, pr.kall, pr.h)
+    zz = float(np.sum(np.abs(np.outer(pr.z, pr.z))))
+    assert abs(E - Ep) <= pr.delta * zz + 1e-13 * scale
+    assert abs(E - pr.energy_direct_snapped()) <= 0.1 * scale
