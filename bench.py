@@ -569,6 +569,41 @@ def run_ours(args, rank, world, local_rank):
         fctx.close()
         del fpot
 
+    # the RS interaction matrix of the grid (Sec. 4.1, case (A)): one product A X with a random
+    # X (all R terms, 3R FFT mode passes), and the energy 1/2 <(A - diag A) z, z> (Eq. (4.6)) of
+    # the workload's charges through it
+    matvec = None
+    if not args.no_plain:
+        try:
+            ctx.solve(xyz, Z, potential=pot, energy=True)
+            Xm = torch.randn((n,) * 3, device="cuda", dtype=pot.dtype)
+            Ym = ctx.matvec(Xm)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(ctx.stream)
+            ctx.matvec(Xm, Ym)
+            b.record(ctx.stream)
+            torch.cuda.synchronize()
+            mv_ms = a.elapsed_time(b)
+            Em = ctx.energy_matvec()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Em = ctx.energy_matvec()
+            em_ms = 1e3 * (time.perf_counter() - t0)
+            R_all = int(cfg["R"])
+            mv_bytes = R_all * 3 * 8 * n ** 3 + R_all * 4 * n ** 3     # read + write per pass, + Y reads
+            matvec = {"ms": mv_ms, "terms": R_all, "mode_passes": 3 * R_all,
+                      "grid_pts_per_s": n ** 3 / (mv_ms * 1e-3),
+                      "achieved_gbs": mv_bytes / (mv_ms * 1e-3) / 1e9, "bytes": mv_bytes,
+                      "bytes_formula": "3R passes x (read + write of n^3 FP32) + R reads of Y",
+                      "energy_matvec_ms": em_ms, "energy_matvec": Em, "energy_rs_tucker": E,
+                      "path": "rs_matvec: Kronecker-Toeplitz terms by batched 1-D FFT convolutions "
+                              "(circulant size M = 2n - 2); rs_energy_matvec: charges embedded, A - diag A"}
+            del Xm, Ym
+        except Exception as e:  # reported, not fatal to the bench line
+            matvec = {"error": str(e)}
+
     # RS-canonical form of the last solve (Def. 3.7): the Tucker-to-canonical transform at the
     # accuracy the paper's RS-canonical ranks are quoted at (eps_T2C = 4e-6), and point values of
     # the canonical form (3 R* products per point, Lemma 3.8) against those of the Tucker form
@@ -671,6 +706,7 @@ def run_ours(args, rank, world, local_rank):
         "large": large,
         "forces": forces,
         "canonical": canonical,
+        "matvec": matvec,
         "als": als,
         "serving": serving,
         "energy": E,

@@ -347,6 +347,40 @@ void rs_server_destroy(rs_server* srv);
 rs_status rs_plain_direct(rs_ctx* ctx, float* out);
 rs_status rs_plain_canonical(rs_ctx* ctx, float* out);
 
+/* ---------------------------------------------------------------- RS interaction matrix
+ * Matrix-vector product with the RS interaction matrix of the n^3 grid points (Sec. 4.1,
+ * problem (B), case (A): the point set is the grid, N = n^3):
+ *   A = sum_{k long} T_k (x) T_k (x) T_k + sum_{k short} T_k^g (x) T_k^g (x) T_k^g,
+ * with T_k[i][i'] = p_k[i - i'] the symmetric Toeplitz matrix of the Galerkin factor vector p_k
+ * (Eq. (2.5)) and T_k^g the same inside the window |i - i'| <= gamma only (Def. 3.4), so that
+ * A applied to the charges embedded in the grid is the long-range canonical sum plus the windows
+ * (the RS tensor before the Tucker truncation).  Each Kronecker term is applied as three mode
+ * products by 1-D FFT convolutions of the fibres (circulant embedding of size M, the power of
+ * two >= 2n - 2): O(R n^3 log n) work, 3R kernel launches.
+ *   X, Y: distinct device buffers of n^3 elements (double for RS_FP64, float otherwise), C order,
+ *         8-byte aligned; Y is overwritten.
+ *   flags: RS_MATVEC_LONG and/or RS_MATVEC_SHORT select the terms (neither = both);
+ *          RS_MATVEC_OFFDIAG subtracts diag(A) X (diag A = sum of p_k[0]^3 over the selected
+ *          terms), the matrix A - diag A of Eq. (4.6).
+ * Needs no solve (the factors depend only on the configuration).  The first call allocates
+ * 2 n^3 elements of scratch and the symbols (R M + M elements), kept until rs_destroy.
+ * Asynchronous on the context stream.  Errors: RS_ERR_INVALID_ARG, RS_ERR_OOM, RS_ERR_CUDA.
+ * The products run in the precision of the context (FFT rounding: about 1e-7 of the result's
+ * norm per mode product in FP32). */
+#define RS_MATVEC_LONG    1
+#define RS_MATVEC_SHORT   2
+#define RS_MATVEC_OFFDIAG 4
+rs_status rs_matvec(rs_ctx* ctx, const void* X, void* Y, int flags);
+
+/* Interaction energy of the last solve's charges through the interaction matrix,
+ * E_N = 1/2 <(A - diag A) z, z> (Sec. 4.2, Eq. (4.6)), z the charges embedded in the grid at
+ * their snapped grid points and A as for rs_matvec (long and short terms): the energy of the RS
+ * tensor without the Tucker truncation, computed without forming the RS-Tucker tensor.  The first
+ * call allocates 2 n^3 more elements (the charge grid and its product).  Synchronises.
+ * Errors: RS_ERR_NOT_READY without a solve, RS_ERR_OOM, RS_ERR_CUDA, and the device-side input
+ * errors of the solve. */
+rs_status rs_energy_matvec(rs_ctx* ctx, double* E);
+
 /* Energy and forces of N centres anywhere in the box (not snapped) with the RS kernel of the
  * context in pair form: E = 1/2 sum_{j != nu} Z_j Z_nu K_h(x_j - x_nu), K_h(r) =
  * sum_{k<R} p_k(r1) p_k(r2) p_k(r3) with the Galerkin factors p_k continued to any offset (cell

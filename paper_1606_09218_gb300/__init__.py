@@ -163,6 +163,29 @@ class RSContext:
                                                   C.c_void_p(F.data_ptr()) if F is not None else None), self.h)
         return float(E.item()), F
 
+    def matvec(self, X, Y=None, long: bool = True, short: bool = True, offdiag: bool = False):
+        """Y = A X with the RS interaction matrix of the grid (rs_matvec; Sec. 4.1, case (A)):
+        X an (n, n, n) CUDA tensor of the context's dtype; returns Y (a new tensor if None)."""
+        torch = self._torch
+        X = X.contiguous()
+        assert X.is_cuda and X.dtype == self.dtype and X.numel() == self.n ** 3
+        if Y is None:
+            Y = torch.empty_like(X)
+        flags = (_lib.RS_MATVEC_LONG if long else 0) | (_lib.RS_MATVEC_SHORT if short else 0)
+        if not (long or short):
+            raise ValueError("select the long terms, the short terms or both")
+        if offdiag:
+            flags |= _lib.RS_MATVEC_OFFDIAG
+        _lib.check(self.lib.rs_matvec(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()), flags), self.h)
+        return Y
+
+    def energy_matvec(self) -> float:
+        """E_N = 1/2 <(A - diag A) z, z> of the last solve's charges through the interaction
+        matrix (rs_energy_matvec; Sec. 4.2, Eq. (4.6))."""
+        E = C.c_double()
+        _lib.check(self.lib.rs_energy_matvec(self.h, C.byref(E)), self.h)
+        return float(E.value)
+
     def plain_direct(self, out=None):
         """Direct sum sum_nu Z_nu / |x - x_nu| of the last solve's particles on the grid
         (plain-method GPU path, no RS format); returns the (n, n, n) float32 CUDA tensor."""

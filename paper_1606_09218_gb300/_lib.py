@@ -38,10 +38,12 @@ EXPORTED = ["rs_create", "rs_destroy", "rs_workspace_bytes", "rs_solve", "rs_ene
             "rs_tucker_als",
             "rs_profile_enable", "rs_profile_read", "rs_stage_name",
             "rs_debug_buffer", "rs_gram_noalloc", "rs_plain_direct", "rs_plain_canonical",
-            "rs_pair_energy_forces",
+            "rs_pair_energy_forces", "rs_matvec", "rs_energy_matvec",
             "rs_server_create", "rs_submit", "rs_wait", "rs_server_info", "rs_server_destroy",
             "rs_last_error", "rs_version"]
 RS_NSTAGE = 9
+# rs_matvec flags
+RS_MATVEC_LONG, RS_MATVEC_SHORT, RS_MATVEC_OFFDIAG = 1, 2, 4
 
 
 class RSConfigC(C.Structure):
@@ -101,6 +103,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.rs_forces.restype = C.c_int
     lib.rs_pair_energy_forces.argtypes = [vp, C.c_int, vp, vp, vp, vp]
     lib.rs_pair_energy_forces.restype = C.c_int
+    lib.rs_matvec.argtypes = [vp, vp, vp, C.c_int]
+    lib.rs_matvec.restype = C.c_int
+    lib.rs_energy_matvec.argtypes = [vp, C.POINTER(C.c_double)]
+    lib.rs_energy_matvec.restype = C.c_int
     for nm in ("rs_plain_direct", "rs_plain_canonical"):
         getattr(lib, nm).argtypes = [vp, vp]
         getattr(lib, nm).restype = C.c_int

@@ -133,7 +133,7 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.fd_s, 4 * n);
   add(v, c.dZ64, 8 * 3 * n * rm);
   add(v, c.dZ32, 4 * 3 * n * rm);
-  add(v, c.T1d, ts * rm * rm * n);
+  add(v, c.T1d, 2 * ts * rm * rm * n);
   add(v, c.sc, sizeof(DevScalars));
   if (c.use_tc) {
     const size_t nT = (size_t)c.tc_ntiles;
@@ -176,6 +176,7 @@ void free_all(Ctx& c) {
   c.h_sc = nullptr;
   free_canonical(c);
   free_als(c);
+  free_matvec(c);
   if (c.ev_part) cudaEventDestroy(c.ev_part);
   if (c.ev_bins) cudaEventDestroy(c.ev_bins);
   if (c.ev_side) cudaEventDestroy(c.ev_side);
@@ -261,6 +262,7 @@ bool ensure_kernel_attributes(std::string& err) {
   if (e == cudaSuccess) e = set_attributes_core(optin);
   if (e == cudaSuccess) e = set_attributes_plain(optin);
   if (e == cudaSuccess) e = set_attributes_canonical(optin);
+  if (e == cudaSuccess) e = set_attributes_matvec(optin);
   if (e != cudaSuccess) {
     err = std::string("kernel attributes: ") + cudaGetErrorString(e);
     cudaGetLastError();
@@ -794,6 +796,42 @@ rs_status rs_pair_energy_forces(rs_ctx* h, int N, const double* xyz, const doubl
   const rs_status st = launch_pair_energy_forces(c, N, xyz, Z, E, F);
   if (st != RS_OK) return fail(c, st, "more quadrature terms than the pair kernel supports");
   return check_launch(c, "pair_energy_forces");
+}
+
+rs_status rs_matvec(rs_ctx* h, const void* X, void* Y, int flags) {
+  if (!h) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!X || !Y || ((uintptr_t)X & 7u) || ((uintptr_t)Y & 7u) || X == Y)
+    return fail(c, RS_ERR_INVALID_ARG, "matvec: X and Y must be distinct 8-byte aligned device buffers");
+  if (flags & ~(RS_MATVEC_LONG | RS_MATVEC_SHORT | RS_MATVEC_OFFDIAG))
+    return fail(c, RS_ERR_INVALID_ARG, "matvec: unknown flags");
+  int which = flags & (RS_MATVEC_LONG | RS_MATVEC_SHORT);
+  if (which == 0) which = RS_MATVEC_LONG | RS_MATVEC_SHORT;
+  std::string err;
+  const int k = launch_matvec(c, X, Y, which, (flags & RS_MATVEC_OFFDIAG) != 0, err);
+  if (k < 0) return fail(c, RS_ERR_OOM, err);
+  return check_launch(c, "matvec");
+}
+
+rs_status rs_energy_matvec(rs_ctx* h, double* E) {
+  if (!h || !E) return RS_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.solved) return fail(c, RS_ERR_NOT_READY, "no solve");
+  std::string err;
+  const int k = launch_energy_matvec(c, err);
+  if (k < 0) return fail(c, RS_ERR_OOM, err);
+  rs_status st = check_launch(c, "energy_matvec");
+  if (st != RS_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(E, c.mv_E, sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, RS_ERR_CUDA, std::string("energy_matvec: ") + cudaGetErrorString(e));
+  }
+  st = sync_scalars(c);
+  if (st != RS_OK) return st;
+  const rs_status s2 = status_of(*c.h_sc);
+  return s2 < 0 ? s2 : RS_OK;
 }
 
 rs_status rs_plain_direct(rs_ctx* h, float* out) { return plain_entry(h, out, 0); }

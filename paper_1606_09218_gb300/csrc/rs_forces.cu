@@ -6,7 +6,7 @@
 //   d1 P_l^T(i) = sum_ab (D_h V1)[i1][a] V2[i2][b] T1[a][b][i3]
 //   d2 P_l^T(i) = sum_ab V1[i1][a] (D_h V2)[i2][b] T1[a][b][i3]
 //   d3 P_l^T(i) = sum_ab V1[i1][a] V2[i2][b] T1d[a][b][i3]
-// with T1 = beta x_3 V3 (already formed for the reconstruction) and T1d = beta x_3 (D_h V3).
+// with T1 = beta x_3 V3 and T1d = beta x_3 (D_h V3), both formed here in i3-major layout.
 // The force on particle j is F_j = -z_j [grad_h P_l^T(x_j) - z_j grad_h K_l(0)] minus the
 // window gradients of the other particles (term by term, as in the pair path), the particle's
 // own long-range term taken out (its centred difference is zero; a one-sided row near the ends
@@ -107,7 +107,7 @@ template <> struct FdBulk<double> {
 // One warp per charged particle: the three differentiated Tucker values at its grid point (the
 // lanes share the (a, b) pairs; products of T, sums in FP64), its own term's difference, and the
 // window gradients of the other particles; F = -z (grad - z grad_self).  Particles without
-// charge keep the zero force of the memset.
+// charge keep the zero force of the memset.  T1, T1d: the slices [i3][a][b] (leading size rmax^2).
 template <typename T>
 __global__ void __launch_bounds__(256)
 forces_rs_kernel(DevView c, const T* __restrict__ Zb, const T* __restrict__ dZb, const T* __restrict__ T1,
@@ -127,10 +127,12 @@ forces_rs_kernel(DevView c, const T* __restrict__ Zb, const T* __restrict__ dZb,
   const T* D1 = dZb + (long long)i1 * rmax;
   const T* D2 = dZb + sZ + (long long)i2 * rmax;
   double g1 = 0.0, g2 = 0.0, g3 = 0.0;
+  const T* S = T1 + (long long)i3 * rmax * rmax;      // slices at i3 ([a][b], i3-major layout)
+  const T* Sd = T1d + (long long)i3 * rmax * rmax;
   for (int e = lane; e < r1 * r2; e += 32) {
     const int a = e / r2, b = e % r2;
-    const long long o = ((long long)a * rmax + b) * n + i3;
-    const double t = (double)T1[o], td = (double)T1d[o];
+    const long long o = (long long)a * rmax + b;
+    const double t = (double)S[o], td = (double)Sd[o];
     const double u = (double)V1[a], ud = (double)D1[a], v = (double)V2[b], vd = (double)D2[b];
     g1 += ud * v * t;
     g2 += u * vd * t;
@@ -174,18 +176,24 @@ template <typename T>
 static int forces_rs_t(Ctx& c) {
   const int n = c.n, rmax = c.rmax;
   fd_basis_kernel<<<dim3(n, 3), 128, 0, c.stream>>>(c.Z64, c.fd_w, c.fd_s, n, rmax, c.sc, c.dZ64, c.dZ32);
-  // T1d[a][b][i3] = sum_c beta[a][b][c] (D_h V3)[i3][c], the product that forms T1
+  // the slices of T1 = beta x_3 V3 and T1d = beta x_3 (D_h V3) at one grid index i3, laid out
+  // i3-major ([i3][a][b], two row blocks of T1d) so that the lanes of a warp read consecutive b:
+  //   T1d[i3][(a, b)] = sum_c V3[i3][c] beta[(a, b)][c],  T1d[n + i3][(a, b)] = sum_c (D_h V3)[i3][c] beta[(a, b)][c]
   const long long sZ = (long long)n * rmax;
-  gemm_batched<T>(c.stream, false, true, rmax * rmax, n, rmax, T(1), (const T*)c.beta, rmax, 0,
-                  FdBulk<T>::dZ(c) + 2 * sZ, rmax, 0, T(0), (T*)c.T1d, n, 0, 1, nullptr, nullptr, c.sc->rank + 2,
+  const long long slab = (long long)n * rmax * rmax;
+  gemm_batched<T>(c.stream, false, true, n, rmax * rmax, rmax, T(1), FdBulk<T>::Z(c) + 2 * sZ, rmax, 0,
+                  (const T*)c.beta, rmax, 0, T(0), (T*)c.T1d, rmax * rmax, 0, 1, nullptr, nullptr, c.sc->rank + 2,
                   &c.gscr);
+  gemm_batched<T>(c.stream, false, true, n, rmax * rmax, rmax, T(1), FdBulk<T>::dZ(c) + 2 * sZ, rmax, 0,
+                  (const T*)c.beta, rmax, 0, T(0), (T*)c.T1d + slab, rmax * rmax, 0, 1, nullptr, nullptr,
+                  c.sc->rank + 2, &c.gscr);
   cudaMemsetAsync(c.Fout, 0, sizeof(double) * 3 * (size_t)c.maxN, c.stream);
   int blocks = (c.maxN + 7) / 8;
   if (blocks < 1) blocks = 1;
   forces_rs_kernel<T><<<blocks, 256, 0, c.stream>>>(make_view(c), FdBulk<T>::Z(c), FdBulk<T>::dZ(c),
-                                                    (const T*)c.T1, (const T*)c.T1d, c.dpk64, c.fd_w, c.fd_s,
-                                                    c.Fout);
-  return 3;
+                                                    (const T*)c.T1d, (const T*)c.T1d + slab, c.dpk64, c.fd_w,
+                                                    c.fd_s, c.Fout);
+  return 4;
 }
 
 int launch_forces_rs(Ctx& c) { return c.fp64 ? forces_rs_t<double>(c) : forces_rs_t<float>(c); }

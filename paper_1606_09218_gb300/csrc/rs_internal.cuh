@@ -158,7 +158,17 @@ struct Ctx {
   int*    fd_s = nullptr;       // n: first grid index of each row's stencil
   double* dZ64 = nullptr;       // 3 x n x rmax: D_h applied to the Tucker bases
   float*  dZ32 = nullptr;
-  void*   T1d = nullptr;        // rmax x rmax x n (T): beta x_3 (D_h V3)
+  void*   T1d = nullptr;        // 2 x n x rmax x rmax (T): beta x_3 V3 and beta x_3 (D_h V3), i3-major
+  // RS interaction matrix products (rs_matvec.cu; allocated by the first call)
+  int mv_M = 0, mv_logM = 0, mv_B = 0;   // circulant size, log2, fibre pairs per CTA
+  void* mv_sym = nullptr;       // R x M symbols (T), divided by M
+  void* mv_tw = nullptr;        // M/2 twiddles (complex T)
+  void* mv_U = nullptr;         // n^3 (T) intermediates of the mode products
+  void* mv_V = nullptr;
+  void* mv_X = nullptr;         // n^3 (T) charge grid and product of the energy call
+  void* mv_Y = nullptr;
+  double* mv_E = nullptr;       // energy of the energy call (device)
+  bool mv_symbols_ready = false;
   // tensor-core assembly of the FP32 output (rs_tc.cu), planned at create
   bool use_tc = false;
   int t2_ld = 0;                // i3 stride of T2 on the CUDA-core path
@@ -306,6 +316,11 @@ constexpr int FD_ORDER = 8;             // order of the centred difference formu
 constexpr int FD_WIDTH = FD_ORDER + 1;  // points per row
 bool fd_table(int n, double h, double* w, int* start);   // host: the rows of D_h
 int launch_forces_rs(Ctx& c);
+// RS interaction matrix (rs_matvec.cu): Y = A X for n^3 tensors; the energy through it
+int launch_matvec(Ctx& c, const void* X, void* Y, int which, bool offdiag, std::string& err);
+int launch_energy_matvec(Ctx& c, std::string& err);
+void free_matvec(Ctx& c);
+cudaError_t set_attributes_matvec(int optin);
 
 // Kernels launched with more than 48 KB of dynamic shared memory.  The limit is an attribute of
 // the kernel (process-wide per device), so it is raised once per device to the opt-in maximum
