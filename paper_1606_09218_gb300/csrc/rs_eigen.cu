@@ -946,6 +946,9 @@ __global__ void gather_Z_kernel(const double* Q, const int* order, int n, int ks
 }
 
 // ------------------------------------------------------------------ driver
+// sweeps and relative off-diagonal tolerance of the Jacobi pass
+constexpr int JACOBI_SWEEPS = 16;
+constexpr float JACOBI_TOL = 1e-5f;
 // T <- W^T T W for the leading ke block (two k x k products through T2k)
 static void congruence(Ctx& c, double* Tm, const double* Wm) {
   const int ks = c.ksub;
@@ -957,40 +960,41 @@ static void congruence(Ctx& c, double* Tm, const double* Wm) {
                        Tm, ks, sK, 3, ke, ke, ke, &c.gscr);
 }
 
-// Rayleigh-Ritz refinement: two FP32 Jacobi passes on the graded T (rotations accumulated in
-// FP64), one Newton-Schulz re-orthonormalisation of the accumulated rotation, one rotation of
-// the basis.  The basis Qa from the block Gram-Schmidt is orthonormal to working precision, so
-// the loss of orthogonality of Qa W1 W2 is that of W = W1 W2 (FP32 rotations): E = W^T W - I,
-// M = I - E/2 + 3/8 E^2, and the final basis is Qa (W M) — k x k products, one n x k product.
+// Rayleigh-Ritz refinement: one FP32 Jacobi pass on the graded T (rotations accumulated in FP32,
+// returned in FP64), one Newton-Schulz re-orthonormalisation of the accumulated rotation, one
+// rotation of the basis and one FP64 congruence of T.  The basis Qa from the block Gram-Schmidt
+// is orthonormal to working precision, so the loss of orthogonality of Qa W is that of W (FP32
+// rotations): E = W^T W - I, M = I - E/2 + 3/8 E^2, and the final basis is Qa (W M) — k x k
+// products, one n x k product.  The diagonal of the final T = (W M)^T T (W M), formed in FP64,
+// gives the eigenvalues of the rank rule: the Jacobi pass stops when every off-diagonal entry is
+// below JACOBI_TOL times the geometric mean of its two diagonal entries, so each diagonal entry
+// differs from its eigenvalue by second order in that bound (relative 1e-8 and below), and a
+// retained and a discarded direction mix by an angle that weighs the discarded energy, which is
+// below the eps budget already.
 static int refine(Ctx& c, double*& Qa, double*& Qb) {
   const int n = c.n, ks = c.ksub;
   const long long sQ = (long long)n * ks, sK = (long long)ks * ks;
   const int* ke = c.sc->k_eff;
   size_t shm = 2ull * ks * (ks + 1) * sizeof(float);
-  // pass 1: T -> W1^T T W1
-  jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, 12, 1e-4f);
-  congruence(c, c.T, c.W);
-  // pass 2: T -> W2^T T W2
-  jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W2, ks, c.sc, 4, 2e-7f);
-  congruence(c, c.T, c.W2);
-  // T2k = W = W1 W2 ; W2 = E = W^T W - I ; c.W = E^2 ; W2 = M
-  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W2, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, ke, ke, ke, &c.gscr);
-  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.T2k, ks, sK, c.T2k, ks, sK, 0.0,
+  // one pass: T -> W^T T W (the FP32 rotations accumulated in W)
+  jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, JACOBI_SWEEPS, JACOBI_TOL);
+  // W2 = E = W^T W - I ; T2k = E^2 ; W2 = M
+  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W, ks, sK, 0.0,
                        c.W2, ks, sK, 3, ke, ke, ke, &c.gscr);
   dim3 g2((ks * ks + 255) / 256, 3);
   sub_identity_kernel<<<g2, 256, 0, c.stream>>>(c.W2, ks, c.sc);
   gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W2, ks, sK, c.W2, ks, sK, 0.0,
-                       c.W, ks, sK, 3, ke, ke, ke, &c.gscr);
-  ns_matrix_kernel<<<g2, 256, 0, c.stream>>>(c.W2, c.W, c.W2, ks, c.sc);
-  // c.W = W M ; Qb = Qa (W M) ; T = M^T T M
-  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.T2k, ks, sK, c.W2, ks, sK, 0.0,
-                       c.W, ks, sK, 3, ke, ke, ke, &c.gscr);
-  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, c.W, ks, sK, 0.0, Qb,
+                       c.T2k, ks, sK, 3, ke, ke, ke, &c.gscr);
+  ns_matrix_kernel<<<g2, 256, 0, c.stream>>>(c.W2, c.T2k, c.W2, ks, c.sc);
+  // WM = W M (in the free product buffer Y) ; Qb = Qa (W M) ; T = (W M)^T T (W M)
+  double* WM = c.Y;
+  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W2, ks, sK, 0.0,
+                       WM, ks, sK, 3, ke, ke, ke, &c.gscr);
+  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, WM, ks, sK, 0.0, Qb,
                        ks, sQ, 3, nullptr, ke, ke, &c.gscr);
-  congruence(c, c.T, c.W2);
+  congruence(c, c.T, WM);
   std::swap(Qa, Qb);
-  return 2 + 2 + 2 + 1 + 1 + 1 + 1 + 1 + 1 + 1 + 2;
+  return 1 + 1 + 1 + 1 + 1 + 1 + 1 + 2;
 }
 
 int launch_subspace(Ctx& c) {
