@@ -26,12 +26,12 @@
 //    byte offset apart: no per-window B is built.
 // The epilogue scales both accumulators back (exact powers of two) and adds them.
 //
-// CTA (persistent, one per SM, 14 warps):
+// CTA (persistent, one per SM, 18 warps):
 //   warp 0     tensor-memory owner; lane 0 issues the MMAs (straight-line, descriptors precomputed)
 //   warp 1     scheduler: bulk copy of the T2 tiles of the next jobs, window list pages
-//   warps 2-5  producers: window operand pairs -> ring of slots (+ ready-made descriptors),
-//              two pairs per step when two slots are free
-//   warps 6-13 epilogue: tensor memory -> registers -> global, each warp writing 128-byte
+//   warps 2-9  producers, two groups of four: window operand pairs -> ring of slots (+ ready-made
+//              descriptors); group g builds the pairs of parity g, so two pairs are built at once
+//   warps 10-17 epilogue: tensor memory -> registers -> global, each warp writing 128-byte
 //              runs of a plane row (streaming stores)
 // A CTA keeps one i1 chunk (its V1 rows, split, as the B operand of the Tucker part) and walks
 // over the tiles; the CTAs are spread over the chunks in proportion to their work (tiles plus
@@ -55,9 +55,10 @@ namespace {
 
 constexpr int AS_M = 128;                  // grid points per tile (tensor-memory lanes)
 constexpr int AS_T3 = 32;                  // i3 columns per CTA of the T2 tile kernel
-constexpr int AS_THREADS = 448;            // 14 warps
-constexpr int WARP_SCHED = 1, WARP_PROD = 2, WARP_EPI = 6;
-constexpr int NPW = 4;                     // producer warps
+constexpr int AS_THREADS = 576;            // 18 warps
+constexpr int WARP_SCHED = 1, WARP_PROD = 2, WARP_EPI = 10;
+constexpr int NPW = 4;                     // warps of one producer group (one per operand row quarter)
+constexpr int NPG = 2;                     // producer groups
 constexpr int NEPI = 8;                    // epilogue warps
 constexpr int NA_MAX = 3, NS_MAX = 8;      // T2 tile stages, window pair slots
 constexpr int STG_ROW = 132;               // floats per staging row (128 + alignment shift)
@@ -66,7 +67,9 @@ constexpr int WL_SORT_CAP = 4096;          // longest window list of one tile co
 constexpr int SMEM_LIMIT = 232448;         // opt-in shared memory per CTA on this GPU family
 constexpr int SMEM_RESERVE = 1024;         // static shared memory of the kernel
 constexpr double COST_TILE = 2500.0;       // relative cost of one tile job (output bound)
-constexpr double COST_WINDOW = 250.0;      // relative cost of one window of a job (fitted to role traces)
+constexpr double COST_WINDOW = 87.0;       // relative cost of one window of a job (fitted to role traces:
+                                           // about 7.8K cycles per job and 270 per window on the
+                                           // protein workload, with two producer groups)
 constexpr int TT_ROWS = 32;                // i2 rows per CTA of the T2 tile kernel
 
 // Scale exponent S of the Tucker operands: 2^(S-8) max_a ||beta[a]|| < 2^14.
@@ -322,7 +325,7 @@ assemble_kernel(const AsmArgs g) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&bar_list_full[b], 1);
-      mbar_init(&bar_list_empty[b], NPW);
+      mbar_init(&bar_list_empty[b], NPW * NPG);
       mbar_init(&bar_d_full[b], 1);
       mbar_init(&bar_d_empty[b], NEPI);
     }
@@ -487,13 +490,29 @@ assemble_kernel(const AsmArgs g) {
     __syncwarp();
   } else if (warp == WARP_SCHED) {
     // ------------------------------------------------------------ scheduler
+    // Per job: the first page of its window list (the producers' input; it needs only a free
+    // page), then the T2 tile (which waits for a free operand stage, that is for the MMAs of an
+    // earlier job), then the rest of the list.  Copying the first page before the stage wait
+    // keeps the producers from waiting behind the MMA issuer.
     int pg = 0, issued = 0, st = 0;
     uint32_t stph = 0;
+    auto copy_page = [&](const int2 rg, int total, int off) -> bool {
+      const int b = pg & 1;
+      if (pg >= 2 && !warp_wait(&bar_list_empty[b], ((pg - 2) >> 1) & 1, abort_flag, sc)) return false;
+      const int cnt = min(LIST_CAP, total - off);
+      for (int i = lane; i < cnt; i += 32) lists[b * LIST_CAP + i] = g.rec[rg.x + off + i];
+      if (lane == 0) { page_n[b] = cnt; page_total[b] = total; }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_list_full[b]);
+      ++pg;
+      return true;
+    };
     for (int t = 0; t < njobs; ++t) {
       const int T = j0 + t * jstride;
       int2 rg = make_int2(0, 0);
       if (g.rng) rg = g.rng[(long long)T * g.nch + chunk];
       const int total = rg.y - rg.x;
+      if (!copy_page(rg, total, 0)) break;
       int ok = 1;
       if (lane == 0) {
         if (t >= g.na) ok = wait_bar(&bar_a_empty[st], stph ^ 1u, abort_flag, sc);
@@ -507,17 +526,8 @@ assemble_kernel(const AsmArgs g) {
       }
       if (++st == g.na) { st = 0; stph ^= 1u; }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      for (int off = 0;; off += LIST_CAP) {
-        const int b = pg & 1;
-        if (pg >= 2 && !warp_wait(&bar_list_empty[b], ((pg - 2) >> 1) & 1, abort_flag, sc)) { ok = 0; break; }
-        const int cnt = min(LIST_CAP, total - off);
-        for (int i = lane; i < cnt; i += 32) lists[b * LIST_CAP + i] = g.rec[rg.x + off + i];
-        if (lane == 0) { page_n[b] = cnt; page_total[b] = total; }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bar_list_full[b]);
-        ++pg;
-        if (off + LIST_CAP >= total) break;
-      }
+      for (int off = LIST_CAP; off < total; off += LIST_CAP)
+        if (!copy_page(rg, total, off)) { ok = 0; break; }
       if (!ok) break;
     }
     // the copies issued last have landed before the CTA exits
@@ -527,18 +537,20 @@ assemble_kernel(const AsmArgs g) {
     __syncwarp();
   } else if (warp < WARP_EPI) {
     // ------------------------------------------------------------ producers
-    // Thread pt builds row m = pt of the A operands; up to two pairs of windows (two slots) per
-    // step, with every load issued before the arithmetic, so the latency of one pair hides
-    // behind the other.  The descriptors of pair q are written by lane 0 of producer warp q mod 4.
-    const int pt = tid - WARP_PROD * 32;       // operand row m
-    const int pw = warp - WARP_PROD;           // producer warp
+    // Two groups of NPW warps.  Pair P (the running count of this CTA's window pairs over its
+    // jobs) goes to slot P mod ns and is built by group P mod 2: thread pt of a group builds row
+    // m = pt of both windows' A operands, every load issued before the arithmetic.  The
+    // descriptors of a pair are written by lane 0 of one warp of its group.  Both groups walk
+    // every page of a job's window list and release it.
+    const int pw = warp - WARP_PROD;           // producer warp 0 .. NPG * NPW - 1
+    const int gp = pw / NPW, wg = pw % NPW;    // group, warp within the group
+    const int pt = (tid - WARP_PROD * 32) & (AS_M - 1);   // operand row m
     unsigned char* slot_base = smem + g.off_slot;
     const float sA = ldexpf(1.0f, s_shiftA);
     const uint32_t tbl_h = smem_addr(Th), tbl_l = smem_addr(Tl);
     const float4* tab4 = (const float4*)tab;
-    int pg = 0, sl = 0;
-    uint32_t slph = 0;
-    int used = 0;                              // pair slots filled so far (first ns need no wait)
+    int pg = 0;                                // list pages walked so far
+    long long P0 = 0;                          // pairs of the earlier jobs
     // 16-column groups of the chunk that a pair reaches (all of them for the first pair of a
     // job, which overwrites the window accumulator), the table rows of its first row for each
     // window, and the descriptors
@@ -569,44 +581,43 @@ assemble_kernel(const AsmArgs g) {
       int b = pg & 1;
       if (!warp_wait(&bar_list_full[b], (pg >> 1) & 1, abort_flag, sc)) break;
       const int nw = page_total[b];
+      const int npair = (nw + 1) >> 1;
+      const int npages = nw > 0 ? (nw + LIST_CAP - 1) / LIST_CAP : 1;
+      int page = 0;                            // page of this job that pg refers to
       const long long p = (long long)T * AS_M + pt;
       const bool valid = p < np;
       const int i2 = valid ? (int)(p / n) : 0, i3 = valid ? (int)(p - (long long)i2 * n) : 0;
       bool ok = true;
-      int pos = 0, pn = page_n[b];
-      for (int q = 0; 2 * q < nw;) {
-        if (pos == pn) {                       // pages hold an even number of records
+      for (int q = gp; q < npair; q += NPG) {
+        const int r0 = 2 * q;                  // first record of the pair (pages hold an even number)
+        while (page < r0 / LIST_CAP) {         // on to the page of this pair
           __syncwarp();
           if (lane == 0) mbar_arrive(&bar_list_empty[b]);
           ++pg;
+          ++page;
           b = pg & 1;
           if (!warp_wait(&bar_list_full[b], (pg >> 1) & 1, abort_flag, sc)) { ok = false; break; }
-          pos = 0;
-          pn = page_n[b];
         }
-        // pairs in this step: two need two distinct slots
-        const int np_ = (g.ns >= 2 && 2 * (q + 1) < nw && pos + 2 < pn) ? 2 : 1;
-        int4 w[4];
-        bool live[4];
+        if (!ok) break;
+        const int pos = r0 - page * LIST_CAP, pn = page_n[b];
+        int4 w[2];
+        bool live[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          live[u] = (u >> 1) < np_ && pos + u < pn;
-          // a missing second window repeats the first of its pair (zero operand, lbo 0)
-          const int r = live[u] ? pos + u : ((u >> 1) < np_ ? pos + (u & 2) : pos);
-          w[u] = lists[b * LIST_CAP + r];
+        for (int u = 0; u < 2; ++u) {
+          live[u] = pos + u < pn;
+          // a missing second window repeats the first (zero operand, lbo 0)
+          w[u] = lists[b * LIST_CAP + (live[u] ? pos + u : pos)];
         }
+        if (live[1] && w[1].x > w[0].x) {      // chunk 0 of a pair: the window with the larger j1
+          const int4 tmp = w[0];
+          w[0] = w[1];
+          w[1] = tmp;
+        }
+        // factor rows of the two windows, loaded before the slot wait
+        float4 ra[2][2], rb[2][2];
+        float zz[2];
 #pragma unroll
-        for (int v = 0; v < 2; ++v)            // chunk 0 of a pair: the window with the larger j1
-          if (live[2 * v + 1] && w[2 * v + 1].x > w[2 * v].x) {
-            const int4 tmp = w[2 * v];
-            w[2 * v] = w[2 * v + 1];
-            w[2 * v + 1] = tmp;
-          }
-        // factor rows of the four windows, loaded before any slot wait
-        float4 ra[4][2], rb[4][2];
-        float zz[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
           const int d2 = i2 - w[u].y, d3 = i3 - w[u].z;
           const bool in23 = live[u] && valid && d2 >= -gam && d2 <= gam && d3 >= -gam && d3 <= gam;
           const float4* r2 = tab4 + 2 * (in23 ? d2 + g.gcap : 0);
@@ -617,47 +628,42 @@ assemble_kernel(const AsmArgs g) {
           rb[u][1] = r3[1];
           zz[u] = in23 ? __int_as_float(w[u].w) * sA : 0.f;
         }
-        const int sl1 = (sl + 1 == g.ns) ? 0 : sl + 1;
-        const uint32_t slph1 = (sl + 1 == g.ns) ? (slph ^ 1u) : slph;
-        if (used >= g.ns && !warp_wait(&bar_slot_free[sl], slph ^ 1u, abort_flag, sc)) { ok = false; break; }
-        if (np_ == 2 && used + 1 >= g.ns && !warp_wait(&bar_slot_free[sl1], slph1 ^ 1u, abort_flag, sc)) {
-          ok = false;
-          break;
-        }
+        const long long P = P0 + q;
+        const int sl = (int)(P % g.ns);
+        const uint32_t ph = (uint32_t)((P / g.ns) & 1);
+        if (P >= g.ns && !warp_wait(&bar_slot_free[sl], ph ^ 1u, abort_flag, sc)) { ok = false; break; }
+        unsigned char* sbh = slot_base + (size_t)sl * 2 * SLOT_HALF;
+        unsigned char* sbl = sbh + SLOT_HALF;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if ((u >> 1) < np_) {
-            unsigned char* sbh = slot_base + (size_t)((u >> 1) ? sl1 : sl) * 2 * SLOT_HALF;
-            unsigned char* sbl = sbh + SLOT_HALF;
-            const float z = zz[u];
-            uint4 hi, lo;
-            split_h2(z * ra[u][0].x * rb[u][0].x, z * ra[u][0].y * rb[u][0].y, hi.x, lo.x);
-            split_h2(z * ra[u][0].z * rb[u][0].z, z * ra[u][0].w * rb[u][0].w, hi.y, lo.y);
-            split_h2(z * ra[u][1].x * rb[u][1].x, z * ra[u][1].y * rb[u][1].y, hi.z, lo.z);
-            split_h2(z * ra[u][1].z * rb[u][1].z, z * ra[u][1].w * rb[u][1].w, hi.w, lo.w);
-            const uint32_t off = kmajor_offset(pt, u & 1, 2);
-            *(uint4*)(sbh + off) = hi;
-            *(uint4*)(sbl + off) = lo;
-          }
+        for (int u = 0; u < 2; ++u) {
+          const float z = zz[u];
+          uint4 hi, lo;
+          split_h2(z * ra[u][0].x * rb[u][0].x, z * ra[u][0].y * rb[u][0].y, hi.x, lo.x);
+          split_h2(z * ra[u][0].z * rb[u][0].z, z * ra[u][0].w * rb[u][0].w, hi.y, lo.y);
+          split_h2(z * ra[u][1].x * rb[u][1].x, z * ra[u][1].y * rb[u][1].y, hi.z, lo.z);
+          split_h2(z * ra[u][1].z * rb[u][1].z, z * ra[u][1].w * rb[u][1].w, hi.w, lo.w);
+          const uint32_t off = kmajor_offset(pt, u, 2);
+          *(uint4*)(sbh + off) = hi;
+          *(uint4*)(sbl + off) = lo;
         }
-        if (lane == 0 && (q & 3) == pw) header(sl, q, w[0], w[1], live[1]);
-        if (np_ == 2 && lane == 0 && ((q + 1) & 3) == pw) header(sl1, q + 1, w[2], w[3], live[3]);
+        if (lane == 0 && ((q / NPG) % NPW) == wg) header(sl, q, w[0], w[1], live[1]);
         fence_proxy_async();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&bar_slot_full[sl]);
-          if (np_ == 2) mbar_arrive(&bar_slot_full[sl1]);
-        }
-        for (int u = 0; u < np_; ++u)
-          if (++sl == g.ns) { sl = 0; slph ^= 1u; }
-        used += np_;
-        q += np_;
-        pos += 2 * np_;
+        if (lane == 0) mbar_arrive(&bar_slot_full[sl]);
       }
       if (!ok) break;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bar_list_empty[b]);
-      ++pg;
+      // release this page and walk (and release) the job's remaining pages
+      while (true) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_list_empty[b]);
+        ++pg;
+        ++page;
+        if (page >= npages) break;
+        b = pg & 1;
+        if (!warp_wait(&bar_list_full[b], (pg >> 1) & 1, abort_flag, sc)) { ok = false; break; }
+      }
+      if (!ok) break;
+      P0 += npair;
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -952,10 +958,11 @@ bool plan_assemble(Ctx& c) {
   const size_t limit = (size_t)(SMEM_LIMIT - SMEM_RESERVE);
   // deepest operand rings that fit, with the staged epilogue (faster stores) unless dropping
   // its staging rows buys a deeper ring (large ranks)
-  const int choices[6][2] = {{2, 8}, {2, 6}, {2, 4}, {1, 4}, {1, 2}, {1, 1}};
+  // (at least two window slots: the two producer groups build alternate pairs)
+  const int choices[5][2] = {{2, 8}, {2, 6}, {2, 4}, {1, 4}, {1, 2}};
   int best[2] = {-1, -1};
   for (int staged = 1; staged >= 0; --staged)
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
       if (smem_total(L, choices[i][0], choices[i][1], staged != 0) <= limit) {
         best[staged] = i;
         break;
