@@ -378,7 +378,9 @@ void launch_mv_warp(const T* X, T* Y, int n, int axis, const T* sym, const typen
 template <typename T>
 bool mode_product_warp(int M, const T* X, T* Y, int n, int axis, const T* sym, const typename Cplx<T>::type* tw,
                        int accumulate, cudaStream_t s) {
-  if constexpr (sizeof(T) != 4) return false;
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
   switch (M) {
     case 32: launch_mv_warp<T, 1>(X, Y, n, axis, sym, tw, accumulate, s); return true;
     case 64: launch_mv_warp<T, 2>(X, Y, n, axis, sym, tw, accumulate, s); return true;
@@ -390,6 +392,7 @@ bool mode_product_warp(int M, const T* X, T* Y, int n, int axis, const T* sym, c
       launch_mv_warp<T, 64>(X, Y, n, axis, sym, tw, accumulate, s);
       return true;
     default: return false;
+  }
   }
 }
 
