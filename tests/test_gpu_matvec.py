@@ -109,3 +109,35 @@ def test_matvec_arguments_and_readiness():
         ctx.matvec(X, Y=X)                     # in place is not allowed
     assert float(ctx.matvec(X).abs().max()) == 0.0
     ctx.close()
+
+
+@pytest.mark.parametrize("n", [33, 129, 257, 601])
+def test_matvec_fp32_transform_sizes(n):
+    """The FP32 transform for the circulant sizes 32 P with P = 2, 8, 16, 64 (n = 601 takes the
+    2048-point circulant): A applied to the charges equals the oracle's long-range canonical sum
+    plus the windows, on the whole grid (n = 33) or at the particle sites and 2000 random grid
+    points."""
+    rng = np.random.default_rng(n)
+    b = 4.0 * (n - 1) / 32
+    cfg = dict(b=b, n=n, R=14, R_s=4, h_q=0.7, u0=-6.5, eps=1e-6, rank_cap=0, delta_rel=1e-8,
+               precision="fp32_split", snap=True)
+    N = 24
+    xyz = rng.uniform(-0.9 * b, 0.9 * b, (N, 3))
+    Z = rng.uniform(-1, 1, N)
+    pr = O.Problem(cfg, xyz, Z)
+    ctx = _ctx(cfg, N)
+    C = torch.zeros((n, n, n), dtype=torch.float32, device="cuda")
+    jt = torch.tensor(pr.j, device="cuda", dtype=torch.long)
+    C.index_put_((jt[:, 0], jt[:, 1], jt[:, 2]), torch.tensor(pr.z, device="cuda", dtype=torch.float32),
+                 accumulate=True)
+    Y = ctx.matvec(C)
+    if n <= 33:
+        ref = pr.Pl_grid() + pr.windows_grid()
+        got = Y.double().cpu().numpy()
+    else:
+        idx = np.concatenate([pr.j, rng.integers(0, n, (2000, 3))])
+        it = torch.tensor(idx, device="cuda", dtype=torch.long)
+        got = Y[it[:, 0], it[:, 1], it[:, 2]].double().cpu().numpy()
+        ref = pr.Pl_points(idx) + pr.windows_points(idx)
+    assert np.abs(got - ref).max() <= TOL["fp32_split"] * np.abs(ref).max(), n
+    ctx.close()
