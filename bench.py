@@ -499,6 +499,40 @@ def run_ours(args, rank, world, local_rank):
             plain_methods[name] = entry
         del outp
 
+    # two independent solves of the workload at a time, each context on its own stream (the
+    # eigen stage leaves most SMs idle): the combined rate of the GPU, beside the sequential
+    # per-solve rate of the headline
+    concurrent = None
+    if not args.no_plain:
+        try:
+            streams = [torch.cuda.Stream() for _ in range(2)]
+            cctx, cpots = [], []
+            for st in streams:
+                with torch.cuda.stream(st):
+                    cctx.append(RSContext(ccfg, stream=st))
+                    cpots.append(cctx[-1].new_potential())
+            for _ in range(2):
+                for cx, pt in zip(cctx, cpots):
+                    cx.solve(xyz, Z, potential=pt, energy=True)
+            torch.cuda.synchronize()
+            csteps = max(4, min(args.steps, 20))
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(csteps):
+                cctx[i & 1].solve(xyz, Z, potential=cpots[i & 1], energy=True)
+            torch.cuda.synchronize()
+            tc = time.perf_counter() - t0
+            concurrent = {"solves": csteps, "streams": 2, "ms_per_solve": 1e3 * tc / csteps,
+                          "value": n ** 3 * csteps / tc, "unit": UNIT,
+                          "timing": "host wall clock around the solves (synchronised), no L2 flush between them",
+                          "energies_equal": cctx[0].energy() == cctx[1].energy() == E}
+            for cx in cctx:
+                cx.close()
+            del cpots
+        except Exception as e:  # reported, not fatal to the bench line
+            concurrent = {"error": str(e)}
+
     # the largest workload (lattice, n = 1025, N = 19,757, eps = 1e-5): whole solves timed the
     # same way, with its stage breakdown and the assembly roofline
     large = None
@@ -703,6 +737,7 @@ def run_ours(args, rank, world, local_rank):
         "stages_ms_per_step": stages,
         "plain_gpu": plain,
         "plain_methods": plain_methods,
+        "concurrent": concurrent,
         "large": large,
         "forces": forces,
         "canonical": canonical,
