@@ -63,12 +63,20 @@ bool derive(const rs_config& cfg, Ctx& c, std::string& err) {
   c.t2_ld = cfg.n;
   c.use_tc = plan_assemble(c);
   {
-    // core contraction: tensor cores where the tolerance allows their FP32 accumulation
-    // (eps >= 1e-5), the CUDA-core two-sum contraction below; RS_CORE_PATH=cuda|tc overrides
+    // core contraction on the FP32 path: the Khatri-Rao tensor-core form where its operand
+    // window takes at most a few passes over K; else the tensor-core form with operands built
+    // per tile where the tolerance allows its FP32 accumulation (eps >= 1e-5), and the CUDA-core
+    // two-sum contraction below that.  RS_CORE_PATH=cuda|tc|kr overrides.
     const char* env = std::getenv("RS_CORE_PATH");
-    c.use_tc_core = !c.fp64 && cfg.eps >= 1e-5;
-    if (env && std::strcmp(env, "cuda") == 0) c.use_tc_core = false;
-    if (env && std::strcmp(env, "tc") == 0) c.use_tc_core = !c.fp64;
+    c.kr_bytes = c.fp64 ? 0 : core_kr_plan(c, c.kr_passes, c.kr_wstride);
+    c.use_kr_core = c.kr_bytes > 0;
+    c.use_tc_core = !c.fp64 && (c.use_kr_core || cfg.eps >= 1e-5);
+    if (env && std::strcmp(env, "cuda") == 0) c.use_tc_core = c.use_kr_core = false;
+    if (env && std::strcmp(env, "tc") == 0) {
+      c.use_tc_core = !c.fp64;
+      c.use_kr_core = false;
+    }
+    if (env && std::strcmp(env, "kr") == 0) c.use_tc_core = c.use_kr_core = c.kr_bytes > 0;
   }
   return true;
 }
@@ -116,6 +124,7 @@ std::vector<std::pair<void**, size_t>> buffer_list(Ctx& c) {
   add(v, c.Z32, 4 * 3 * n * rm);
   add(v, c.Qp, ts * 3 * n * Rl * rm);
   if (c.use_tc_core) add(v, c.kmeta, 16 * (size_t)N * Rl);
+  if (c.use_kr_core) add(v, c.kr_buf, c.kr_bytes);
   add(v, c.pe, 8 * (size_t)N);
   add(v, c.ewin, 8 * (size_t)N);
   add(v, c.beta64, 8 * rm * rm * rm);

@@ -14,8 +14,13 @@
 // is coarser than round-to-nearest: measured on the protein workload (n = 513, eps = 1e-6)
 // against the CUDA-core contraction with two-sum chunks, the potentials differ by 4e-7 with
 // 64-term segments, 9e-7 with 256 and 2e-6 with 1024 (energies by 2e-6 .. 3e-5 relative), so
-// this contraction is used where the Tucker tolerance is at least 1e-5 (1025^3 lattice: 2e-7
-// of the oracle), and the CUDA-core contraction below that.
+// segments stay at 64 terms.
+//
+// Two forms.  core_tc_kernel (this header) builds both operands per output tile; the
+// Khatri-Rao form further down (core_w_kernel + core_kr_kernel) forms z q1 q2 once per solve
+// and streams it, and is the default on the FP32 path wherever its operand window covers K in
+// at most KR_MAX_PASSES passes (every workload here); core_tc_kernel remains for larger
+// problems at tolerances of at least 1e-5, the CUDA-core contraction below that.
 //
 // Operand scales: A carries 2^sA with 2^sA max|z| max|q| < 2^14 and B 2^sB with
 // 2^sB max|q|^2 < 2^14 (exact powers of two, removed when the units add to beta).
@@ -25,6 +30,8 @@
 //   warps 1-7   producers: A and B chunks of 64 K terms -> ring of four stages
 //   warps 8-15  epilogue: a segment's accumulator -> (hi, lo) registers; FP64 atomics per unit
 // Every wait is bounded (FLAG_TIMEOUT, abort flag, tensor memory released before return).
+#include <algorithm>
+
 #include "rs_internal.cuh"
 #include "rs_tcgen05.cuh"
 
@@ -342,6 +349,408 @@ __global__ void __launch_bounds__(CT_THREADS, 1) core_tc_kernel(CoreArgs g) {
   }
 }
 
+// ------------------------------------------------------------------ Khatri-Rao form
+// The same contraction with the Khatri-Rao product of the first two modes formed once:
+//   W[(a, b)][K] = z_K q1[K][a] q2[K][b]     (rows rho = a r2 + b, r1 r2 of them)
+//   beta[a][b][c] = sum_K W[(a, b)][K] q3[K][c]
+// a GEMM with M = 128 pairs (a, b), N = 64 values of c and K in chunks of 64 terms.
+// core_w_kernel writes W and q3 as FP16 hi / lo chunks in the canonical K-major layout of the
+// MMA operands (32 KB per 128 pairs and chunk, 16 KB per 64 c and chunk), scaled by 2^sA and 2^sB
+// as above.  core_kr_kernel copies them into a ring of shared-memory stages with bulk copies (one
+// loader warp), accumulates 64-term segments in tensor memory, folds every segment into FP32
+// (hi, lo) pairs and adds each unit's pairs to beta as fixed-point integers.  Against the producers
+// of core_tc_kernel every operand value is built once instead of once per output tile, and all
+// 128 rows of a tile are live (r1 r2 pairs instead of r1 < 128 rows a).
+//
+// The operands of all K would take Mt Kc 48 KB at the largest ranks (Mt tiles of pairs, Kc
+// chunks); a workspace of a fixed size holds a window of chunks, and the K range is covered in
+// `passes` windows (the same number for every launch, fixed on the host from the rank cap and the
+// particle capacity; each window holds ceil(Kc / passes) chunks of the actual ranks).
+
+constexpr uint32_t KR_A = 2 * CT_A_HALF;          // one A block: hi and lo of 128 pairs x 64 K
+constexpr uint32_t KR_B = 2 * CT_B_HALF;          // one B block: hi and lo of 64 c x 64 K
+constexpr int KR_EPI = 8;
+constexpr int KR_THREADS = 32 * (2 + KR_EPI);     // MMA warp, loader warp, 8 epilogue warps
+constexpr int KR_MAX_PASSES = 8;
+
+struct KrGeom {
+  int mt, nt, w;           // tiles of 128 pairs, tiles of 64 c, chunks of a window
+  long long kc, ktot;      // chunks and terms of K
+};
+
+__device__ __forceinline__ KrGeom kr_geom(const DevScalars* sc, int R_l, int passes) {
+  KrGeom G;
+  G.ktot = (long long)sc->n_nz * R_l;
+  G.kc = (G.ktot + CT_KC - 1) / CT_KC;
+  G.mt = (sc->rank[0] * sc->rank[1] + CT_M - 1) / CT_M;
+  G.nt = (sc->rank[2] + CT_N - 1) / CT_N;
+  G.w = (int)((G.kc + passes - 1) / passes);
+  return G;
+}
+
+// A = 2^sA z q1 q2 with 2^sA max|z| max|q|^2 < 2^14, B = 2^sB q3 with 2^sB max|q| < 2^14
+__device__ __forceinline__ void kr_scales(const DevScalars* sc, int& sA, int& sB) {
+  const float qmax = __uint_as_float(sc->qmax_bits), zmax = __uint_as_float(sc->zmax_bits);
+  sA = (qmax > 0.f && zmax > 0.f) ? max(-100, min(100, 14 - exp2_above((double)zmax * qmax * qmax))) : 0;
+  sB = (qmax > 0.f) ? max(-100, min(100, 14 - exp2_above((double)qmax))) : 0;
+}
+
+// Operands of window `pass`: blocks (tile, chunk - first chunk of the window), wstride chunks per
+// tile in the workspace.  A task is a chunk and KR_AB values of a (all b), or a chunk's q3 tiles;
+// one 256-thread block per task, grid-stride.  Warp g builds K group g (8 terms) of the rows
+// (a, b), lane = b - b0: it keeps q2[K][b] of its 8 terms in registers and reads 2^sA z q1[K][a]
+// from shared memory (one broadcast per 8 terms), so a value of W costs one multiply and its
+// FP16 split.  The rows past the last pair of the last tile are written as zeros.
+constexpr int KR_AB = 8;
+
+__global__ void __launch_bounds__(256, 4)
+core_w_kernel(const float* __restrict__ Qp, const int4* __restrict__ meta, const DevScalars* sc, int R_l,
+              int passes, int pass, int wstride, unsigned char* __restrict__ W, unsigned char* __restrict__ B3) {
+  __shared__ int4 sm[CT_KC];
+  __shared__ __align__(16) float zq1[KR_AB][CT_KC];
+  const int r1 = sc->rank[0], r2 = sc->rank[1], r3 = sc->rank[2];
+  const KrGeom G = kr_geom(sc, R_l, passes);
+  const long long c0 = (long long)pass * G.w;
+  const int wl = (int)max(0ll, min((long long)G.w, G.kc - c0));    // chunks of this window
+  const int nab = (r1 + KR_AB - 1) / KR_AB;
+  const long long ntask = (long long)(nab + 1) * wl;
+  if (ntask == 0 || G.mt == 0) return;
+  int sA, sB;
+  kr_scales(sc, sA, sB);
+  const float fA = ldexpf(1.0f, sA), fB = ldexpf(1.0f, sB);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, pairs = r1 * r2;
+  for (long long t = blockIdx.x; t < ntask; t += gridDim.x) {
+    const int ab = (int)(t / wl), cl = (int)(t % wl);
+    const long long K0 = (c0 + cl) * CT_KC;
+    __syncthreads();                                   // the previous task's reads of sm, zq1
+    if (tid < CT_KC) sm[tid] = K0 + tid < G.ktot ? meta[K0 + tid] : make_int4(0, 0, 0, 0);
+    __syncthreads();
+    if (ab < nab) {
+      const int a0 = ab * KR_AB, na = min(KR_AB, r1 - a0);
+      for (int e = tid; e < KR_AB * CT_KC; e += 256) {
+        const int i = e >> 6, kk = e & (CT_KC - 1);
+        const int4 mt = sm[kk];
+        zq1[i][kk] = (i < na && K0 + kk < G.ktot) ? fA * __int_as_float(mt.w) * Qp[mt.x + a0 + i] : 0.f;
+      }
+      __syncthreads();
+      for (int b0 = 0; b0 < r2; b0 += 32) {
+        const int b = b0 + lane;
+        if (b >= r2) continue;
+        float q2v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int kk = 8 * warp + q;
+          q2v[q] = K0 + kk < G.ktot ? Qp[sm[kk].y + b] : 0.f;
+        }
+        for (int i = 0; i < na; ++i) {
+          const float4 z0 = *reinterpret_cast<const float4*>(&zq1[i][8 * warp]);
+          const float4 z1 = *reinterpret_cast<const float4*>(&zq1[i][8 * warp + 4]);
+          float x[8] = {z0.x * q2v[0], z0.y * q2v[1], z0.z * q2v[2], z0.w * q2v[3],
+                        z1.x * q2v[4], z1.y * q2v[5], z1.z * q2v[6], z1.w * q2v[7]};
+          uint4 hi, lo;
+          split8_f16(x, hi, lo);
+          const int rho = (a0 + i) * r2 + b;
+          unsigned char* blk = W + ((unsigned long long)(rho >> 7) * wstride + cl) * KR_A;
+          const uint32_t off = kmajor_offset(rho & (CT_M - 1), warp, CT_KC / 8);
+          *(uint4*)(blk + off) = hi;
+          *(uint4*)(blk + CT_A_HALF + off) = lo;
+        }
+      }
+    } else {
+      for (int nl = 0; nl < G.nt; ++nl) {
+        unsigned char* blk = B3 + ((unsigned long long)nl * wstride + cl) * KR_B;
+        for (int task = tid; task < CT_N * 8; task += 256) {
+          const int row = task & (CT_N - 1), kg = task >> 6;
+          const int cc = nl * CT_N + row;
+          float x[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int kk = 8 * kg + q;
+            x[q] = (cc < r3 && K0 + kk < G.ktot) ? fB * Qp[sm[kk].z + cc] : 0.f;
+          }
+          uint4 hi, lo;
+          split8_f16(x, hi, lo);
+          const uint32_t off = kmajor_offset(row, kg, CT_KC / 8);
+          *(uint4*)(blk + off) = hi;
+          *(uint4*)(blk + CT_B_HALF + off) = lo;
+        }
+      }
+      const int first = pairs - (G.mt - 1) * CT_M;    // live rows of the last pair tile
+      unsigned char* blk = W + ((unsigned long long)(G.mt - 1) * wstride + cl) * KR_A;
+      for (int e = tid; e < (CT_M - first) * 8; e += 256) {
+        const uint32_t off = kmajor_offset(first + (e >> 3), e & 7, CT_KC / 8);
+        *(uint4*)(blk + off) = make_uint4(0u, 0u, 0u, 0u);
+        *(uint4*)(blk + CT_A_HALF + off) = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+  }
+}
+
+// x 2^e as a 64-bit integer, rounded to nearest (halves away from zero), from the bits of x
+// with integer operations only; |x| 2^e < 2^63 (the fixed-point scale guarantees it)
+__device__ __forceinline__ long long fx_f32(float x, int e) {
+  const uint32_t u = __float_as_uint(x);
+  const int ex = (int)((u >> 23) & 0xFFu);
+  long long m = (long long)(u & 0x7FFFFFu);
+  int s = e - 149;                                     // subnormal: x = m 2^-149
+  if (ex != 0) {
+    m |= 0x800000ll;
+    s = ex - 150 + e;
+  }
+  long long r = 0;
+  if (s >= 0)
+    r = m << min(s, 39);
+  else if (s > -26)
+    r = (m + (1ll << (-s - 1))) >> (-s);
+  return (u >> 31) ? -r : r;
+}
+
+struct KrArgs {
+  const unsigned char* W;
+  const unsigned char* B3;
+  DevScalars* sc;
+  double* beta64;
+  int rmax, R_l, passes, pass, wstride;
+};
+
+__global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_full[CT_STAGES], bar_empty[CT_STAGES];
+  __shared__ __align__(8) uint64_t bar_dfull[2], bar_dempty[2], bar_drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_s;
+  volatile int* abort_flag = &abort_s;
+
+  DevScalars* sc = g.sc;
+  const KrGeom G = kr_geom(sc, g.R_l, g.passes);
+  const long long c0 = (long long)g.pass * G.w;
+  const int wl = (int)max(0ll, min((long long)G.w, G.kc - c0));
+  const int tiles = G.mt * G.nt;
+  // the (tile, chunk) pairs of the window, tile-major, split evenly over the CTAs; a CTA's range
+  // falls into work units (one tile, consecutive chunks), each flushed to beta at its end
+  const long long total = (long long)tiles * wl;
+  const long long lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
+  if (lo >= hi) return;                                // whole CTA, before any set-up
+  auto next_unit = [&](long long pos, int& m, int& nl, int& cb, int& ce) -> long long {
+    const int t = (int)(pos / wl);
+    const long long end = min(hi, (long long)(t + 1) * wl);
+    m = t / G.nt;
+    nl = t - m * G.nt;
+    cb = (int)(pos - (long long)t * wl);
+    ce = cb + (int)(end - pos);
+    return end;
+  };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r1 = sc->rank[0], r2 = sc->rank[1], r3 = sc->rank[2];
+  int sA, sB;
+  kr_scales(sc, sA, sB);
+
+  if (tid == 0) {
+    for (int s = 0; s < CT_STAGES; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_dfull[b], 1);
+      mbar_init(&bar_dempty[b], KR_EPI);
+    }
+    mbar_init(&bar_drain, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(CT_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint64_t dA = smem_desc(smem_addr(smem), 128, (CT_KC / 8) * 128);
+      const uint64_t dB = smem_desc(smem_addr(smem + KR_A), 128, (CT_KC / 8) * 128);
+      const uint64_t st_step = (uint64_t)CT_STAGE >> 4;
+      const uint64_t a_lo = (uint64_t)CT_A_HALF >> 4, b_lo = (uint64_t)CT_B_HALF >> 4;
+      const uint32_t idesc = idesc_f16(CT_N, CT_M);
+      long long gc = 0, gseg = 0;
+      bool ok = true;
+      for (long long pos = lo; ok && pos < hi;) {
+        int m, nl, cb, ce;
+        pos = next_unit(pos, m, nl, cb, ce);
+        for (int cl = cb; cl < ce; ++cl) {
+          const int buf = (int)(gseg & 1);
+          if (gseg >= 2 && !wait_bar(&bar_dempty[buf], (uint32_t)((gseg - 2) >> 1) & 1u, abort_flag, sc)) {
+            ok = false;
+            break;
+          }
+          const int st = (int)(gc % CT_STAGES);
+          if (!wait_bar(&bar_full[st], (uint32_t)(gc / CT_STAGES) & 1u, abort_flag, sc)) {
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint32_t d = tmem + (uint32_t)(buf * CT_N);
+          const uint64_t ah = dA + (uint64_t)st * st_step, al = ah + a_lo;
+          const uint64_t bh = dB + (uint64_t)st * st_step, bl = bh + b_lo;
+#pragma unroll
+          for (int s4 = 0; s4 < CT_KC / 16; ++s4) {
+            const uint64_t ko = (uint64_t)s4 * 16u;        // 16 FP16 = 32 bytes per row = 2 chunks
+            mma_f16(d, ah + ko, bh + ko, idesc, s4 == 0 ? 0u : 1u);
+            mma_f16(d, ah + ko, bl + ko, idesc, 1u);
+            mma_f16(d, al + ko, bh + ko, idesc, 1u);
+          }
+          mma_commit(&bar_empty[st]);
+          mma_commit(&bar_dfull[buf]);
+          ++gc;
+          ++gseg;
+        }
+      }
+      // every MMA of this thread has completed before the tensor memory is released
+      mma_commit(&bar_drain);
+      drain_bar(&bar_drain, 0, sc);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ loader: bulk copies
+    if (lane == 0) {
+      long long gc = 0;
+      bool ok = true;
+      for (long long pos = lo; ok && pos < hi;) {
+        int m, nl, cb, ce;
+        pos = next_unit(pos, m, nl, cb, ce);
+        for (int cl = cb; cl < ce; ++cl) {
+          const int st = (int)(gc % CT_STAGES);
+          if (gc >= CT_STAGES && !wait_bar(&bar_empty[st], (uint32_t)(gc / CT_STAGES - 1) & 1u, abort_flag, sc)) {
+            ok = false;
+            break;
+          }
+          unsigned char* base = smem + (size_t)st * CT_STAGE;
+          mbar_expect_tx(&bar_full[st], KR_A + KR_B);
+          bulk_load(base, g.W + ((unsigned long long)m * g.wstride + cl) * KR_A, KR_A, &bar_full[st]);
+          bulk_load(base + KR_A, g.B3 + ((unsigned long long)nl * g.wstride + cl) * KR_B, KR_B, &bar_full[st]);
+          ++gc;
+        }
+      }
+      // the copies issued last have landed before the shared memory goes away
+      for (long long t = gc > CT_STAGES ? gc - CT_STAGES : 0; t < gc; ++t)
+        drain_bar(&bar_full[t % CT_STAGES], (uint32_t)(t / CT_STAGES) & 1u, sc);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - 2;                         // 0 .. 7
+    const int q = warp & 3;                          // tensor-memory lanes 32q .. 32q + 31
+    const int half = ew >> 2;                        // columns 32 half .. 32 half + 31
+    const int fx_e = beta_fx_shift(sc, g.R_l) - sA - sB;   // fixed-point exponent of the sums
+    long long gseg = 0;
+    bool ok = true;
+    for (long long pos = lo; ok && pos < hi;) {
+      int m, nl, cb, ce;
+      pos = next_unit(pos, m, nl, cb, ce);
+      float hi[32], lo[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        hi[j] = 0.f;
+        lo[j] = 0.f;
+      }
+      for (int cl = cb; cl < ce; ++cl) {
+        const int buf = (int)(gseg & 1);
+        if (!warp_wait(&bar_dfull[buf], (uint32_t)(gseg >> 1) & 1u, abort_flag, sc)) {
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * CT_N + 32 * half);
+        uint32_t v[32];
+#pragma unroll
+        for (int u8 = 0; u8 < 4; ++u8) tmem_ld8(ta + (uint32_t)(8 * u8), v + 8 * u8);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) two_sum_acc(hi[j], lo[j], __uint_as_float(v[j]));
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_dempty[buf]);
+        ++gseg;
+      }
+      if (!ok) break;
+      const int rho = m * CT_M + 32 * q + lane;
+      const int cbase = nl * CT_N + 32 * half;
+      if (rho < r1 * r2) {
+        const int a = rho / r2, b = rho - a * r2;
+        unsigned long long* out = reinterpret_cast<unsigned long long*>(g.beta64) +
+                                  ((long long)a * g.rmax + b) * g.rmax + cbase;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (cbase + j < r3) atomicAdd(out + j, (unsigned long long)(fx_f32(hi[j], fx_e) + fx_f32(lo[j], fx_e)));
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CT_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+
+// Workspace of the Khatri-Rao contraction for the context's rank cap and particle capacity:
+// windows of at most `wstride` chunks, `passes` of them; 0 when it would take more than
+// KR_MAX_PASSES windows (the contraction is then left to the other two forms).
+size_t core_kr_plan(const Ctx& c, int& passes, int& wstride) {
+  const long long mt = ((long long)c.rmax * c.rmax + CT_M - 1) / CT_M;
+  const long long nt = (c.rmax + CT_N - 1) / CT_N;
+  const long long kc = ((long long)c.maxN * c.R_l + CT_KC - 1) / CT_KC;
+  const size_t per_chunk = (size_t)mt * KR_A + (size_t)nt * KR_B;
+  const size_t grid_bytes = (size_t)4 * c.n * c.n * c.n;
+  const size_t budget = std::max<size_t>((size_t)256 << 20, 2 * grid_bytes);
+  long long p = (long long)(((size_t)kc * per_chunk + budget - 1) / budget);
+  if (p < 1) p = 1;
+  passes = (int)std::min<long long>(p, KR_MAX_PASSES + 1);
+  wstride = (int)((kc + p - 1) / p);
+  if (p > KR_MAX_PASSES || kc == 0) return 0;
+  return per_chunk * (size_t)wstride;
+}
+
+int launch_core_kr(Ctx& c) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  const long long Kmax = (long long)c.maxN * c.R_l;
+  const int mblocks = (int)((Kmax + 255) / 256);
+  core_meta_kernel<<<mblocks > 0 ? mblocks : 1, 256, 0, c.stream>>>(c.j, c.nz_idx, c.Z, c.n, c.rmax, c.R_l, c.sc,
+                                                                     (int4*)c.kmeta);
+  const long long mt_max = ((long long)c.rmax * c.rmax + CT_M - 1) / CT_M;
+  unsigned char* W = (unsigned char*)c.kr_buf;
+  unsigned char* B3 = W + (size_t)mt_max * c.kr_wstride * KR_A;
+  KrArgs g;
+  g.W = W;
+  g.B3 = B3;
+  g.sc = c.sc;
+  g.beta64 = c.beta64;
+  g.rmax = c.rmax;
+  g.R_l = c.R_l;
+  g.passes = c.kr_passes;
+  g.wstride = c.kr_wstride;
+  for (int p = 0; p < c.kr_passes; ++p) {
+    core_w_kernel<<<4 * sms, 256, 0, c.stream>>>((const float*)c.Qp, (const int4*)c.kmeta, c.sc, c.R_l,
+                                                 c.kr_passes, p, c.kr_wstride, W, B3);
+    g.pass = p;
+    core_kr_kernel<<<sms, KR_THREADS, CT_SMEM, c.stream>>>(g);
+  }
+  return 1 + 2 * c.kr_passes;
+}
+
 int launch_core_tc(Ctx& c) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -363,7 +772,11 @@ int launch_core_tc(Ctx& c) {
 
 cudaError_t set_attributes_core(int optin) {
   (void)optin;
-  return cudaFuncSetAttribute((const void*)core_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT_SMEM);
+  cudaError_t e = cudaFuncSetAttribute((const void*)core_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)CT_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)core_kr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT_SMEM);
+  return e;
 }
 
 }  // namespace rs

@@ -181,7 +181,11 @@ struct Ctx {
   size_t tc_smem = 0;           // dynamic shared memory of the assembly kernel
   bool tc_staged = false;       // assembly epilogue through shared staging rows
   bool use_tc_core = false;     // tensor-core core contraction (FP32 bulk path)
+  bool use_kr_core = false;     // ... in the Khatri-Rao form (operands formed once, bulk copies)
   void*   kmeta = nullptr;      // per K term of the core: Qp row offsets and charge (int4)
+  void*   kr_buf = nullptr;     // Khatri-Rao operand window (FP16 hi / lo blocks)
+  size_t  kr_bytes = 0;
+  int     kr_passes = 0, kr_wstride = 0;
   double* pe = nullptr;         // per-particle pair energies (off-grid energy and forces)
   double* ewin = nullptr;       // window part of each charged particle's value (energy)
   long long wl_cap = 0;         // capacity of the window lists (entries)
@@ -337,6 +341,8 @@ cudaError_t set_attributes_tucker(int optin);
 cudaError_t set_attributes_tc(int optin);
 cudaError_t set_attributes_core(int optin);
 int launch_core_tc(Ctx& c);
+int launch_core_kr(Ctx& c);
+size_t core_kr_plan(const Ctx& c, int& passes, int& wstride);
 int launch_energy_t2(Ctx& c, double* part, int blocks);
 int launch_energy_windows(Ctx& c);
 int launch_canonical(Ctx& c, double eps, int r1, int r2, int r3, int P);

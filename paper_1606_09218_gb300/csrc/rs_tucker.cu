@@ -301,7 +301,9 @@ static int projection_core_t(Ctx& c) {
   if (ksplit < kmin_split) ksplit = kmin_split;
   dim3 g2(ntile, ksplit);
   int kcore = 1;
-  if (sizeof(T) == 4 && c.use_tc_core)
+  if (sizeof(T) == 4 && c.use_kr_core)
+    kcore = launch_core_kr(c);                       // tcgen05, Khatri-Rao operands formed once
+  else if (sizeof(T) == 4 && c.use_tc_core)
     kcore = launch_core_tc(c);                       // tcgen05, FP16-split operands
   else
     core_kernel<T><<<g2, 256, core_smem_bytes<T>(), c.stream>>>(Qp, c.j, c.nz_idx, c.Z, n, rmax, c.R_l, c.sc,

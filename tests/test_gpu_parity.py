@@ -319,12 +319,14 @@ def test_tensor_core_reconstruction_matches_cuda_core_path(name, monkeypatch):
     ctx.close()
 
 
-def test_tensor_core_core_matches_cuda_core_path(monkeypatch):
-    """The tcgen05 core contraction (FP16-split operands, 64-term FP32 segments folded into
-    two-sums, FP64 across units; chosen by default for eps >= 1e-5) forced on config 2 against
-    the CUDA-core FP32 contraction with two-sum chunks (the default at eps = 1e-6): the same
-    Tucker ranks, and potentials within 1e-6 (the tensor cores' FP32 accumulation costs about
-    4e-7 here)."""
+@pytest.mark.parametrize("path", ["kr", "tc"])
+def test_tensor_core_core_matches_cuda_core_path(monkeypatch, path):
+    """The two tcgen05 forms of the core contraction (FP16-split operands, 64-term FP32 segments
+    folded into two-sums, fixed-point sums across work units) forced on config 2 against the
+    CUDA-core FP32 contraction with two-sum chunks: the same Tucker ranks, and potentials within
+    1e-6 (the tensor cores' FP32 accumulation costs about 4e-7 here).  "kr" forms the Khatri-Rao
+    operand z q1 q2 once per solve and streams it (the default on the FP32 path); "tc" builds
+    both operands per output tile."""
     cfg = load_config("c2_protein1000_n513")
     p = make_particles(cfg)
     xyz = torch.tensor(p.xyz, device="cuda")
@@ -336,17 +338,54 @@ def test_tensor_core_core_matches_cuda_core_path(monkeypatch):
     Eref = cref.energy()
     rref = cref.report()
     cref.close()
-    monkeypatch.setenv("RS_CORE_PATH", "tc")
+    monkeypatch.setenv("RS_CORE_PATH", path)
     ctx = _ctx(cfg, len(p.Z))
     ctx.solve(xyz, Z, energy=True)
     rep = ctx.report()
     assert rep["status"] == 0 and rep["ranks"] == rref["ranks"]
-    assert rep["kernel_launches"] == rref["kernel_launches"] + 1       # + the K-term table
+    if path == "tc":
+        assert rep["kernel_launches"] == rref["kernel_launches"] + 1       # + the K-term table
+    else:
+        # + the K-term table, and per window of K an operand kernel and an MMA kernel
+        extra = rep["kernel_launches"] - rref["kernel_launches"]
+        assert extra >= 2 and extra % 2 == 0, extra
     d = float((ctx.potential.double() - ref.double()).norm() / ref.double().norm())
     assert d < 1e-6, d
     pr = O.Problem(cfg, p.xyz, p.Z)
     scale = O.energy_scale(pr.xyz_snapped, pr.z)
     assert abs(ctx.energy() - Eref) <= 3e-7 * scale
+    ctx.close()
+
+
+def test_khatri_rao_core_over_windows_and_c_tiles(monkeypatch):
+    """The forces workload (N = 4096, r = 66, snapped): its Khatri-Rao operands take several
+    windows of K and two tiles of 64 values of c.  Against the CUDA-core contraction: the same
+    ranks, potentials within 1e-6, the energy within 3e-7 of its scale, and a repeated solve
+    bit-identical (fixed-point sums)."""
+    cfg = dict(load_config("c5_forces4096_n513"), snap=True)
+    p = make_particles(cfg)
+    xyz = torch.tensor(p.xyz, device="cuda")
+    Z = torch.tensor(p.Z, device="cuda")
+    monkeypatch.setenv("RS_CORE_PATH", "cuda")
+    cref = _ctx(cfg, len(p.Z))
+    cref.solve(xyz, Z, energy=True)
+    ref = cref.potential.clone()
+    Eref = cref.energy()
+    rref = cref.report()
+    cref.close()
+    monkeypatch.setenv("RS_CORE_PATH", "kr")
+    ctx = _ctx(cfg, len(p.Z))
+    ctx.solve(xyz, Z, energy=True)
+    rep = ctx.report()
+    assert rep["status"] == 0 and rep["ranks"] == rref["ranks"] and max(rep["ranks"]) > 64
+    assert rep["kernel_launches"] - rref["kernel_launches"] >= 4          # two windows at least
+    P1 = ctx.potential.clone()
+    d = float((P1.double() - ref.double()).norm() / ref.double().norm())
+    assert d < 1e-6, d
+    pr = O.Problem(cfg, p.xyz, p.Z)
+    assert abs(ctx.energy() - Eref) <= 3e-7 * O.energy_scale(pr.xyz_snapped, pr.z)
+    ctx.solve(xyz, Z, energy=True)
+    assert torch.equal(ctx.potential, P1)
     ctx.close()
 
 
