@@ -840,6 +840,219 @@ jacobi32_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* s
   }
 }
 
+// The same Jacobi pass with one barrier per round (subspaces up to JF_KMAX).  A is kept in slot
+// order: with the round-robin schedule, pair m of every round is slots (m, ke-1-m), and between
+// rounds the indices move one slot down (slot 1 wraps to ke-1, slot 0 stays), so round r reads
+// A_r in its slot order and writes A_{r+1} = J_r^T A_r J_r straight into the next round's slot
+// order (the other copy).  Thread (warp w, lane i) owns the 2 x 2 blocks of pairs (w + 32 u,
+// i + 32 v): the slots of a block never change, so its addresses and whether one of its entries
+// becomes the off-diagonal of a pair of the next round are fixed; that entry gives the pair's
+// rotation at once (its diagonal is the rotated diagonal of round r), so rotations, A and V
+// never wait for one another within a round.  V stays in the original index order: the two
+// indices of a pair in round r are closed-form and each thread follows its own pairs.
+constexpr int JF_KMAX = 128;
+constexpr int JF_THREADS = 1024;
+
+__device__ __forceinline__ float jf_rot(float a, float b, float c, float s, int i) {
+  return i ? __fmaf_rn(s, a, __fmul_rn(c, b)) : __fmaf_rn(c, a, -__fmul_rn(s, b));
+}
+
+struct JfShared {
+  float2 rot[2][JF_KMAX / 2];                  // (c, s) of pair m
+  float dsl[2][JF_KMAX];                       // diagonal of each slot after the round's rotation
+  int s_cnt[32];                               // rotations of each sweep (nonzero flag)
+};
+
+// rotation of pair m (slots m, ke-1-m) for the round in buffer b and sweep sw
+__device__ __forceinline__ void jf_set_rotation(JfShared& S, int ke, float tol, int b, int sw, int m, float apq,
+                                                float app, float aqq) {
+  float c = 1.f, s = 0.f, t = 0.f;
+  if (apq != 0.f && apq * apq > tol * tol * fabsf(app * aqq)) {
+    const float theta = __fdividef(aqq - app, 2.f * apq);
+    const float w = fmaf(theta, theta, 1.f);
+    t = copysignf(__fdividef(1.f, fabsf(theta) + w * rsqrtf(w)), theta);
+    c = rsqrtf(fmaf(t, t, 1.f));
+    s = t * c;
+    S.s_cnt[sw] = 1;
+  }
+  S.rot[b][m] = make_float2(c, s);
+  S.dsl[b][m] = app - t * apq;                 // graded-accurate diagonal of the rotated pair
+  S.dsl[b][ke - 1 - m] = aqq + t * apq;
+}
+
+__device__ __forceinline__ int jf_snext(int k, int ke) { return k == 0 ? 0 : (k == 1 ? ke - 1 : k - 1); }
+
+// the rounds of the pass; B x B blocks and B V pairs per thread (ke <= 64 B)
+template <int B>
+__device__ void jf_rounds(float* A0, float* A1, float* V, int ke, int ld, int sweeps, float tol, JfShared& S,
+                          DevScalars* sc) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half = ke / 2, rounds = ke - 1;
+  // fixed per block: read offsets (slots s/t of pair m1) x (slots s/t of pair m2), write offsets
+  // in the next slot order, and the entry on the next round's anti-diagonal (-1: none; only in
+  // blocks m1 < m2, which hold at most one)
+  int rd[B * B][4], wr[B * B][4], anti[B * B], tgt[B * B], dp[B * B], dq[B * B];
+#pragma unroll
+  for (int u = 0; u < B * B; ++u) {
+    const int m1 = warp + 32 * (u / B), m2 = lane + 32 * (u % B);
+    const int sl[2] = {m1, ke - 1 - m1}, cl[2] = {m2, ke - 1 - m2};
+    anti[u] = -1;
+    tgt[u] = dp[u] = dq[u] = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = sl[e >> 1], c = cl[e & 1];
+      const int rn = jf_snext(r, ke), cn = jf_snext(c, ke);
+      rd[u][e] = r * ld + c;
+      wr[u][e] = rn * ld + cn;
+      if (m1 < m2 && m2 < half && rn + cn == ke - 1) {
+        anti[u] = e;
+        tgt[u] = min(rn, cn);
+        dp[u] = rn < cn ? r : c;                 // slot (round r) of the pair's first index
+        dq[u] = rn < cn ? c : r;
+      }
+    }
+  }
+  int pa[B], pb[B];
+#pragma unroll
+  for (int u = 0; u < B; ++u) {
+    pa[u] = warp + 32 * u;
+    pb[u] = ke - 1 - (warp + 32 * u);
+  }
+  int sw = 0, j = 0;                             // sweep and round within it
+  for (int R = 0; sw < sweeps; ++R) {
+    const int b = R & 1;
+    const float* A = b ? A1 : A0;
+    float* An = b ? A0 : A1;
+    const int swn = (j + 1 == rounds) ? sw + 1 : sw;
+    const bool more = swn < sweeps;
+#pragma unroll
+    for (int u = 0; u < B * B; ++u) {
+      const int m1 = warp + 32 * (u / B), m2 = lane + 32 * (u % B);
+      if (m1 < half && m2 < half) {
+        if (m1 == m2) {
+          const int s1 = m1, t1 = ke - 1 - m1;
+          const float d0 = S.dsl[b][s1], d1 = S.dsl[b][t1];
+          An[wr[u][0]] = d0;
+          An[wr[u][1]] = 0.f;
+          An[wr[u][2]] = 0.f;
+          An[wr[u][3]] = d1;
+          if (more && ke == 2) jf_set_rotation(S, ke, tol, b ^ 1, swn, 0, 0.f, d0, d1);   // the same pair
+        } else {
+          const float2 r1 = S.rot[b][m1], r2 = S.rot[b][m2];
+          const float x00 = A[rd[u][0]], x01 = A[rd[u][1]], x10 = A[rd[u][2]], x11 = A[rd[u][3]];
+          const float u0 = jf_rot(x00, x10, r1.x, r1.y, 0), u1 = jf_rot(x01, x11, r1.x, r1.y, 0);
+          const float w0 = jf_rot(x00, x10, r1.x, r1.y, 1), w1 = jf_rot(x01, x11, r1.x, r1.y, 1);
+          const float y00 = jf_rot(u0, u1, r2.x, r2.y, 0), y01 = jf_rot(u0, u1, r2.x, r2.y, 1);
+          const float y10 = jf_rot(w0, w1, r2.x, r2.y, 0), y11 = jf_rot(w0, w1, r2.x, r2.y, 1);
+          An[wr[u][0]] = y00;
+          An[wr[u][1]] = y01;
+          An[wr[u][2]] = y10;
+          An[wr[u][3]] = y11;
+          const int e = anti[u];
+          if (more && e >= 0) {
+            const float y = e == 0 ? y00 : (e == 1 ? y01 : (e == 2 ? y10 : y11));
+            jf_set_rotation(S, ke, tol, b ^ 1, swn, tgt[u], y, S.dsl[b][dp[u]], S.dsl[b][dq[u]]);
+          }
+        }
+      }
+    }
+    // V <- V J_r: columns (index at slot m, index at slot ke-1-m) of each pair
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int m = warp + 32 * u;
+      if (m < half) {
+        const float2 r = S.rot[b][m];
+        if (r.y != 0.f) {
+          const int p = pa[u], q = pb[u];
+#pragma unroll
+          for (int k = 0; k < 2 * B; ++k) {
+            const int row = lane + 32 * k;
+            if (row < ke) {
+              float* Vr = V + row * ld;
+              const float vp = Vr[p], vq = Vr[q];
+              Vr[p] = r.x * vp - r.y * vq;
+              Vr[q] = r.y * vp + r.x * vq;
+            }
+          }
+        }
+        if (m != 0) pa[u] = (pa[u] == ke - 1) ? 1 : pa[u] + 1;
+        pb[u] = (pb[u] == ke - 1) ? 1 : pb[u] + 1;
+      }
+    }
+    __syncthreads();
+    if (++j == rounds) {                         // end of a sweep
+      if (tid == 0) atomicAdd(&sc->jacobi_sweeps, 1);
+      if (S.s_cnt[sw] == 0) break;               // no rotation in this sweep
+      j = 0;
+      ++sw;
+      // the next sweep rotates nothing unless a pair of the present A meets the rotation test
+      // (nothing changes before that pair's round): test all pairs at once
+      if (sw < sweeps) {
+        int any = 0;
+        for (int e = tid; e < ke * ke; e += blockDim.x) {
+          const int r = e / ke, c = e - (e / ke) * ke;
+          if (r < c) {
+            const float apq = An[r * ld + c];
+            if (apq != 0.f && apq * apq > tol * tol * fabsf(An[r * ld + r] * An[c * ld + c])) any = 1;
+          }
+        }
+        if (__syncthreads_or(any) == 0) break;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(JF_THREADS)
+jacobi32f_kernel(const double* __restrict__ Tm, double* Wm, int ks, DevScalars* sc, int max_sweeps,
+                 float tol) {
+  extern __shared__ float smem[];
+  __shared__ JfShared S;
+  __shared__ double s_scale;
+  const int l = blockIdx.x;
+  const int ke0 = sc->k_eff[l];
+  const int ke = (ke0 + 1) & ~1;               // even size (padding row/column is zero)
+  const int ld = ke + 1;
+  float* const A0 = smem;                      // A_r and A_{r+1} in slot order, alternating
+  float* const A1 = smem + ke * ld;
+  float* const V = smem + 2 * ke * ld;         // original index order
+  const double* T = Tm + (long long)l * ks * ks;
+  double* W = Wm + (long long)l * ks * ks;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid < 32) {                              // largest diagonal entry (one warp)
+    double m = 0.0;
+    for (int i = tid; i < ke0; i += 32) m = fmax(m, fabs(T[(long long)i * ks + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (tid == 0) s_scale = (m > 0.0) ? 1.0 / m : 1.0;
+    S.s_cnt[tid] = 0;
+  }
+  __syncthreads();
+  const double scl = s_scale;
+  for (int e = tid; e < ke * ke; e += nt) {
+    const int i = e / ke, jc = e % ke;
+    const double v = (i < ke0 && jc < ke0) ? T[(long long)i * ks + jc] * scl : 0.0;
+    A0[i * ld + jc] = (float)v;                // round 0: slot k holds index k
+    V[i * ld + jc] = (i == jc) ? 1.f : 0.f;
+  }
+  const int half = ke / 2;
+  const int sweeps = min(max_sweeps, 31);
+  __syncthreads();
+  if (ke > 1 && sweeps > 0) {
+    for (int m = tid; m < half; m += nt)
+      jf_set_rotation(S, ke, tol, 0, 0, m, A0[m * ld + (ke - 1 - m)], A0[m * ld + m],
+                      A0[(ke - 1 - m) * ld + (ke - 1 - m)]);
+    __syncthreads();
+    if (ke <= 64)
+      jf_rounds<1>(A0, A1, V, ke, ld, sweeps, tol, S, sc);
+    else
+      jf_rounds<2>(A0, A1, V, ke, ld, sweeps, tol, S, sc);
+  }
+  // W (ks x ks, FP64): eigenvectors in the leading ke0 x ke0 block, zero elsewhere
+  for (long long e = tid; e < (long long)ks * ks; e += nt) {
+    const int i = (int)(e / ks), jc = (int)(e % ks);
+    W[e] = (i < ke0 && jc < ke0) ? (double)V[i * ld + jc] : 0.0;
+  }
+}
+
 // M = I - E/2 + 3/8 E^2 (Newton-Schulz step for (Q^T Q)^{-1/2}) from E = Q^T Q - I and
 // E2 = E^2 on the leading ke block; zero elsewhere.  In place on E is allowed.
 __global__ void ns_matrix_kernel(const double* E, const double* E2, double* M, int ks,
@@ -975,9 +1188,14 @@ static int refine(Ctx& c, double*& Qa, double*& Qb) {
   const int n = c.n, ks = c.ksub;
   const long long sQ = (long long)n * ks, sK = (long long)ks * ks;
   const int* ke = c.sc->k_eff;
-  size_t shm = 2ull * ks * (ks + 1) * sizeof(float);
   // one pass: T -> W^T T W (the FP32 rotations accumulated in W)
-  jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, JACOBI_SWEEPS, JACOBI_TOL);
+  if (ks <= JF_KMAX) {
+    const size_t shm = 3ull * ks * (ks + 1) * sizeof(float);
+    jacobi32f_kernel<<<3, JF_THREADS, shm, c.stream>>>(c.T, c.W, ks, c.sc, JACOBI_SWEEPS, JACOBI_TOL);
+  } else {
+    const size_t shm = 2ull * ks * (ks + 1) * sizeof(float);
+    jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, JACOBI_SWEEPS, JACOBI_TOL);
+  }
   // W2 = E = W^T W - I ; T2k = E^2 ; W2 = M
   gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W, ks, sK, 0.0,
                        c.W2, ks, sK, 3, ke, ke, ke, &c.gscr);
@@ -1034,6 +1252,7 @@ int launch_subspace(Ctx& c) {
 
 cudaError_t set_attributes_eigen(int optin) {
   cudaError_t e = allow_max_dynamic_smem((const void*)jacobi32_kernel, optin);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)jacobi32f_kernel, optin);
   if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)bcgs2_kernel, optin);
   return e;
 }
