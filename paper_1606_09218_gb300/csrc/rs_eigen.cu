@@ -206,6 +206,170 @@ template void gemm_batched<float>(cudaStream_t, bool, bool, int, int, int, float
                                   int, long long, int, const int*, const int*, const int*,
                                   const GemmScratch*);
 
+// FP64 products in double-float arithmetic on the FP32 units (the FP32-bulk path's eigen stage):
+// operands split on load as x = hi + lo (FP32 pair), each term hi_a hi_b taken exactly as its
+// rounded product plus the FMA residual, the products summed with an error-free two-sum into
+// (s, s_lo) and the residuals with the cross terms hi_a lo_b + lo_a hi_b in an FP32 correction;
+// about 2^-44 relative to the sum of |terms|, against 2^-49 for FP64 sums of these lengths, and
+// the same order as the double-float Gram matrices they multiply.  Same tiles, K split and
+// deterministic partial sums as gemm_small_kernel: 16 x 16 outputs per CTA; K in chunks of 64,
+// four groups of 64 threads (2 x 2 outputs each) take 16 terms of a chunk and their sums are
+// added in FP64 at the end.
+
+// x = hi + lo from the bits of x with integer operations (this GPU's FP64 pipe, conversions
+// included, is a small fraction of its FP32 rate): hi keeps the sign, the exponent and the top
+// 23 stored mantissa bits (truncated), lo the remaining 29 bits rounded to FP32 (x - hi exactly,
+// then one rounding: |x - hi - lo| <= 2^-48 |x|).  Values below 2^-126 in magnitude become 0.
+__device__ __forceinline__ float2 df_split(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF) - 1023;
+  if (e < -126 || e > 127) return make_float2(0.f, 0.f);   // zero, FP32 underflow or overflow
+  const unsigned sign = (unsigned)(u >> 63) << 31;
+  const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((u >> 29) & 0x7FFFFFull));
+  const float r = __uint2float_rn((unsigned)(u & 0x1FFFFFFFull));   // x - hi = +-r 2^(e - 52)
+  const float m = (e >= -74) ? __fmul_rn(r, __uint_as_float((unsigned)(e + 75) << 23)) : ldexpf(r, e - 52);
+  return make_float2(hi, sign ? -m : m);
+}
+
+constexpr int DF_KC = 64;                      // K terms of one chunk (4 groups x 16)
+
+__global__ void __launch_bounds__(256)
+gemm_df_kernel(bool tA, bool tB, int M, int N, int K, double alpha, const double* __restrict__ A, int lda,
+               long long sA, const double* __restrict__ B, int ldb, long long sB, double* C, int ldc,
+               long long sC, int splitK, const int* dynM, const int* dynN, const int* dynK, double* part,
+               unsigned* count) {
+  constexpr int BT = 16;
+  __shared__ __align__(16) float2 As[DF_KC][BT], Bs[DF_KC][BT];   // (hi, lo) of A[m][k] at [k][m], B[k][n] at [k][n]
+  __shared__ double red[3][BT * BT];
+  __shared__ unsigned s_last;
+  const int bz = blockIdx.z / splitK, kz = blockIdx.z % splitK;
+  int m = M, nn = N, kk = K;
+  if (dynM) m = min(m, dynM[bz]);
+  if (dynN) nn = min(nn, dynN[bz]);
+  if (dynK) kk = min(kk, dynK[bz]);
+  const int row0 = blockIdx.y * BT, col0 = blockIdx.x * BT;
+  const int tid = threadIdx.x, grp = tid >> 6, t6 = tid & 63, tx = t6 & 7, ty = t6 >> 3;
+  C += bz * sC;
+  if (row0 >= m || col0 >= nn) {                 // the whole tile is outside the dynamic sizes
+    if (kz == 0) {
+      const int gr = row0 + (tid >> 4), gc = col0 + (tid & 15);
+      if (gr < M && gc < N) C[(long long)gr * ldc + gc] = 0.0;
+    }
+    return;
+  }
+  const int chunk = ((kk + splitK - 1) / splitK + BT - 1) / BT * BT;
+  const int kbeg = kz * chunk, kend = min(kk, kbeg + chunk);
+  A += bz * sA;
+  B += bz * sB;
+  float s[2][2], sl[2][2], cr[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) s[i][j] = sl[i][j] = cr[i][j] = 0.f;
+  for (int k0 = kbeg; k0 < kend; k0 += DF_KC) {
+    // 1024 elements of each operand, 4 per thread, all loads issued before the splits
+    double xa[4], xb[4];
+    int ka[4], ma[4], kb[4], nb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      if (!tA) { ma[q] = e >> 6; ka[q] = e & 63; } else { ka[q] = e >> 4; ma[q] = e & 15; }
+      if (!tB) { kb[q] = e >> 4; nb[q] = e & 15; } else { nb[q] = e >> 6; kb[q] = e & 63; }
+      const int ar = row0 + ma[q], gka = k0 + ka[q], bc = col0 + nb[q], gkb = k0 + kb[q];
+      xa[q] = (ar < m && gka < kend) ? (tA ? A[(long long)gka * lda + ar] : A[(long long)ar * lda + gka]) : 0.0;
+      xb[q] = (bc < nn && gkb < kend) ? (tB ? B[(long long)bc * ldb + gkb] : B[(long long)gkb * ldb + bc]) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      As[ka[q]][ma[q]] = df_split(xa[q]);
+      Bs[kb[q]][nb[q]] = df_split(xb[q]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 16 * grp; k < 16 * grp + 16; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[k][2 * ty]);   // rows 2ty, 2ty+1: (hi, lo)
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[k][2 * tx]);
+      const float ah[2] = {a.x, a.z}, al[2] = {a.y, a.w}, bh[2] = {b.x, b.z}, bl[2] = {b.y, b.w};
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const float p = __fmul_rn(ah[i], bh[j]);
+          const float e = __fmaf_rn(ah[i], bh[j], -p);
+          cr[i][j] = __fmaf_rn(al[i], bh[j], __fmaf_rn(ah[i], bl[j], __fadd_rn(cr[i][j], e)));
+          const float t = __fadd_rn(s[i][j], p);
+          const float bp = __fsub_rn(t, s[i][j]);
+          sl[i][j] = __fadd_rn(sl[i][j], __fadd_rn(__fsub_rn(s[i][j], __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+          s[i][j] = t;
+        }
+    }
+    __syncthreads();
+  }
+  // the four groups' sums, added in FP64 in group order
+  double acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      acc[i][j] = (double)s[i][j] + ((double)sl[i][j] + (double)cr[i][j]);
+      if (grp > 0) red[grp - 1][(2 * ty + i) * BT + 2 * tx + j] = acc[i][j];
+    }
+  __syncthreads();
+  if (grp > 0) return;                         // no barrier below involves the other groups
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int o = (2 * ty + i) * BT + 2 * tx + j;
+      acc[i][j] = ((acc[i][j] + red[0][o]) + red[1][o]) + red[2][o];
+    }
+  if (splitK > 1) {
+    const long long tile = ((long long)bz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) part[(tile * splitK + kz) * 256 + (2 * ty + i) * BT + 2 * tx + j] = acc[i][j];
+    __threadfence();
+    asm volatile("bar.sync 1, 64;" ::: "memory");   // the 64 threads of group 0
+    if (t6 == 0) s_last = (atomicAdd(&count[tile], 1u) == (unsigned)(splitK - 1));
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        double v = 0.0;
+        for (int z = 0; z < splitK; ++z) v += __ldcg(&part[(tile * splitK + z) * 256 + (2 * ty + i) * BT + 2 * tx + j]);
+        acc[i][j] = v;
+      }
+    if (t6 == 0) count[tile] = 0u;             // ready for the next product
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gr = row0 + 2 * ty + i, gc = col0 + 2 * tx + j;
+      if (gr < M && gc < N) C[(long long)gr * ldc + gc] = (gr < m && gc < nn) ? alpha * acc[i][j] : 0.0;
+    }
+}
+
+void gemm_batched_df(cudaStream_t s, bool transA, bool transB, int M, int N, int K, const double* A, int lda,
+                     long long sA, const double* B, int ldb, long long sB, double* C, int ldc, long long sC,
+                     int batch, const int* dynM, const int* dynN, const int* dynK, const GemmScratch* scr) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  const long long tiles = (long long)((N + 15) / 16) * ((M + 15) / 16) * batch;
+  int sk = (int)((2 * 152 + tiles - 1) / tiles);
+  const int maxs = (K + 15) / 16;
+  if (sk > maxs) sk = maxs;
+  if (!scr || !scr->part) sk = 1;
+  else if (tiles * sk > GEMM_SPLIT_SLOTS) sk = (int)(GEMM_SPLIT_SLOTS / tiles);
+  if (sk < 1) sk = 1;
+  dim3 grid((N + 15) / 16, (M + 15) / 16, batch * sk);
+  gemm_df_kernel<<<grid, 256, 0, s>>>(transA, transB, M, N, K, 1.0, A, lda, sA, B, ldb, sB, C, ldc, sC, sk, dynM,
+                                     dynN, dynK, sk > 1 ? scr->part : nullptr, sk > 1 ? scr->count : nullptr);
+}
+
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
@@ -1163,14 +1327,24 @@ __global__ void gather_Z_kernel(const double* Q, const int* order, int n, int ks
 constexpr int JACOBI_SWEEPS = 16;
 constexpr float JACOBI_TOL = 1e-5f;
 // T <- W^T T W for the leading ke block (two k x k products through T2k)
+// The eigen stage's FP64 products: double-float on the FP32-bulk path, FP64 on the FP64 path
+// (C = op(A) op(B), overwritten; deterministic K split through the context's scratch)
+static void eig_prod(Ctx& c, bool tA, bool tB, int M, int N, int K, const double* A, int lda, long long sA,
+                     const double* B, int ldb, long long sB, double* C, int ldc, long long sC, int batch,
+                     const int* dM, const int* dN, const int* dK) {
+  if (c.fp64)
+    gemm_batched<double>(c.stream, tA, tB, M, N, K, 1.0, A, lda, sA, B, ldb, sB, 0.0, C, ldc, sC, batch, dM, dN, dK,
+                         &c.gscr);
+  else
+    gemm_batched_df(c.stream, tA, tB, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, dM, dN, dK, &c.gscr);
+}
+
 static void congruence(Ctx& c, double* Tm, const double* Wm) {
   const int ks = c.ksub;
   const long long sK = (long long)ks * ks;
   const int* ke = c.sc->k_eff;
-  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, Tm, ks, sK, Wm, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, ke, ke, ke, &c.gscr);
-  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, Wm, ks, sK, c.T2k, ks, sK, 0.0,
-                       Tm, ks, sK, 3, ke, ke, ke, &c.gscr);
+  eig_prod(c, false, false, ks, ks, ks, Tm, ks, sK, Wm, ks, sK, c.T2k, ks, sK, 3, ke, ke, ke);
+  eig_prod(c, true, false, ks, ks, ks, Wm, ks, sK, c.T2k, ks, sK, Tm, ks, sK, 3, ke, ke, ke);
 }
 
 // Rayleigh-Ritz refinement: one FP32 Jacobi pass on the graded T (rotations accumulated in FP32,
@@ -1197,19 +1371,15 @@ static int refine(Ctx& c, double*& Qa, double*& Qb) {
     jacobi32_kernel<<<3, 1024, shm, c.stream>>>(c.T, c.W, ks, c.sc, JACOBI_SWEEPS, JACOBI_TOL);
   }
   // W2 = E = W^T W - I ; T2k = E^2 ; W2 = M
-  gemm_batched<double>(c.stream, true, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W, ks, sK, 0.0,
-                       c.W2, ks, sK, 3, ke, ke, ke, &c.gscr);
+  eig_prod(c, true, false, ks, ks, ks, c.W, ks, sK, c.W, ks, sK, c.W2, ks, sK, 3, ke, ke, ke);
   dim3 g2((ks * ks + 255) / 256, 3);
   sub_identity_kernel<<<g2, 256, 0, c.stream>>>(c.W2, ks, c.sc);
-  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W2, ks, sK, c.W2, ks, sK, 0.0,
-                       c.T2k, ks, sK, 3, ke, ke, ke, &c.gscr);
+  eig_prod(c, false, false, ks, ks, ks, c.W2, ks, sK, c.W2, ks, sK, c.T2k, ks, sK, 3, ke, ke, ke);
   ns_matrix_kernel<<<g2, 256, 0, c.stream>>>(c.W2, c.T2k, c.W2, ks, c.sc);
   // WM = W M (in the free product buffer Y) ; Qb = Qa (W M) ; T = (W M)^T T (W M)
   double* WM = c.Y;
-  gemm_batched<double>(c.stream, false, false, ks, ks, ks, 1.0, c.W, ks, sK, c.W2, ks, sK, 0.0,
-                       WM, ks, sK, 3, ke, ke, ke, &c.gscr);
-  gemm_batched<double>(c.stream, false, false, n, ks, ks, 1.0, Qa, ks, sQ, WM, ks, sK, 0.0, Qb,
-                       ks, sQ, 3, nullptr, ke, ke, &c.gscr);
+  eig_prod(c, false, false, ks, ks, ks, c.W, ks, sK, c.W2, ks, sK, WM, ks, sK, 3, ke, ke, ke);
+  eig_prod(c, false, false, n, ks, ks, Qa, ks, sQ, WM, ks, sK, Qb, ks, sQ, 3, nullptr, ke, ke);
   congruence(c, c.T, WM);
   std::swap(Qa, Qb);
   return 1 + 1 + 1 + 1 + 1 + 1 + 1 + 2;
@@ -1232,10 +1402,8 @@ int launch_subspace(Ctx& c) {
   }
   const int* ke = c.sc->k_eff;
   // Y = G Q ; T = Q^T Y
-  gemm_batched<double>(c.stream, false, false, n, ks, n, 1.0, c.G, n, sG, c.Q, ks, sQ, 0.0, c.Y,
-                       ks, sQ, 3, nullptr, ke, nullptr, &c.gscr);
-  gemm_batched<double>(c.stream, true, false, ks, ks, n, 1.0, c.Q, ks, sQ, c.Y, ks, sQ, 0.0, c.T,
-                       ks, sK, 3, ke, ke, nullptr, &c.gscr);
+  eig_prod(c, false, false, n, ks, n, c.G, n, sG, c.Q, ks, sQ, c.Y, ks, sQ, 3, nullptr, ke, nullptr);
+  eig_prod(c, true, false, ks, ks, n, c.Q, ks, sQ, c.Y, ks, sQ, c.T, ks, sK, 3, ke, ke, nullptr);
   // Rayleigh-Ritz refinement; the rotated basis ends in c.X
   double* Qa = c.Q;
   double* Qb = c.X;
