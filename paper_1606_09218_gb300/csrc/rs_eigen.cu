@@ -266,25 +266,33 @@ gemm_df_kernel(bool tA, bool tB, int M, int N, int K, double alpha, const double
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) s[i][j] = sl[i][j] = cr[i][j] = 0.f;
-  for (int k0 = kbeg; k0 < kend; k0 += DF_KC) {
-    // 1024 elements of each operand, 4 per thread, all loads issued before the splits
-    double xa[4], xb[4];
-    int ka[4], ma[4], kb[4], nb[4];
+  // 1024 elements of each operand per chunk, 4 per thread (positions fixed across chunks); the
+  // next chunk's loads are issued before the present chunk's arithmetic
+  int ka[4], ma[4], kb[4], nb[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = tid + 256 * q;
+    if (!tA) { ma[q] = e >> 6; ka[q] = e & 63; } else { ka[q] = e >> 4; ma[q] = e & 15; }
+    if (!tB) { kb[q] = e >> 4; nb[q] = e & 15; } else { nb[q] = e >> 6; kb[q] = e & 63; }
+  }
+  double xa[4], xb[4];
+  auto load = [&](int k0) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int e = tid + 256 * q;
-      if (!tA) { ma[q] = e >> 6; ka[q] = e & 63; } else { ka[q] = e >> 4; ma[q] = e & 15; }
-      if (!tB) { kb[q] = e >> 4; nb[q] = e & 15; } else { nb[q] = e >> 6; kb[q] = e & 63; }
       const int ar = row0 + ma[q], gka = k0 + ka[q], bc = col0 + nb[q], gkb = k0 + kb[q];
       xa[q] = (ar < m && gka < kend) ? (tA ? A[(long long)gka * lda + ar] : A[(long long)ar * lda + gka]) : 0.0;
       xb[q] = (bc < nn && gkb < kend) ? (tB ? B[(long long)bc * ldb + gkb] : B[(long long)gkb * ldb + bc]) : 0.0;
     }
+  };
+  if (kbeg < kend) load(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += DF_KC) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       As[ka[q]][ma[q]] = df_split(xa[q]);
       Bs[kb[q]][nb[q]] = df_split(xb[q]);
     }
     __syncthreads();
+    if (k0 + DF_KC < kend) load(k0 + DF_KC);
 #pragma unroll 4
     for (int k = 16 * grp; k < 16 * grp + 16; ++k) {
       const float4 a = *reinterpret_cast<const float4*>(&As[k][2 * ty]);   // rows 2ty, 2ty+1: (hi, lo)
@@ -360,7 +368,7 @@ void gemm_batched_df(cudaStream_t s, bool transA, bool transB, int M, int N, int
   if (M <= 0 || N <= 0 || batch <= 0) return;
   const long long tiles = (long long)((N + 15) / 16) * ((M + 15) / 16) * batch;
   int sk = (int)((2 * 152 + tiles - 1) / tiles);
-  const int maxs = (K + 15) / 16;
+  const int maxs = (K + 2 * DF_KC - 1) / (2 * DF_KC);     // at least two chunks per part
   if (sk > maxs) sk = maxs;
   if (!scr || !scr->part) sk = 1;
   else if (tiles * sk > GEMM_SPLIT_SLOTS) sk = (int)(GEMM_SPLIT_SLOTS / tiles);

@@ -105,14 +105,14 @@ constexpr uint32_t SLOT_HALF = AS_M * 16 * 2;    // one pair slot: 128 rows x K 
 // T2[a][i2][i3] = sum_b V2[i2][b] T1[a][b][i3]  (mode-2 product, Eq. (2.3)) written as the A
 // operand of the assembly: per output tile (128 consecutive points p = i2 n + i3, K = kp ranks)
 // an FP16 hi block and an FP16 lo block in the canonical K-major layout, scaled by 2^(S-8);
-// ranks a >= r1 and points beyond the grid are zero.  One CTA: 32 i3 x 32 i2, ranks in groups
-// of 8 (one 16-byte chunk of a row).
+// ranks a >= r1 and points beyond the grid are zero.  One CTA: 32 i3 x 32 i2, ranks in stages
+// of 4, two stages to a 16-byte chunk of a row.
 __global__ void __launch_bounds__(256)
 t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int n, int rmax, int kp,
                 int ntiles, DevScalars* sc, unsigned char* __restrict__ out,
                 unsigned long long tile_bytes) {
   extern __shared__ __align__(16) float tsm[];
-  float* T1s = tsm;                          // [rmax][2][32][4]: ranks a0 + 4h + (0..3) of (b, i3)
+  float* T1s = tsm;                          // [2][rmax][32][4]: stage of ranks 4h + (0..3) at (b, i3)
   float* V2s = tsm + 8 * rmax * 32;          // [rmax][8][4]: V2[i2b + w + 8q][b] at (b, w, q)
   __shared__ float s_scale;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -151,70 +151,84 @@ t2_tiles_kernel(const float* __restrict__ T1, const float* __restrict__ V2, int 
     for (int b = lane; b < rmax; b += 32)
       V2s[(b * 8 + (r & 7)) * 4 + (r >> 3)] = (i2 < n && b < r2) ? V2[(long long)i2 * rmax + b] : 0.f;
   }
-  for (int a0 = 0; a0 < kp; a0 += 8) {
-    if (a0 >= r1) {
-      // rank slices beyond r1: zero chunks, nothing to compute
-      if (i3 < n)
-        for (int q = 0; q < 4; ++q) {
-          const int i2 = i2b + warp + 8 * q;
-          if (i2 >= n) continue;
-          const long long p = (long long)i2 * n + i3;
-          unsigned char* tile = out + (unsigned long long)(p >> 7) * tile_bytes;
-          const uint32_t off = kmajor_offset((int)(p & 127), a0 >> 3, kp >> 3);
-          *(uint4*)(tile + off) = make_uint4(0, 0, 0, 0);
-          *(uint4*)(tile + half_bytes + off) = make_uint4(0, 0, 0, 0);
+  // 16-byte chunk (8 ranks from a0) of the four points (i2b + warp + 8 q, i3)
+  auto store_chunk = [&](int a0, const float (&lo4)[4][4], const float (&hi4)[4][4], bool zero) {
+    if (i3 >= n) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i2 = i2b + warp + 8 * q;
+      if (i2 >= n) continue;
+      uint4 hi = make_uint4(0, 0, 0, 0), lo = make_uint4(0, 0, 0, 0);
+      if (!zero) {
+        float xs[8];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          xs[x] = lo4[q][x] * scale;
+          xs[4 + x] = hi4[q][x] * scale;
         }
-      continue;
-    }
-    __syncthreads();
-    // asynchronous 4-byte copies (all in flight at once; warps over (rank, b) rows, lanes over
-    // i3); zero fill outside the ranks / grid
-    for (int x = 0; x < 8; ++x) {
-      const int a = a0 + x;
-      const bool in = a < r1 && i3 < n;
-      for (int b = warp; b < r2; b += 8) {
-        const float* src = in ? T1 + ((long long)a * rmax + b) * n + i3 : T1;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
-                         smem_addr(&T1s[((b * 2 + (x >> 2)) * 32 + lane) * 4 + (x & 3)])),
-                     "l"(src), "r"(in ? 4 : 0)
-                     : "memory");
+        split8_f16(xs, hi, lo);
       }
+      const long long p = (long long)i2 * n + i3;
+      unsigned char* tile = out + (unsigned long long)(p >> 7) * tile_bytes;
+      const uint32_t off = kmajor_offset((int)(p & 127), a0 >> 3, kp >> 3);
+      *(uint4*)(tile + off) = hi;
+      *(uint4*)(tile + half_bytes + off) = lo;
     }
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+  };
+  float lo4[4][4], hi4[4][4];
+  // rank slices beyond r1: zero chunks, nothing to compute
+  for (int a0 = (r1 + 7) & ~7; a0 < kp; a0 += 8) store_chunk(a0, lo4, hi4, true);
+  // ranks in stages of four (a0 = 4h), two stages in flight: the asynchronous 4-byte copies of
+  // stage h + 1 run while stage h is multiplied.  One copy instruction of a warp moves four
+  // ranks of eight consecutive i3 (thread t: rank t % 4, column 8 k + t / 4), 128 contiguous
+  // bytes of shared memory; zero fill outside the ranks / grid
+  const int H = 2 * ((r1 + 7) >> 3);
+  const int cx = lane & 3, cl = lane >> 2;
+  auto issue = [&](int h) {
+    float* buf = T1s + (size_t)(h & 1) * rmax * 128;
+    const int a = 4 * h + cx;
+    for (int e = warp; e < 4 * r2; e += 8) {
+      const int b = e >> 2, col = 8 * (e & 3) + cl;
+      const int i3c = t3 * AS_T3 + col;
+      const bool in = a < r1 && i3c < n;
+      const float* src = in ? T1 + ((long long)a * rmax + b) * n + i3c : T1;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(&buf[(b * 32 + col) * 4 + cx])),
+                   "l"(src), "r"(in ? 4 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // stage h -> ac[i2 row q][rank x]
+  auto stage = [&](int h, float (&ac)[4][4]) {
+    if (h + 1 < H) {
+      issue(h + 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
     __syncthreads();
-    float acc[4][8];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int x = 0; x < 8; ++x) acc[q][x] = 0.f;
-    const float4* T4 = reinterpret_cast<const float4*>(T1s);
+      for (int x = 0; x < 4; ++x) ac[q][x] = 0.f;
+    const float4* T4 = reinterpret_cast<const float4*>(T1s + (size_t)(h & 1) * rmax * 128);
     const float4* V4 = reinterpret_cast<const float4*>(V2s);
     for (int b = 0; b < r2; ++b) {
-      const float4 t0 = T4[(b * 2) * 32 + lane], t1 = T4[(b * 2 + 1) * 32 + lane], v = V4[b * 8 + warp];
-      const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+      const float4 t = T4[b * 32 + lane], v = V4[b * 8 + warp];
+      const float tv[4] = {t.x, t.y, t.z, t.w};
       const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int x = 0; x < 8; ++x) acc[q][x] = fmaf(vv[q], tv[x], acc[q][x]);
+        for (int x = 0; x < 4; ++x) ac[q][x] = fmaf(vv[q], tv[x], ac[q][x]);
     }
-    if (i3 < n) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i2 = i2b + warp + 8 * q;
-        if (i2 >= n) continue;
-        float xs[8];
-#pragma unroll
-        for (int x = 0; x < 8; ++x) xs[x] = acc[q][x] * scale;
-        uint4 hi, lo;
-        split8_f16(xs, hi, lo);
-        const long long p = (long long)i2 * n + i3;
-        unsigned char* tile = out + (unsigned long long)(p >> 7) * tile_bytes;
-        const uint32_t off = kmajor_offset((int)(p & 127), a0 >> 3, kp >> 3);
-        *(uint4*)(tile + off) = hi;
-        *(uint4*)(tile + half_bytes + off) = lo;
-      }
-    }
+    __syncthreads();                           // stage h's buffer is free for stage h + 2
+  };
+  if (H > 0) issue(0);
+  for (int h = 0; h < H; h += 2) {
+    stage(h, lo4);
+    stage(h + 1, hi4);
+    store_chunk(4 * h, lo4, hi4, false);
   }
 }
 
