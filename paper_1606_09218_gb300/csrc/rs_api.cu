@@ -189,8 +189,10 @@ void free_all(Ctx& c) {
   if (c.ev_part) cudaEventDestroy(c.ev_part);
   if (c.ev_bins) cudaEventDestroy(c.ev_bins);
   if (c.ev_side) cudaEventDestroy(c.ev_side);
+  if (c.ev_start) cudaEventDestroy(c.ev_start);
+  if (c.ev_fac) cudaEventDestroy(c.ev_fac);
   if (c.aux) cudaStreamDestroy(c.aux);
-  c.ev_part = c.ev_bins = c.ev_side = nullptr;
+  c.ev_part = c.ev_bins = c.ev_side = c.ev_start = c.ev_fac = nullptr;
   c.aux = nullptr;
 }
 
@@ -334,7 +336,9 @@ rs_status rs_create(const rs_config* cfg, void* stream, rs_ctx** out) {
   if (cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c.ev_part, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c.ev_bins, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c.ev_side, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c.ev_side, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.ev_start, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.ev_fac, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     g_create_err = "stream or event creation failed";
     free_all(c);
@@ -438,9 +442,19 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
     cudaMemcpyAsync(c.Z, Z, sizeof(double) * N, kind, s);
   }
   mark(0);
+  // the configuration's factors, window width and F (a1, a2 and the F of a3) on the context's
+  // second stream, beside the particle preparation: neither needs the other (so the "factors"
+  // stage of the profile is empty and the "particles" stage covers both)
+  cudaEventRecord(c.ev_start, s);
+  cudaStreamWaitEvent(c.aux, c.ev_start, 0);
+  c.stream = c.aux;
   k += launch_factors(c);                  // a1, a2: quadrature, factors, split, window width
+  k += launch_gram_setup(c);               // a3: F = sum_k p_k p_k^T; Gram matrices cleared
+  cudaEventRecord(c.ev_fac, c.aux);
+  c.stream = s;
   mark(1);
   k += launch_prepare_particles(c, N, min_sep, (flags & RS_VALIDATE_SEPARATION) != 0);
+  cudaStreamWaitEvent(s, c.ev_fac, 0);
   mark(2);
   // particle bins and window lists need only the particles and gamma: on the context's second
   // stream, overlapped with the Gram and eigen stages (which leave most SMs idle)

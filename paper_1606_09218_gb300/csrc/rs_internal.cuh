@@ -99,7 +99,7 @@ struct Ctx {
   int* als_start = nullptr;      // 3 x (n + 1): charged particles grouped by coordinate (CSR)
   int* als_items = nullptr;      // 3 x maxN
   int als_kc = 0;                // rows of one K chunk
-  cudaEvent_t ev_part = nullptr, ev_bins = nullptr, ev_side = nullptr;
+  cudaEvent_t ev_part = nullptr, ev_bins = nullptr, ev_side = nullptr, ev_start = nullptr, ev_fac = nullptr;
   int n = 0, R = 0, R_l = 0, R_s = 0, L = 0;   // L = 2n - 1
   int ksub = 0;        // subspace width (multiple of KB)
   int rmax = 0;        // rank bound = leading dimension of Tucker factors
@@ -299,7 +299,8 @@ inline DevView make_view(const Ctx& c) {
 // setup (rs_setup.cu)
 int launch_factors(Ctx& c);
 int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep);
-int launch_gram(Ctx& c);                 // F matrix + Gram matrices
+int launch_gram_setup(Ctx& c);           // F matrix, Gram matrices cleared (configuration only)
+int launch_gram(Ctx& c);                 // Gram matrices (after launch_gram_setup)
 // eigen stage (rs_eigen.cu)
 int launch_subspace(Ctx& c);
 // Tucker stage (rs_tucker.cu)

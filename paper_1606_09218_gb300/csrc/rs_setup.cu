@@ -451,15 +451,19 @@ gram_df_kernel(const float2* __restrict__ F2, const double* __restrict__ C, cons
   }
 }
 
+int launch_gram_setup(Ctx& c) {
+  launch_fmatrix(c, !c.fp64);                // double-float F on the FP32 bulk path
+  cudaMemsetAsync(c.G, 0, sizeof(double) * 3 * (size_t)c.n * c.n, c.stream);
+  return 1;
+}
+
 int launch_gram(Ctx& c) {
   const bool df = !c.fp64;                   // double-float sums on the FP32 bulk path
-  launch_fmatrix(c, df);
   int nt = (c.n + 31) / 32;
   dim3 grid(nt * (nt + 1) / 2, 3, 2);
-  cudaMemsetAsync(c.G, 0, sizeof(double) * 3 * (size_t)c.n * c.n, c.stream);
   if (df) gram_df_kernel<<<grid, 256, 0, c.stream>>>((const float2*)c.F, c.C, c.nzj, c.sc, c.n, c.G);
   else gram_kernel<<<grid, 256, 0, c.stream>>>(c.F, c.C, c.nzj, c.sc, c.n, c.G);
-  return 2;
+  return 1;
 }
 
 }  // namespace rs
