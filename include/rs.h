@@ -59,7 +59,10 @@ typedef enum {
 
 typedef enum {
     RS_FP64 = 0,        /* every stage in FP64 (the plain RS path) */
-    RS_FP32_SPLIT = 1,  /* FP64 eigen stage; FP32 bulk contractions with FP64 chunk accumulation */
+    RS_FP32_SPLIT = 1,  /* eigen stage in FP64-level arithmetic (double-float sums and products on
+                           the FP32 units, FP32 Jacobi rotations); FP32 bulk: the core contraction
+                           and the grid assembly on the tensor cores with FP16 hi/lo operands, FP32
+                           accumulation folded into compensated pairs and 64-bit fixed-point sums */
     RS_FP32 = 2         /* as RS_FP32_SPLIT (serving tolerance 1e-4 against the oracle) */
 } rs_precision;
 
