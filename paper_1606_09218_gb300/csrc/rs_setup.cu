@@ -43,16 +43,24 @@ __global__ void scalars_kernel(const double* pk64, int R, int R_l, int n, double
   const int L = 2 * n - 1, c0 = n - 1;
   __shared__ double sPR0, sPRl0;
   __shared__ int cnt;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // one warp loads the factors at the centre (32 at a time); lane 0 adds the cubes in the
+    // order k = 0, 1, ... (the order of the host's window-width computation)
+    const int lane = threadIdx.x;
     double a = 0.0, b = 0.0;
-    for (int k = 0; k < R; ++k) {
-      double v = pk64[k * L + c0];
-      a += v * v * v;
-      if (k < R_l) b += v * v * v;
+    for (int k0 = 0; k0 < R; k0 += 32) {
+      const double v = (k0 + lane < R) ? pk64[(k0 + lane) * L + c0] : 0.0;
+      for (int q = 0; q < 32 && k0 + q < R; ++q) {
+        const double w = __shfl_sync(0xffffffffu, v, q);
+        a += w * w * w;
+        if (k0 + q < R_l) b += w * w * w;
+      }
     }
-    sPR0 = a;
-    sPRl0 = b;
-    cnt = 0;
+    if (lane == 0) {
+      sPR0 = a;
+      sPRl0 = b;
+      cnt = 0;
+    }
   }
   __syncthreads();
   const double delta = delta_rel * sPR0;
@@ -77,8 +85,10 @@ __global__ void scalars_kernel(const double* pk64, int R, int R_l, int n, double
 
 int launch_factors(Ctx& c) {
   int tot = c.R * c.L;
-  factors_kernel<<<(tot + 255) / 256, 256, 0, c.stream>>>(c.pk64, c.pk32, c.pk32lo, c.dpk64, c.dpk32, c.R,
-                                                          c.n, c.h, c.cfg.h_q, c.cfg.u0);
+  // 64-thread CTAs: the FP64 special functions are bound by each SM's FP64 pipe, so the work is
+  // spread over every SM instead of a hundred
+  factors_kernel<<<(tot + 63) / 64, 64, 0, c.stream>>>(c.pk64, c.pk32, c.pk32lo, c.dpk64, c.dpk32, c.R, c.n,
+                                                       c.h, c.cfg.h_q, c.cfg.u0);
   scalars_kernel<<<1, 256, 0, c.stream>>>(c.pk64, c.R, c.R_l, c.n, c.cfg.delta_rel, c.sc);
   return 2;
 }
@@ -250,30 +260,58 @@ __global__ void fmatrix_kernel(const double* pk64, int R_l, int L, double* F) {
 // The same F for the double-float Gram, as FP32 pairs (hi, lo), from the factors as FP32 pairs:
 // each product p_k[a] p_k[b] as hi*hi plus its exact rounding error plus the two cross terms,
 // the R_l positive terms added by two-sums (relative error about 2^-46), no FP64 arithmetic.
-__global__ void fmatrix_df_kernel(const float* __restrict__ ph, const float* __restrict__ pl, int R_l, int L,
-                                  float2* F2) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  int a = blockIdx.y;
-  if (b >= L) return;
-  float s = 0.f, t = 0.f;
-  for (int k = 0; k < R_l; ++k) {
-    const float xa = ph[k * L + a], ya = pl[k * L + a], xb = ph[k * L + b], yb = pl[k * L + b];
-    const float p = __fmul_rn(xa, xb);
-    float e = fmaf(xa, xb, -p);
-    e = fmaf(xa, yb, e);
-    e = fmaf(ya, xb, e);
-    const float u = __fadd_rn(s, p);
-    const float z = __fsub_rn(u, s);
-    t = __fadd_rn(t, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(u, z)), __fsub_rn(p, z)), e));
-    s = u;
+// (a CTA takes FM_ROWS rows a and 256 columns b: each column's factors are loaded once for its
+// rows, the rows' factors are staged in shared memory)
+constexpr int FM_ROWS = 4;
+__global__ void __launch_bounds__(256)
+fmatrix_df_kernel(const float* __restrict__ ph, const float* __restrict__ pl, int R_l, int L, float2* F2) {
+  __shared__ float2 pa[FM_ROWS][32];           // (hi, lo) of p_k[a] for the CTA's rows, 32 ranks k
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a0 = blockIdx.y * FM_ROWS;
+  float s[FM_ROWS], t[FM_ROWS];
+#pragma unroll
+  for (int r = 0; r < FM_ROWS; ++r) s[r] = t[r] = 0.f;
+  for (int k0 = 0; k0 < R_l; k0 += 32) {
+    const int nk = min(32, R_l - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < FM_ROWS * 32; e += blockDim.x) {
+      const int r = e >> 5, k = e & 31, a = a0 + r;
+      pa[r][k] = (a < L && k < nk) ? make_float2(ph[(k0 + k) * L + a], pl[(k0 + k) * L + a]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (b < L)
+      for (int k = 0; k < nk; ++k) {
+        const float xb = ph[(k0 + k) * L + b], yb = pl[(k0 + k) * L + b];
+#pragma unroll
+        for (int r = 0; r < FM_ROWS; ++r) {
+          const float xa = pa[r][k].x, ya = pa[r][k].y;
+          const float p = __fmul_rn(xa, xb);
+          float e = fmaf(xa, xb, -p);
+          e = fmaf(xa, yb, e);
+          e = fmaf(ya, xb, e);
+          const float u = __fadd_rn(s[r], p);
+          const float z = __fsub_rn(u, s[r]);
+          t[r] = __fadd_rn(t[r], __fadd_rn(__fadd_rn(__fsub_rn(s[r], __fsub_rn(u, z)), __fsub_rn(p, z)), e));
+          s[r] = u;
+        }
+      }
   }
-  const float hi = __fadd_rn(s, t);
-  F2[(long long)a * L + b] = make_float2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
+  if (b >= L) return;
+#pragma unroll
+  for (int r = 0; r < FM_ROWS; ++r) {
+    const int a = a0 + r;
+    if (a < L) {
+      const float hi = __fadd_rn(s[r], t[r]);
+      F2[(long long)a * L + b] = make_float2(hi, __fsub_rn(t[r], __fsub_rn(hi, s[r])));
+    }
+  }
 }
 
 static void launch_fmatrix(Ctx& c, bool split) {
   dim3 grid((c.L + 255) / 256, c.L);
-  if (split) fmatrix_df_kernel<<<grid, 256, 0, c.stream>>>(c.pk32, c.pk32lo, c.R_l, c.L, (float2*)c.F);
+  if (split)
+    fmatrix_df_kernel<<<dim3((c.L + 255) / 256, (c.L + FM_ROWS - 1) / FM_ROWS), 256, 0, c.stream>>>(
+        c.pk32, c.pk32lo, c.R_l, c.L, (float2*)c.F);
   else fmatrix_kernel<<<grid, 256, 0, c.stream>>>(c.pk64, c.R_l, c.L, c.F);
 }
 
