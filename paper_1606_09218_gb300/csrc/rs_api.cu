@@ -442,14 +442,16 @@ rs_status rs_solve(rs_ctx* h, int N, const double* xyz, const double* Z, int fla
     cudaMemcpyAsync(c.Z, Z, sizeof(double) * N, kind, s);
   }
   mark(0);
-  // the configuration's factors, window width and F (a1, a2 and the F of a3) on the context's
-  // second stream, beside the particle preparation: neither needs the other (so the "factors"
-  // stage of the profile is empty and the "particles" stage covers both)
+  // the configuration's factors, window width and F (a1, a2 and the F of a3), and the list of
+  // charged particles, on the context's second stream beside the snapping and aggregation of the
+  // particles: neither needs the other (so the "factors" stage of the profile is empty and the
+  // "particles" stage covers both)
   cudaEventRecord(c.ev_start, s);
   cudaStreamWaitEvent(c.aux, c.ev_start, 0);
   c.stream = c.aux;
   k += launch_factors(c);                  // a1, a2: quadrature, factors, split, window width
   k += launch_gram_setup(c);               // a3: F = sum_k p_k p_k^T; Gram matrices cleared
+  k += launch_compact_nz(c, N);            // the charged particles (needs only Z)
   cudaEventRecord(c.ev_fac, c.aux);
   c.stream = s;
   mark(1);

@@ -298,7 +298,8 @@ inline DevView make_view(const Ctx& c) {
 // Each launcher enqueues its kernels on c.stream and returns how many kernels it launched.
 // setup (rs_setup.cu)
 int launch_factors(Ctx& c);
-int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep);
+int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep);   // snap, weights, nzj
+int launch_compact_nz(Ctx& c, int N);   // charged particles, their count and sum |z|
 int launch_gram_setup(Ctx& c);           // F matrix, Gram matrices cleared (configuration only)
 int launch_gram(Ctx& c);                 // Gram matrices (after launch_gram_setup)
 // eigen stage (rs_eigen.cu)

@@ -118,11 +118,17 @@ __global__ void prepare_kernel(const double* xyz, const double* Z, int N, int n,
   int jj[3];
   const bool ok = snap_particle(xyz, z, p, n, b, h, jj);
   for (int l = 0; l < 3; ++l) j[3 * p + l] = jj[l];
-  if (!ok) {
-    atomicOr(&sc->flags, (unsigned)FLAG_OUTSIDE);
-    return;
+  if (!ok) atomicOr(&sc->flags, (unsigned)FLAG_OUTSIDE);
+  // the largest w^2 of the warp first (bits of non-negative doubles order as their values), one
+  // atomic per warp instead of one per particle on a single address
+  unsigned long long wb = (ok && z != 0.0) ? (unsigned long long)__double_as_longlong(pow(fabs(z), 2.0 / 3.0)) : 0ull;
+  const unsigned act = __activemask();
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(act, wb, o);
+    const int src = (threadIdx.x & 31) ^ o;
+    if ((act >> src) & 1u) wb = u > wb ? u : wb;
   }
-  if (z != 0.0) atomicMax(&sc->w2max_bits, (unsigned long long)__double_as_longlong(pow(fabs(z), 2.0 / 3.0)));
+  if ((threadIdx.x & 31) == __ffs(act) - 1 && wb != 0ull) atomicMax(&sc->w2max_bits, wb);
 }
 
 // The weights C_l[j] = sum_{nu at j} w_nu^2 per grid coordinate (columns at equal shifts add in
@@ -229,15 +235,19 @@ __global__ void separation_kernel(const double* xyz, int N, double min_sep2, Dev
   }
 }
 
+int launch_compact_nz(Ctx& c, int N) {
+  compact_nz_kernel<<<1, 1024, 0, c.stream>>>(c.Z, N, c.nz_idx, c.sc);
+  return 1;
+}
+
 int launch_prepare_particles(Ctx& c, int N, double min_sep, bool check_sep) {
-  int k = 2;
+  int k = 1;
   cudaMemsetAsync(c.C, 0, sizeof(double) * 3 * c.n, c.stream);
   if (N > 0) {
     prepare_kernel<<<(N + 255) / 256, 256, 0, c.stream>>>(c.xyz, c.Z, N, c.n, c.cfg.b, c.h, c.j, c.sc);
     aggregate_kernel<<<(N + 255) / 256, 256, 0, c.stream>>>(c.xyz, c.Z, N, c.n, c.cfg.b, c.h, c.C, c.sc);
     k += 2;
   }
-  compact_nz_kernel<<<1, 1024, 0, c.stream>>>(c.Z, N, c.nz_idx, c.sc);
   compact_nzj_kernel<<<3, 1024, 0, c.stream>>>(c.C, c.n, N, c.nzj, c.sc);
   if (check_sep && N > 1) {
     separation_kernel<<<(N + 127) / 128, 128, 0, c.stream>>>(c.xyz, N, min_sep * min_sep, c.sc);
