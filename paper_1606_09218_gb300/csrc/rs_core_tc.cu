@@ -368,13 +368,16 @@ __global__ void __launch_bounds__(CT_THREADS, 1) core_tc_kernel(CoreArgs g) {
 // particle capacity; each window holds ceil(Kc / passes) chunks of the actual ranks).
 
 constexpr uint32_t KR_A = 2 * CT_A_HALF;          // one A block: hi and lo of 128 pairs x 64 K
-constexpr uint32_t KR_B = 2 * CT_B_HALF;          // one B block: hi and lo of 64 c x 64 K
+// one B block: hi and lo of cn values of c x 64 K (cn = 64 when r3 <= 64, else 96)
+__host__ __device__ constexpr uint32_t kr_b(int cn) { return 2u * (uint32_t)cn * CT_KC * 2u; }
+constexpr uint32_t KR_SMEM = CT_SMEM;             // stage ring: 4 stages at cn = 64, 3 at cn = 96
+constexpr uint32_t KR_TMEM_COLS = 256;            // two accumulators of up to 96 columns
 constexpr int KR_EPI = 8;
 constexpr int KR_THREADS = 32 * (2 + KR_EPI);     // MMA warp, loader warp, 8 epilogue warps
 constexpr int KR_MAX_PASSES = 8;
 
 struct KrGeom {
-  int mt, nt, w;           // tiles of 128 pairs, tiles of 64 c, chunks of a window
+  int mt, nt, cn, w;       // tiles of 128 pairs, tiles of cn values of c, chunks of a window
   long long kc, ktot;      // chunks and terms of K
 };
 
@@ -383,7 +386,8 @@ __device__ __forceinline__ KrGeom kr_geom(const DevScalars* sc, int R_l, int pas
   G.ktot = (long long)sc->n_nz * R_l;
   G.kc = (G.ktot + CT_KC - 1) / CT_KC;
   G.mt = (sc->rank[0] * sc->rank[1] + CT_M - 1) / CT_M;
-  G.nt = (sc->rank[2] + CT_N - 1) / CT_N;
+  G.cn = sc->rank[2] <= 64 ? 64 : 96;               // one c tile up to r3 = 96: each A block read once
+  G.nt = (sc->rank[2] + G.cn - 1) / G.cn;
   G.w = (int)((G.kc + passes - 1) / passes);
   return G;
 }
@@ -457,11 +461,12 @@ core_w_kernel(const float* __restrict__ Qp, const int4* __restrict__ meta, const
         }
       }
     } else {
+      const uint32_t krb = kr_b(G.cn);
       for (int nl = 0; nl < G.nt; ++nl) {
-        unsigned char* blk = B3 + ((unsigned long long)nl * wstride + cl) * KR_B;
-        for (int task = tid; task < CT_N * 8; task += 256) {
-          const int row = task & (CT_N - 1), kg = task >> 6;
-          const int cc = nl * CT_N + row;
+        unsigned char* blk = B3 + ((unsigned long long)nl * wstride + cl) * krb;
+        for (int task = tid; task < G.cn * 8; task += 256) {
+          const int kg = task / G.cn, row = task - kg * G.cn;
+          const int cc = nl * G.cn + row;
           float x[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -472,7 +477,7 @@ core_w_kernel(const float* __restrict__ Qp, const int4* __restrict__ meta, const
           split8_f16(x, hi, lo);
           const uint32_t off = kmajor_offset(row, kg, CT_KC / 8);
           *(uint4*)(blk + off) = hi;
-          *(uint4*)(blk + CT_B_HALF + off) = lo;
+          *(uint4*)(blk + krb / 2 + off) = lo;
         }
       }
       const int first = pairs - (G.mt - 1) * CT_M;    // live rows of the last pair tile
@@ -513,16 +518,19 @@ struct KrArgs {
   int rmax, R_l, passes, pass, wstride;
 };
 
-__global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_full[CT_STAGES], bar_empty[CT_STAGES];
+template <int CN>
+__device__ __forceinline__ void kr_body(const KrArgs& g, const KrGeom& G, unsigned char* smem) {
+  // c tiles of CN values: stages of one A block and one B block, CN / 2 columns per epilogue warp
+  constexpr uint32_t KRB = kr_b(CN);
+  constexpr uint32_t KR_STAGE = KR_A + KRB;
+  constexpr int KR_ST = (int)(KR_SMEM / KR_STAGE);
+  constexpr int CH = CN / 2;
+  __shared__ __align__(8) uint64_t bar_full[KR_ST], bar_empty[KR_ST];
   __shared__ __align__(8) uint64_t bar_dfull[2], bar_dempty[2], bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_s;
   volatile int* abort_flag = &abort_s;
-
   DevScalars* sc = g.sc;
-  const KrGeom G = kr_geom(sc, g.R_l, g.passes);
   const long long c0 = (long long)g.pass * G.w;
   const int wl = (int)max(0ll, min((long long)G.w, G.kc - c0));
   const int tiles = G.mt * G.nt;
@@ -547,7 +555,7 @@ __global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
   kr_scales(sc, sA, sB);
 
   if (tid == 0) {
-    for (int s = 0; s < CT_STAGES; ++s) {
+    for (int s = 0; s < KR_ST; ++s) {
       mbar_init(&bar_full[s], 1);
       mbar_init(&bar_empty[s], 1);
     }
@@ -563,7 +571,7 @@ __global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
     __syncwarp();
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&tmem_slot)),
-                 "r"(CT_TMEM_COLS)
+                 "r"(KR_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -577,9 +585,9 @@ __global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
     if (lane == 0) {
       const uint64_t dA = smem_desc(smem_addr(smem), 128, (CT_KC / 8) * 128);
       const uint64_t dB = smem_desc(smem_addr(smem + KR_A), 128, (CT_KC / 8) * 128);
-      const uint64_t st_step = (uint64_t)CT_STAGE >> 4;
-      const uint64_t a_lo = (uint64_t)CT_A_HALF >> 4, b_lo = (uint64_t)CT_B_HALF >> 4;
-      const uint32_t idesc = idesc_f16(CT_N, CT_M);
+      const uint64_t st_step = (uint64_t)KR_STAGE >> 4;
+      const uint64_t a_lo = (uint64_t)CT_A_HALF >> 4, b_lo = (uint64_t)(KRB / 2) >> 4;
+      const uint32_t idesc = idesc_f16(CN, CT_M);
       long long gc = 0, gseg = 0;
       bool ok = true;
       for (long long pos = lo; ok && pos < hi;) {
@@ -591,13 +599,13 @@ __global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
             ok = false;
             break;
           }
-          const int st = (int)(gc % CT_STAGES);
-          if (!wait_bar(&bar_full[st], (uint32_t)(gc / CT_STAGES) & 1u, abort_flag, sc)) {
+          const int st = (int)(gc % KR_ST);
+          if (!wait_bar(&bar_full[st], (uint32_t)(gc / KR_ST) & 1u, abort_flag, sc)) {
             ok = false;
             break;
           }
           fence_after_sync();
-          const uint32_t d = tmem + (uint32_t)(buf * CT_N);
+          const uint32_t d = tmem + (uint32_t)(buf * CN);
           const uint64_t ah = dA + (uint64_t)st * st_step, al = ah + a_lo;
           const uint64_t bh = dB + (uint64_t)st * st_step, bl = bh + b_lo;
 #pragma unroll
@@ -627,37 +635,37 @@ __global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
         int m, nl, cb, ce;
         pos = next_unit(pos, m, nl, cb, ce);
         for (int cl = cb; cl < ce; ++cl) {
-          const int st = (int)(gc % CT_STAGES);
-          if (gc >= CT_STAGES && !wait_bar(&bar_empty[st], (uint32_t)(gc / CT_STAGES - 1) & 1u, abort_flag, sc)) {
+          const int st = (int)(gc % KR_ST);
+          if (gc >= KR_ST && !wait_bar(&bar_empty[st], (uint32_t)(gc / KR_ST - 1) & 1u, abort_flag, sc)) {
             ok = false;
             break;
           }
-          unsigned char* base = smem + (size_t)st * CT_STAGE;
-          mbar_expect_tx(&bar_full[st], KR_A + KR_B);
+          unsigned char* base = smem + (size_t)st * KR_STAGE;
+          mbar_expect_tx(&bar_full[st], KR_A + KRB);
           bulk_load(base, g.W + ((unsigned long long)m * g.wstride + cl) * KR_A, KR_A, &bar_full[st]);
-          bulk_load(base + KR_A, g.B3 + ((unsigned long long)nl * g.wstride + cl) * KR_B, KR_B, &bar_full[st]);
+          bulk_load(base + KR_A, g.B3 + ((unsigned long long)nl * g.wstride + cl) * KRB, KRB, &bar_full[st]);
           ++gc;
         }
       }
       // the copies issued last have landed before the shared memory goes away
-      for (long long t = gc > CT_STAGES ? gc - CT_STAGES : 0; t < gc; ++t)
-        drain_bar(&bar_full[t % CT_STAGES], (uint32_t)(t / CT_STAGES) & 1u, sc);
+      for (long long t = gc > KR_ST ? gc - KR_ST : 0; t < gc; ++t)
+        drain_bar(&bar_full[t % KR_ST], (uint32_t)(t / KR_ST) & 1u, sc);
     }
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;                         // 0 .. 7
     const int q = warp & 3;                          // tensor-memory lanes 32q .. 32q + 31
-    const int half = ew >> 2;                        // columns 32 half .. 32 half + 31
+    const int half = ew >> 2;                        // columns CH half .. CH half + CH - 1
     const int fx_e = beta_fx_shift(sc, g.R_l) - sA - sB;   // fixed-point exponent of the sums
     long long gseg = 0;
     bool ok = true;
     for (long long pos = lo; ok && pos < hi;) {
       int m, nl, cb, ce;
       pos = next_unit(pos, m, nl, cb, ce);
-      float hi[32], lo[32];
+      float hi[CH], lo[CH];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < CH; ++j) {
         hi[j] = 0.f;
         lo[j] = 0.f;
       }
@@ -668,13 +676,13 @@ __global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
           break;
         }
         fence_after_sync();
-        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * CT_N + 32 * half);
-        uint32_t v[32];
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * CN + CH * half);
+        uint32_t v[CH];
 #pragma unroll
-        for (int u8 = 0; u8 < 4; ++u8) tmem_ld8(ta + (uint32_t)(8 * u8), v + 8 * u8);
+        for (int u8 = 0; u8 < CH / 8; ++u8) tmem_ld8(ta + (uint32_t)(8 * u8), v + 8 * u8);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) two_sum_acc(hi[j], lo[j], __uint_as_float(v[j]));
+        for (int j = 0; j < CH; ++j) two_sum_acc(hi[j], lo[j], __uint_as_float(v[j]));
         fence_before_sync();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar_dempty[buf]);
@@ -682,13 +690,13 @@ __global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
       }
       if (!ok) break;
       const int rho = m * CT_M + 32 * q + lane;
-      const int cbase = nl * CT_N + 32 * half;
+      const int cbase = nl * CN + CH * half;
       if (rho < r1 * r2) {
         const int a = rho / r2, b = rho - a * r2;
         unsigned long long* out = reinterpret_cast<unsigned long long*>(g.beta64) +
                                   ((long long)a * g.rmax + b) * g.rmax + cbase;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
+        for (int j = 0; j < CH; ++j)
           if (cbase + j < r3) atomicAdd(out + j, (unsigned long long)(fx_f32(hi[j], fx_e) + fx_f32(lo[j], fx_e)));
       }
     }
@@ -697,20 +705,29 @@ __global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
   __syncthreads();
   if (warp == 0) {
     fence_after_sync();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CT_TMEM_COLS)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(KR_TMEM_COLS)
                  : "memory");
   }
 }
 
+__global__ void __launch_bounds__(KR_THREADS, 1) core_kr_kernel(KrArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const KrGeom G = kr_geom(g.sc, g.R_l, g.passes);
+  if (G.cn == 64)
+    kr_body<64>(g, G, smem);
+  else
+    kr_body<96>(g, G, smem);
+}
 
 // Workspace of the Khatri-Rao contraction for the context's rank cap and particle capacity:
 // windows of at most `wstride` chunks, `passes` of them; 0 when it would take more than
 // KR_MAX_PASSES windows (the contraction is then left to the other two forms).
 size_t core_kr_plan(const Ctx& c, int& passes, int& wstride) {
   const long long mt = ((long long)c.rmax * c.rmax + CT_M - 1) / CT_M;
-  const long long nt = (c.rmax + CT_N - 1) / CT_N;
   const long long kc = ((long long)c.maxN * c.R_l + CT_KC - 1) / CT_KC;
-  const size_t per_chunk = (size_t)mt * KR_A + (size_t)nt * KR_B;
+  // q3 blocks for the wider of the two c tilings the ranks may choose
+  const size_t b3 = std::max<size_t>((size_t)((c.rmax + 63) / 64) * kr_b(64), (size_t)((c.rmax + 95) / 96) * kr_b(96));
+  const size_t per_chunk = (size_t)mt * KR_A + b3;
   const size_t grid_bytes = (size_t)4 * c.n * c.n * c.n;
   const size_t budget = std::max<size_t>((size_t)256 << 20, 2 * grid_bytes);
   long long p = (long long)(((size_t)kc * per_chunk + budget - 1) / budget);

@@ -359,7 +359,7 @@ def test_tensor_core_core_matches_cuda_core_path(monkeypatch, path):
 
 def test_khatri_rao_core_over_windows_and_c_tiles(monkeypatch):
     """The forces workload (N = 4096, r = 66, snapped): its Khatri-Rao operands take several
-    windows of K and two tiles of 64 values of c.  Against the CUDA-core contraction: the same
+    windows of K, and r3 > 64 puts c in one tile of 96 values.  Against the CUDA-core contraction: the same
     ranks, potentials within 1e-6, the energy within 3e-7 of its scale, and a repeated solve
     bit-identical (fixed-point sums)."""
     cfg = dict(load_config("c5_forces4096_n513"), snap=True)
