@@ -353,17 +353,18 @@ __global__ void __launch_bounds__(CT_THREADS, 1) core_tc_kernel(CoreArgs g) {
 // The same contraction with the Khatri-Rao product of the first two modes formed once:
 //   W[(a, b)][K] = z_K q1[K][a] q2[K][b]     (rows rho = a r2 + b, r1 r2 of them)
 //   beta[a][b][c] = sum_K W[(a, b)][K] q3[K][c]
-// a GEMM with M = 128 pairs (a, b), N = 64 values of c and K in chunks of 64 terms.
+// a GEMM with M = 128 pairs (a, b), N = cn values of c (64 when r3 <= 64, else 96, so that one
+// tile holds every c up to r3 = 96 and each W block is read once) and K in chunks of 64 terms.
 // core_w_kernel writes W and q3 as FP16 hi / lo chunks in the canonical K-major layout of the
-// MMA operands (32 KB per 128 pairs and chunk, 16 KB per 64 c and chunk), scaled by 2^sA and 2^sB
-// as above.  core_kr_kernel copies them into a ring of shared-memory stages with bulk copies (one
+// MMA operands (32 KB per 128 pairs and chunk, cn x 256 bytes per cn values of c and chunk),
+// scaled by 2^sA and 2^sB as above.  core_kr_kernel copies them into a ring of shared-memory stages with bulk copies (one
 // loader warp), accumulates 64-term segments in tensor memory, folds every segment into FP32
 // (hi, lo) pairs and adds each unit's pairs to beta as fixed-point integers.  Against the producers
 // of core_tc_kernel every operand value is built once instead of once per output tile, and all
 // 128 rows of a tile are live (r1 r2 pairs instead of r1 < 128 rows a).
 //
-// The operands of all K would take Mt Kc 48 KB at the largest ranks (Mt tiles of pairs, Kc
-// chunks); a workspace of a fixed size holds a window of chunks, and the K range is covered in
+// The operands of all K would take Mt Kc (32 KB + q3 blocks) at the largest ranks (Mt tiles of
+// pairs, Kc chunks); a workspace of a fixed size holds a window of chunks, and the K range is covered in
 // `passes` windows (the same number for every launch, fixed on the host from the rank cap and the
 // particle capacity; each window holds ceil(Kc / passes) chunks of the actual ranks).
 
