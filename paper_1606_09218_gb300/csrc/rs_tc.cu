@@ -67,6 +67,8 @@ constexpr int WL_SORT_CAP = 4096;          // longest window list of one tile co
 constexpr int SMEM_LIMIT = 232448;         // opt-in shared memory per CTA on this GPU family
 constexpr int SMEM_RESERVE = 1024;         // static shared memory of the kernel
 constexpr double COST_TILE = 2500.0;       // relative cost of one tile job (output bound)
+constexpr double COST_TILE_STAGED = 1500.0;  // ... with the staged epilogue (fitted: 1000 / 1500 / 2500
+                                           // gave 492 / 416 / 424 us on the protein workload)
 constexpr double COST_WINDOW = 87.0;       // relative cost of one window of a job (fitted to role traces:
                                            // about 7.8K cycles per job and 270 per window on the
                                            // protein workload, with two producer groups)
@@ -94,6 +96,7 @@ struct AsmArgs {
   int nch, Nc, kp, gcap, TR, D0, ntiles, dstride, tmem_cols, na, ns;
   uint32_t off_bv, off_a, off_slot, off_tbl, off_tab, off_list, off_stage;
   int staged;                  // epilogue through shared staging rows and bulk stores
+  double cost_tile;            // relative cost of a tile job in the CTA split (COST_TILE*)
   uint32_t bv_half, a_half, tbl_half;   // bytes of each hi part (the lo part follows)
 };
 
@@ -352,7 +355,7 @@ assemble_kernel(const AsmArgs g) {
     // spread the CTAs over the i1 chunks in proportion to their work (same result in every CTA)
     double cost[32], tot = 0.0;
     for (int c = 0; c < g.nch; ++c) {
-      cost[c] = COST_TILE * g.ntiles + COST_WINDOW * (double)sc->chunk_w[c];
+      cost[c] = g.cost_tile * g.ntiles + COST_WINDOW * (double)sc->chunk_w[c];
       tot += cost[c];
     }
     int cnt[32], used = 0;
@@ -970,8 +973,9 @@ bool plan_assemble(Ctx& c) {
   if (c.tc_nch > 32) return false;
   const Layout L = layout_of(c);
   const size_t limit = (size_t)(SMEM_LIMIT - SMEM_RESERVE);
-  // deepest operand rings that fit, with the staged epilogue (faster stores) unless dropping
-  // its staging rows buys a deeper ring (large ranks)
+  // deepest operand rings that fit, with the staged epilogue (faster stores: the protein
+  // workload's assembly 431 -> 416 us at a split refitted to it, with six window slots instead of
+  // eight) unless dropping its staging rows buys a ring more than one step deeper (large ranks)
   // (at least two window slots: the two producer groups build alternate pairs)
   const int choices[5][2] = {{2, 8}, {2, 6}, {2, 4}, {1, 4}, {1, 2}};
   int best[2] = {-1, -1};
@@ -982,7 +986,7 @@ bool plan_assemble(Ctx& c) {
         break;
       }
   if (best[0] < 0) return false;
-  c.tc_staged = best[1] >= 0 && best[1] <= best[0];
+  c.tc_staged = best[1] >= 0 && best[1] <= best[0] + 1;   // staging may cost one ring step
   const int pick = c.tc_staged ? best[1] : best[0];
   c.tc_na = choices[pick][0];
   c.tc_ns = choices[pick][1];
@@ -1049,6 +1053,7 @@ int launch_assemble(Ctx& c, float* out) {
   g.off_list = (uint32_t)(g.off_tab + L.tab);
   g.off_stage = (uint32_t)(g.off_list + L.list);
   g.staged = c.tc_staged ? 1 : 0;
+  g.cost_tile = c.tc_staged ? COST_TILE_STAGED : COST_TILE;
   g.bv_half = (uint32_t)L.bv_half;
   g.a_half = (uint32_t)L.a_half;
   g.tbl_half = (uint32_t)L.tbl_half;
